@@ -1,0 +1,177 @@
+/*
+ * snk.h -- C ABI of libsnk: the seminumerical exact-exchange (sn-K) build of
+ * hybrid Gaussian-basis Kohn-Sham DFT (arXiv 2303.14280) on one GB300 GPU.
+ *
+ * The library evaluates, for a basis set B, a quadrature grid Q = {(w_i, r_i)}
+ * and a symmetric density matrix P,
+ *
+ *   Phi_{nu i}  = phi_nu(r_i)                              Sec. II.C, Eq. (collocation)
+ *   F_{lam i}   = sum_nu P_{lam nu} Phi_{nu i}            Sec. II.C, Eq. (fmat)
+ *   A_{mu lam}(r_i) = int phi_mu phi_lam / |r - r_i|       Sec. II.D, Eq. (3c_grid)
+ *   G_{mu i}    = w_i sum_lam A_{mu lam}(r_i) F_{lam i}   Sec. II.D, Eq. (gmat)
+ *   Kt_{mu nu}  = sum_i G_{mu i} Phi_{nu i}               Sec. II.D, Eq. (usym_k)
+ *   K_{mu nu}   = (Kt_{mu nu} + Kt_{nu mu}) / 2           Sec. II.D, Eq. (sn_k)
+ *
+ * over octree grid batches Q_j (Sec. II.E) with the basis screen B_j
+ * (Eq. basis_screen) and the sn-LinK pair screen V_j (Eqs. sp_set,
+ * exx_fmat_approx, batch_local_exx).  A is evaluated by the Obara-Saika
+ * recursions of App. A (Eqs. vrr, hrr), contracted with F on the fly.
+ *
+ * Conventions
+ *   - Units: bohr and hartree.  K is the bare exchange matrix: no -c_x factor
+ *     and no closed-shell factor (P is used as given).
+ *   - Basis functions are contracted Cartesian Gaussians, l = 0, 1, 2.  Order:
+ *     shells in input order; inside a shell the Cartesian components in
+ *     lexicographic order (l,0,0), (l-1,1,0), (l-1,0,1), (l-2,2,0), ...,
+ *     i.e. x y z for p and xx xy xz yy yz zz for d.  Each component is
+ *     normalised to unit self-overlap; the caller's contraction coefficients
+ *     refer to x^l-normalised primitives.
+ *   - Matrices are N_b x N_b, row-major, double precision.
+ *
+ * Ownership: every input is copied during the call that receives it; the
+ * caller keeps ownership of all pointers it passes.  Device pointers must be
+ * allocations on the device that was current at snk_create.
+ *
+ * Errors: every call returns SNK_OK (0) or a negative snk_status.  After an
+ * error the handle stays valid for snk_last_error and snk_destroy; a build
+ * that failed leaves the output untouched or partially written.  A handle is
+ * not re-entrant: calls on one handle must not overlap.  No call aborts the
+ * process.
+ */
+#ifndef SNK_H
+#define SNK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SNK_OK = 0,
+  SNK_ERR_INVALID_ARG = -1,   /* NULL pointer, negative size, bad index      */
+  SNK_ERR_UNSUPPORTED = -2,   /* l > 2, non-finite or non-positive input     */
+  SNK_ERR_NOT_SYMMETRIC = -3, /* max|P - P^T| > 1e-12 max|P|                 */
+  SNK_ERR_BAD_STATE = -4,     /* build before set_density, ...               */
+  SNK_ERR_OOM = -5,           /* device or host allocation failed            */
+  SNK_ERR_CUDA = -6,          /* a CUDA runtime call failed                  */
+  SNK_ERR_TIMEOUT = -7        /* a bounded device wait ran out               */
+} snk_status;
+
+typedef struct snk_ctx snk_ctx; /* opaque handle */
+
+/* Contracted Cartesian basis.  All arrays are host memory, copied at create. */
+typedef struct {
+  int32_t n_shells;
+  const int32_t *l;      /* [n_shells], 0..2, else SNK_ERR_UNSUPPORTED       */
+  const int32_t *nprim;  /* [n_shells], 1..16 primitives per shell            */
+  const int32_t *atom;   /* [n_shells], owning atom (informational)           */
+  const double *center;  /* [3 n_shells], bohr                                */
+  const double *exps;    /* [sum nprim], > 0, shell after shell               */
+  const double *coefs;   /* [sum nprim], w.r.t. x^l-normalised primitives     */
+} snk_basis;
+
+/* Quadrature grid (Sec. II.C): nodes, weights (atomic quadrature x partition
+ * weight) and the atom each node belongs to (used for atom-centred batching). */
+typedef struct {
+  int64_t n_points;      /* >= 0                                              */
+  const double *xyz;     /* [3 n_points], bohr                                */
+  const double *w;       /* [n_points]                                        */
+  const int32_t *atom;   /* [n_points], >= 0                                  */
+} snk_grid;
+
+typedef enum { SNK_PREC_FP64 = 0, SNK_PREC_MIXED = 1 } snk_precision;
+typedef enum { SNK_SCREEN_NONE = 0, SNK_SCREEN_LINK = 1, SNK_SCREEN_LEARNED = 2 } snk_screen_mode;
+
+typedef struct {
+  double eps_basis;        /* epsilon_B of Eq. (basis_screen); <= 0 keeps all   */
+  double eps_E;            /* epsilon_E of Eq. (sp_set)                          */
+  double eps_K;            /* epsilon_K of Eq. (sp_set)                          */
+  int32_t batch_max;       /* largest grid batch (octree leaf), Sec. III: 4096  */
+  int32_t precision;       /* snk_precision                                      */
+  int32_t screen;          /* snk_screen_mode                                    */
+  int32_t reserved0;
+  double fp32_bound;       /* mixed form: pairs whose bound is below go FP32     */
+  int64_t workspace_bytes; /* device workspace cap for batch chunks (Alg. 1); 0 = auto */
+  double reserved[8];
+} snk_options;
+
+/* Per-build counters and phase times (CUDA events on the library stream). */
+typedef struct {
+  int64_t n_points, n_batches, n_shells, n_functions, n_pairs;
+  int64_t pairs_kept;          /* sum_j |V_j| (shell pairs)                         */
+  int64_t pair_points;         /* sum_j |V_j| |Q_j|                                 */
+  double integrals;            /* sum_j sum_{(a,b) in V_j} |Q_j| n_a n_b            */
+  double integral_flops;       /* algorithmic FP64 flops of the integral kernel     */
+  double gemm_flops;           /* flops of F = X P and Kt = G^T X                    */
+  int64_t n_chunks;            /* batch chunks of the last build (Alg. 1)           */
+  int64_t workspace_bytes;     /* device workspace held                              */
+  int64_t kernel_launches;     /* kernels launched by the last set_density + build  */
+  double ms_screen;            /* last set_density: upload, F-tilde, pair screen    */
+  double ms_collocation, ms_fgemm, ms_integrals, ms_kgemm, ms_finish; /* last build  */
+  double ms_build;             /* last build, first to last event                   */
+  double ms_integrals_class[6];/* per class ss ps pp ds dp dd                        */
+  double integrals_class[6];
+  double flops_class[6];
+} snk_stats;
+
+/* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,
+ * batch_max = 4096, FP64, sn-LinK screen, fp32_bound = 1e-6, workspace auto. */
+void snk_options_default(snk_options *opt);
+
+/* Geometry setup (not density dependent): normalisation, shell pairs with
+ * their rigorous integral bounds, octree batches (Sec. II.E), basis screen
+ * B_j (Eq. basis_screen) and the batch maxima Phi-tilde, phi-tilde of
+ * Eq. (exx_fmat_approx).  opt may be NULL for the defaults. */
+int snk_create(const snk_basis *basis, const snk_grid *grid, const snk_options *opt,
+               snk_ctx **out);
+
+/* Load a density matrix (N_b x N_b, row-major, symmetric to 1e-12 relative)
+ * and run the density-dependent sn-LinK screen: F-tilde (Eq. exx_fmat_approx)
+ * and the pair lists V_j (Eq. sp_set).  P is a host pointer. */
+int snk_set_density(snk_ctx *ctx, const double *P);
+/* Same with P in device memory. */
+int snk_set_density_device(snk_ctx *ctx, const double *dP);
+
+/* Build K for the loaded density (Alg. 1 on one GPU).  K is host memory,
+ * N_b x N_b row-major; the call returns when K is written. */
+int snk_build_K(snk_ctx *ctx, double *K);
+/* Same, writing into device memory; returns once the work is enqueued on the
+ * library stream (synchronise that stream before reading dK). */
+int snk_build_K_device(snk_ctx *ctx, double *dK);
+
+/* Stream for all later work on this handle (a cudaStream_t; NULL = the legacy
+ * default stream). */
+int snk_set_stream(snk_ctx *ctx, void *stream);
+
+int snk_get_stats(const snk_ctx *ctx, snk_stats *stats);
+int64_t snk_n_functions(const snk_ctx *ctx);
+const char *snk_last_error(const snk_ctx *ctx);
+const char *snk_status_string(int status);
+void snk_destroy(snk_ctx *ctx);
+
+/* ---- test exports: expose intermediate steps for unit parity ------------- */
+
+/* Device Boys function F_0..F_nmax (Eq. boys) at n host values T (host arrays;
+ * out is n x (nmax+1)).  nmax <= 4. */
+int snk_debug_boys(int64_t n, const double *T, int nmax, double *out);
+
+/* Device 3c-CP integrals A_{mu lam}(r) (Eq. 3c_grid, normalised functions) of
+ * shells sa, sb at n host points; out is n x ncart(l_sa) x ncart(l_sb). */
+int snk_debug_shell_A(snk_ctx *ctx, int32_t sa, int32_t sb, int64_t n, const double *xyz,
+                      double *out);
+
+/* Host-side rigorous bound of max_r |A_{mu lam}(r)| over the shell pair
+ * (sa, sb) (the A-tilde of Eq. exx_fmat_approx). */
+int snk_debug_pair_bound(snk_ctx *ctx, int32_t sa, int32_t sb, double *bound);
+
+/* Octree batches: n_batches, then for each batch the point count; the
+ * permutation from batch order to input order (n_points entries). */
+int snk_debug_batches(snk_ctx *ctx, int64_t *n_batches, int32_t *counts, int64_t counts_cap,
+                      int64_t *perm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNK_H */

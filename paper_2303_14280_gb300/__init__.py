@@ -1,0 +1,263 @@
+"""Python binding of libsnk, the GB300 sn-K exact-exchange build.
+
+Argument marshalling only: every step of the build runs in the CUDA kernels of
+``libsnk.so`` behind the C ABI of ``include/snk.h``.  There is no CPU fallback:
+if the library is missing or no GPU is present the calls raise.
+
+    eng = Engine(basis, grid)          # snk_create
+    eng.set_density(P)                 # snk_set_density (NumPy) / _device (torch CUDA tensor)
+    K = eng.build_K()                  # snk_build_K -> NumPy, or build_K(out=cuda_tensor)
+
+``basis`` needs the attributes l, nprim, atom, center, exps, coefs and
+``grid`` the attributes xyz, w, atom (NumPy arrays), as produced by the
+``synth`` generators.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Engine", "SnkError", "lib", "options", "debug_boys", "SYMBOLS"]
+
+_lib = None
+_lock = threading.Lock()
+
+SNK_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported input", -3: "density matrix not symmetric",
+          -4: "bad call order", -5: "out of memory", -6: "CUDA error", -7: "device wait timed out"}
+SCREEN = {"none": 0, "link": 1, "learned": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+# every entry point declared in include/snk.h
+SYMBOLS = ["snk_options_default", "snk_create", "snk_set_density", "snk_set_density_device", "snk_build_K",
+           "snk_build_K_device", "snk_set_stream", "snk_get_stats", "snk_n_functions", "snk_last_error",
+           "snk_status_string", "snk_destroy", "snk_debug_boys", "snk_debug_shell_A", "snk_debug_pair_bound",
+           "snk_debug_batches"]
+
+
+class SnkError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"libsnk: {STATUS.get(status, status)}" + (f": {msg}" if msg else ""))
+
+
+class SnkBasis(ctypes.Structure):
+    _fields_ = [("n_shells", ctypes.c_int32), ("l", ctypes.POINTER(ctypes.c_int32)),
+                ("nprim", ctypes.POINTER(ctypes.c_int32)), ("atom", ctypes.POINTER(ctypes.c_int32)),
+                ("center", ctypes.POINTER(ctypes.c_double)), ("exps", ctypes.POINTER(ctypes.c_double)),
+                ("coefs", ctypes.POINTER(ctypes.c_double))]
+
+
+class SnkGrid(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("w", ctypes.POINTER(ctypes.c_double)), ("atom", ctypes.POINTER(ctypes.c_int32))]
+
+
+class SnkOptions(ctypes.Structure):
+    _fields_ = [("eps_basis", ctypes.c_double), ("eps_E", ctypes.c_double), ("eps_K", ctypes.c_double),
+                ("batch_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_int64), ("reserved", ctypes.c_double * 8)]
+
+
+class SnkStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_points", "n_batches", "n_shells", "n_functions", "n_pairs",
+                                               "pairs_kept", "pair_points")] + \
+               [("integrals", ctypes.c_double), ("integral_flops", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("n_chunks", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)] + \
+               [(n, ctypes.c_double) for n in ("ms_screen", "ms_collocation", "ms_fgemm", "ms_integrals", "ms_kgemm",
+                                                "ms_finish", "ms_build")] + \
+               [("ms_integrals_class", ctypes.c_double * 6), ("integrals_class", ctypes.c_double * 6),
+                ("flops_class", ctypes.c_double * 6)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_P = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsnk.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise SnkError(-6, f"{path} is missing; run paper_2303_14280_gb300.build.build()")
+            L = ctypes.CDLL(path)
+            L.snk_options_default.argtypes = [ctypes.POINTER(SnkOptions)]
+            L.snk_options_default.restype = None
+            L.snk_create.argtypes = [ctypes.POINTER(SnkBasis), ctypes.POINTER(SnkGrid), ctypes.POINTER(SnkOptions),
+                                     ctypes.POINTER(_P)]
+            for name in ("snk_set_density", "snk_set_density_device", "snk_build_K", "snk_build_K_device"):
+                getattr(L, name).argtypes = [_P, _P]
+            L.snk_set_stream.argtypes = [_P, _P]
+            L.snk_get_stats.argtypes = [_P, ctypes.POINTER(SnkStats)]
+            L.snk_n_functions.argtypes = [_P]
+            L.snk_n_functions.restype = ctypes.c_int64
+            L.snk_last_error.argtypes = [_P]
+            L.snk_last_error.restype = ctypes.c_char_p
+            L.snk_status_string.argtypes = [ctypes.c_int]
+            L.snk_status_string.restype = ctypes.c_char_p
+            L.snk_destroy.argtypes = [_P]
+            L.snk_destroy.restype = None
+            L.snk_debug_boys.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
+            L.snk_debug_shell_A.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D]
+            L.snk_debug_pair_bound.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _D]
+            L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+            _lib = L
+    return _lib
+
+
+def options(**kw) -> SnkOptions:
+    o = SnkOptions()
+    lib().snk_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "screen" and isinstance(v, str):
+            v = SCREEN[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "eps":
+            o.eps_basis = o.eps_E = o.eps_K = float(v)
+            continue
+        setattr(o, k, v)
+    return o
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def debug_boys(T, nmax: int) -> np.ndarray:
+    """Device Boys function F_0..F_nmax at the given T (test export)."""
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+    out = np.zeros((T.shape[0], nmax + 1))
+    rc = lib().snk_debug_boys(T.shape[0], _dptr(T), nmax, _dptr(out))
+    if rc != SNK_OK:
+        raise SnkError(rc)
+    return out
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Engine:
+    """One sn-K problem (basis + grid) on the current CUDA device."""
+
+    def __init__(self, basis, grid, **opts):
+        L = lib()
+        self._keep = []
+        l = np.ascontiguousarray(basis.l, dtype=np.int32)
+        nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
+        atom = np.ascontiguousarray(basis.atom, dtype=np.int32)
+        center = np.ascontiguousarray(basis.center, dtype=np.float64)
+        exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
+        coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+        gxyz = np.ascontiguousarray(grid.xyz, dtype=np.float64)
+        gw = np.ascontiguousarray(grid.w, dtype=np.float64)
+        gatom = np.ascontiguousarray(grid.atom, dtype=np.int32)
+        i32 = ctypes.POINTER(ctypes.c_int32)
+        b = SnkBasis(int(l.shape[0]), l.ctypes.data_as(i32), nprim.ctypes.data_as(i32), atom.ctypes.data_as(i32),
+                     _dptr(center), _dptr(exps), _dptr(coefs))
+        g = SnkGrid(int(gw.shape[0]), _dptr(gxyz), _dptr(gw), gatom.ctypes.data_as(i32))
+        self.opts = options(**opts)
+        h = _P()
+        rc = L.snk_create(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(h))
+        if rc != SNK_OK:
+            raise SnkError(rc, "snk_create")
+        self._h = h
+        self._l = l
+        self.nf = int(L.snk_n_functions(h))
+        self._stream = None
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != SNK_OK:
+            msg = lib().snk_last_error(self._h).decode()
+            raise SnkError(rc, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().snk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """Use a torch.cuda.Stream (or a raw cudaStream_t int) for all work."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        self._stream = stream
+        self._check(lib().snk_set_stream(self._h, _P(int(ptr) if ptr else None)), "snk_set_stream")
+
+    # -- the sn-K build ---------------------------------------------------
+    def set_density(self, P):
+        """P: NumPy (host) array or torch CUDA tensor, N_b x N_b float64, symmetric."""
+        if _is_cuda_tensor(P):
+            assert P.dtype.is_floating_point and P.element_size() == 8 and P.is_contiguous()
+            assert tuple(P.shape) == (self.nf, self.nf)
+            self._check(lib().snk_set_density_device(self._h, _P(P.data_ptr())), "snk_set_density_device")
+        else:
+            Pn = np.ascontiguousarray(P, dtype=np.float64)
+            assert Pn.shape == (self.nf, self.nf)
+            self._check(lib().snk_set_density(self._h, _P(Pn.ctypes.data)), "snk_set_density")
+
+    def build_K(self, out=None):
+        """Host K (NumPy) by default; with out = a CUDA tensor the build writes there
+        and returns it once the work is enqueued on the engine's stream."""
+        if out is not None and _is_cuda_tensor(out):
+            assert out.element_size() == 8 and out.is_contiguous() and tuple(out.shape) == (self.nf, self.nf)
+            self._check(lib().snk_build_K_device(self._h, _P(out.data_ptr())), "snk_build_K_device")
+            return out
+        K = out if out is not None else np.empty((self.nf, self.nf))
+        assert K.dtype == np.float64 and K.flags.c_contiguous and K.shape == (self.nf, self.nf)
+        self._check(lib().snk_build_K(self._h, _P(K.ctypes.data)), "snk_build_K")
+        return K
+
+    def stats(self) -> dict:
+        s = SnkStats()
+        self._check(lib().snk_get_stats(self._h, ctypes.byref(s)), "snk_get_stats")
+        out = {}
+        for name, _ in SnkStats._fields_:
+            v = getattr(s, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+    # -- test exports -----------------------------------------------------
+    def debug_shell_A(self, sa, sb, xyz):
+        """Device 3c-CP block A_{mu lam}(r) of shells sa, sb at the points: (n, n_a, n_b)."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        na = (int(self._l[sa]) + 1) * (int(self._l[sa]) + 2) // 2
+        nb = (int(self._l[sb]) + 1) * (int(self._l[sb]) + 2) // 2
+        out = np.zeros((xyz.shape[0], na, nb))
+        self._check(lib().snk_debug_shell_A(self._h, int(sa), int(sb), xyz.shape[0], _dptr(xyz), _dptr(out)),
+                    "snk_debug_shell_A")
+        return out
+
+    def debug_pair_bound(self, sa, sb) -> float:
+        v = ctypes.c_double()
+        self._check(lib().snk_debug_pair_bound(self._h, int(sa), int(sb), ctypes.byref(v)), "snk_debug_pair_bound")
+        return v.value
+
+    def debug_batches(self):
+        n = ctypes.c_int64()
+        self._check(lib().snk_debug_batches(self._h, ctypes.byref(n), None, 0, None), "snk_debug_batches")
+        counts = np.zeros(max(n.value, 1), dtype=np.int32)
+        perm = np.zeros(int(self.stats()["n_points"]), dtype=np.int64)
+        self._check(lib().snk_debug_batches(self._h, ctypes.byref(n), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            counts.shape[0], perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+                    "snk_debug_batches")
+        return counts[:n.value], perm

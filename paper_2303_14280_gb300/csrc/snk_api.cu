@@ -1,0 +1,735 @@
+// C ABI of libsnk (include/snk.h): handle management, the density-dependent
+// screen and the K build driver (Alg. 1 of the paper on one GPU: batches are
+// processed in chunks whose intermediates X, F, G fit a preallocated device
+// workspace; every chunk adds its contribution to one K-tilde accumulator).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "snk_internal.h"
+
+using namespace snk;
+
+namespace {
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t ensure(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * std::max<size_t>(count, 1));
+    if (e == cudaSuccess) n = count;
+    return e;
+  }
+};
+
+// pairs per integral tile for each class: cheap classes take longer runs
+constexpr int kPairsPerTile[kNumClasses] = {64, 32, 16, 16, 8, 8};
+constexpr int kPhaseEvents = 3 + kNumClasses;  // per chunk: collocation, F GEMM, classes, K GEMM
+
+}  // namespace
+
+struct snk_ctx {
+  Setup s;
+  snk_options opt;
+  int device = 0, num_sms = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int nbatch = 0;
+  int64_t ws_budget = 0;
+
+  // geometry (device)
+  DevBuf<int> l, poff, nprim, foff, fshell, bshell, bshell_col, xfunc;
+  DevBuf<double> center, exps, d, fcomp, xyz, w, boys, bound, phit_f, phit_b;
+  DevBuf<PairHdr> pairs;
+  DevBuf<PrimPair> prims;
+
+  // density-dependent state
+  bool have_density = false;
+  DevBuf<double> P, ft, sym, Khat, K;
+  DevBuf<int> counts, list, sfunc, colmap, tickets;
+  DevBuf<unsigned char> sflag;
+  DevBuf<int64_t> list_off;
+  DevBuf<BatchDesc> batch;
+  DevBuf<Tile> tiles;
+  DevBuf<double> ws;
+  std::vector<int> hcounts;
+  std::vector<int64_t> hlist_off;
+
+  struct Chunk {
+    int b0 = 0, b1 = 0;
+    int64_t bytes = 0, goff = 0, gbytes = 0;
+    int max_ldq = 0, max_nS = 0, max_nB = 0, max_nBshell = 0;
+    int64_t tile_off[kNumClasses] = {0}, tile_n[kNumClasses] = {0};
+  };
+  std::vector<Chunk> chunks;
+  int max_ctas[kNumClasses] = {0};
+
+  // timing
+  std::vector<cudaEvent_t> events;
+  cudaEvent_t ev_screen0 = nullptr, ev_screen1 = nullptr;
+  int64_t launches_density = 0, launches_build = 0;
+  bool built = false;
+  snk_stats st;
+
+  ~snk_ctx() {
+    for (auto e : events) cudaEventDestroy(e);
+    if (ev_screen0) cudaEventDestroy(ev_screen0);
+    if (ev_screen1) cudaEventDestroy(ev_screen1);
+  }
+};
+
+namespace {
+
+int fail(snk_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(snk_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? SNK_ERR_OOM : SNK_ERR_CUDA, m);
+}
+
+#define SNK_CK(ctx, call)                                  \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t upload(DevBuf<T>& b, const std::vector<T>& h, cudaStream_t st) {
+  cudaError_t e = b.ensure(h.size());
+  if (e != cudaSuccess || h.empty()) return e;
+  return cudaMemcpyAsync(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st);
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+DeviceBasis dev_basis(snk_ctx* c) {
+  DeviceBasis b;
+  b.l = c->l.p;
+  b.poff = c->poff.p;
+  b.nprim = c->nprim.p;
+  b.center = c->center.p;
+  b.exps = c->exps.p;
+  b.d = c->d.p;
+  b.fcomp = c->fcomp.p;
+  b.foff = c->foff.p;
+  return b;
+}
+
+// Geometry-only screen maxima Phi-tilde and phi-tilde (Eq. exx_fmat_approx):
+// collocate the batches chunk by chunk and reduce.
+int geometry_screen(snk_ctx* c) {
+  Setup& s = c->s;
+  const int nb = c->nbatch;
+  SNK_CK(c, c->phit_f.ensure((size_t)std::max(nb, 1) * s.nf));
+  SNK_CK(c, c->phit_b.ensure(std::max(nb, 1)));
+  SNK_CK(c, cudaMemsetAsync(c->phit_f.p, 0, sizeof(double) * (size_t)std::max(nb, 1) * s.nf, c->stream));
+  SNK_CK(c, cudaMemsetAsync(c->phit_b.p, 0, sizeof(double) * std::max(nb, 1), c->stream));
+  if (nb == 0) return SNK_OK;
+  std::vector<BatchDesc> bd(nb);
+  int j = 0;
+  while (j < nb) {
+    int64_t off = 0;
+    int j0 = j, max_ldq = 0, max_nBs = 0, max_nB = 0;
+    while (j < nb) {
+      BatchDesc b{};
+      b.p0 = s.bstart[j];
+      b.q = (int)(s.bstart[j + 1] - s.bstart[j]);
+      b.ldq = (int)round_up(std::max(b.q, 1), kLdqAlign);
+      b.nB = s.bnf[j];
+      b.nS = 0;
+      b.xfunc_off = s.xfunc_off[j];
+      b.bshell_off = s.bshell_off[j];
+      b.nBshell = s.bshell_off[j + 1] - s.bshell_off[j];
+      int64_t bytes = (int64_t)b.ldq * b.nB * 8;
+      if (j > j0 && (off + bytes) * 1 > c->ws_budget) break;
+      b.xoff = off;
+      off += (int64_t)b.ldq * b.nB;
+      bd[j] = b;
+      max_ldq = std::max(max_ldq, b.ldq);
+      max_nBs = std::max(max_nBs, b.nBshell);
+      max_nB = std::max(max_nB, b.nB);
+      ++j;
+    }
+    SNK_CK(c, c->ws.ensure((size_t)std::max<int64_t>(off, 1)));
+    SNK_CK(c, c->batch.ensure(nb));
+    SNK_CK(c, cudaMemcpyAsync(c->batch.p + j0, bd.data() + j0, sizeof(BatchDesc) * (j - j0), cudaMemcpyHostToDevice,
+                              c->stream));
+    SNK_CK(c, launch_collocation(c->stream, c->batch.p + j0, j - j0, max_ldq, max_nBs, c->bshell.p, c->bshell_col.p,
+                                 c->xyz.p, dev_basis(c), c->ws.p));
+    // the phit kernels index phit_f / phit_b by blockIdx relative to batch j0
+    SNK_CK(c, launch_screen_geom(c->stream, c->batch.p + j0, j - j0, max_nB, c->ws.p, c->w.p, c->xfunc.p, s.nf,
+                                 c->phit_f.p + (size_t)j0 * s.nf, c->phit_b.p + j0));
+    SNK_CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return SNK_OK;
+}
+
+int ensure_events(snk_ctx* c, size_t n) {
+  while (c->events.size() < n) {
+    cudaEvent_t e;
+    SNK_CK(c, cudaEventCreate(&e));
+    c->events.push_back(e);
+  }
+  return SNK_OK;
+}
+
+// Density-dependent part of set_density once P is on the device.
+int screen_and_plan(snk_ctx* c) {
+  Setup& s = c->s;
+  const int nb = c->nbatch, ns = s.ns, nf = s.nf;
+  const cudaStream_t st = c->stream;
+  c->have_density = false;
+  c->launches_density = 0;
+  SNK_CK(c, cudaEventRecord(c->ev_screen0, st));
+  // symmetry check
+  SNK_CK(c, c->sym.ensure(2));
+  SNK_CK(c, cudaMemsetAsync(c->sym.p, 0, 2 * sizeof(double), st));
+  SNK_CK(c, launch_symcheck(st, c->P.p, nf, c->sym.p));
+  ++c->launches_density;
+  double hsym[2];
+  SNK_CK(c, cudaMemcpyAsync(hsym, c->sym.p, sizeof(hsym), cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaStreamSynchronize(st));
+  if (!(hsym[0] <= 1e-12 * hsym[1]))
+    return fail(c, std::isfinite(hsym[0]) ? SNK_ERR_NOT_SYMMETRIC : SNK_ERR_UNSUPPORTED,
+                "density matrix is not symmetric (or not finite)");
+  const int nbx = std::max(nb, 1);
+  // F-tilde and the pair screen, Eqs. (exx_fmat_approx), (sp_set)
+  SNK_CK(c, c->ft.ensure((size_t)nbx * ns));
+  SNK_CK(c, c->counts.ensure((size_t)nbx * kNumClasses));
+  SNK_CK(c, c->sflag.ensure((size_t)nbx * ns));
+  SNK_CK(c, cudaMemsetAsync(c->ft.p, 0, sizeof(double) * nbx * ns, st));
+  SNK_CK(c, cudaMemsetAsync(c->sflag.p, 0, (size_t)nbx * ns, st));
+  const int screen = c->opt.screen == SNK_SCREEN_NONE ? SNK_SCREEN_NONE : SNK_SCREEN_LINK;
+  if (screen != SNK_SCREEN_NONE) {
+    SNK_CK(c, launch_ftilde(st, c->P.p, c->phit_f.p, nf, nb, c->fshell.p, ns, c->ft.p));
+    ++c->launches_density;
+  }
+  SNK_CK(c, launch_pair_count(st, c->pairs.p, c->bound.p, s.class_begin, c->ft.p, c->phit_b.p, ns, nb, c->opt.eps_E,
+                              c->opt.eps_K, screen, c->counts.p, c->sflag.p));
+  ++c->launches_density;
+  c->hcounts.assign((size_t)nbx * kNumClasses, 0);
+  std::vector<unsigned char> hflag((size_t)nbx * ns);
+  SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumClasses, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(hflag.data(), c->sflag.p, (size_t)nbx * ns, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaStreamSynchronize(st));
+
+  // pair lists: offsets, then the deterministic compaction pass
+  c->hlist_off.assign((size_t)nbx * kNumClasses + 1, 0);
+  int64_t tot = 0;
+  for (int j = 0; j < nb; ++j)
+    for (int k = 0; k < kNumClasses; ++k) {
+      c->hlist_off[(size_t)j * kNumClasses + k] = tot;
+      tot += c->hcounts[(size_t)j * kNumClasses + k];
+    }
+  c->hlist_off[(size_t)nb * kNumClasses] = tot;
+  if (tot > (int64_t)0x7fffffff)
+    return fail(c, SNK_ERR_UNSUPPORTED, "more than 2^31 screened (batch, pair) entries: tighten the screen");
+  SNK_CK(c, c->list.ensure((size_t)std::max<int64_t>(tot, 1)));
+  SNK_CK(c, upload(c->list_off, c->hlist_off, st));
+  SNK_CK(c, launch_pair_write(st, c->pairs.p, c->bound.p, s.class_begin, c->ft.p, c->phit_b.p, ns, nb, c->opt.eps_E,
+                              c->opt.eps_K, screen, c->list_off.p, c->list.p));
+  ++c->launches_density;
+
+  // shells of V_j -> F / G columns; batch descriptors; chunks (Alg. 1)
+  std::vector<int> hcolmap((size_t)nbx * ns, -1), hsfunc;
+  std::vector<BatchDesc> bd(nbx);
+  c->chunks.clear();
+  int64_t pair_points = 0, kept = 0;
+  double integrals = 0.0, iflops = 0.0, gflops = 0.0;
+  double icls[kNumClasses] = {0}, fcls[kNumClasses] = {0};
+  for (int j = 0; j < nb; ++j) {
+    BatchDesc& b = bd[j];
+    b = BatchDesc{};
+    b.p0 = s.bstart[j];
+    b.q = (int)(s.bstart[j + 1] - s.bstart[j]);
+    b.ldq = (int)round_up(std::max(b.q, 1), kLdqAlign);
+    b.nB = s.bnf[j];
+    b.xfunc_off = s.xfunc_off[j];
+    b.bshell_off = s.bshell_off[j];
+    b.nBshell = s.bshell_off[j + 1] - s.bshell_off[j];
+    b.sfunc_off = (int)hsfunc.size();
+    int col = 0;
+    for (int a = 0; a < ns; ++a)
+      if (hflag[(size_t)j * ns + a]) {
+        hcolmap[(size_t)j * ns + a] = col;
+        for (int u = 0; u < ncart(s.l[a]); ++u) hsfunc.push_back(s.foff[a] + u);
+        col += ncart(s.l[a]);
+      }
+    b.nS = col;
+    for (int k = 0; k < kNumClasses; ++k) {
+      int64_t n = c->hcounts[(size_t)j * kNumClasses + k];
+      kept += n;
+      pair_points += n * b.q;
+    }
+    gflops += 2.0 * b.q * (double)b.nB * b.nS * 2.0;
+  }
+  // integral counts and algorithmic flops: walk the kept pairs per class
+  // (counts only: the lists stay on the device; all pairs of a class share nprim
+  // in practice, otherwise the class's mean primitive-pair count is used)
+  for (int k = 0; k < kNumClasses; ++k) {
+    int la = 0, lb = 0;
+    for (int x = 0; x <= 2; ++x)
+      for (int y = 0; y <= x; ++y)
+        if (class_of(x, y) == k) {
+          la = x;
+          lb = y;
+        }
+    double npp = 0.0;
+    int cnt = s.class_begin[k + 1] - s.class_begin[k];
+    for (int p = s.class_begin[k]; p < s.class_begin[k + 1]; ++p) npp += s.pairs[p].pp_n;
+    double mean_np = cnt ? npp / cnt : 1.0;
+    double f;
+    class_flops(k, (int)std::lround(mean_np), &f);
+    for (int j = 0; j < nb; ++j) {
+      double pp = (double)c->hcounts[(size_t)j * kNumClasses + k] * bd[j].q;
+      icls[k] += pp * ncart(la) * ncart(lb);
+      fcls[k] += pp * f;
+    }
+    integrals += icls[k];
+    iflops += fcls[k];
+  }
+  SNK_CK(c, upload(c->colmap, hcolmap, st));
+  if (hsfunc.empty()) hsfunc.push_back(0);
+  SNK_CK(c, upload(c->sfunc, hsfunc, st));
+
+  // chunks under the workspace budget
+  int j = 0;
+  while (j < nb) {
+    snk_ctx::Chunk ch;
+    ch.b0 = j;
+    int64_t xo = 0, fo = 0;
+    std::vector<int> members;
+    while (j < nb) {
+      int64_t xs = (int64_t)bd[j].ldq * bd[j].nB, fs = (int64_t)bd[j].ldq * bd[j].nS;
+      if (j > ch.b0 && (xo + xs + 2 * (fo + fs)) * 8 > c->ws_budget) break;
+      xo += xs;
+      fo += fs;
+      ++j;
+    }
+    ch.b1 = j;
+    int64_t xcur = 0, fcur = xo, gcur = xo + fo;
+    ch.goff = gcur;
+    ch.gbytes = fo * 8;
+    for (int t = ch.b0; t < ch.b1; ++t) {
+      bd[t].xoff = xcur;
+      xcur += (int64_t)bd[t].ldq * bd[t].nB;
+      bd[t].foff = fcur;
+      bd[t].goff = gcur;
+      fcur += (int64_t)bd[t].ldq * bd[t].nS;
+      gcur += (int64_t)bd[t].ldq * bd[t].nS;
+      ch.max_ldq = std::max(ch.max_ldq, bd[t].ldq);
+      ch.max_nS = std::max(ch.max_nS, bd[t].nS);
+      ch.max_nB = std::max(ch.max_nB, bd[t].nB);
+      ch.max_nBshell = std::max(ch.max_nBshell, bd[t].nBshell);
+    }
+    ch.bytes = (xo + 2 * fo) * 8;
+    c->chunks.push_back(ch);
+  }
+  int64_t need = 1;
+  for (auto& ch : c->chunks) need = std::max(need, ch.bytes / 8);
+  SNK_CK(c, c->ws.ensure((size_t)need));
+  SNK_CK(c, upload(c->batch, bd, st));
+
+  // integral tiles per (chunk, class): (batch, pair run, 128-point slab),
+  // larger runs first so that the persistent CTAs finish together
+  std::vector<Tile> htiles;
+  for (auto& ch : c->chunks)
+    for (int k = 0; k < kNumClasses; ++k) {
+      ch.tile_off[k] = (int64_t)htiles.size();
+      size_t first = htiles.size();
+      for (int t = ch.b0; t < ch.b1; ++t) {
+        int64_t n = c->hcounts[(size_t)t * kNumClasses + k];
+        int64_t base = c->hlist_off[(size_t)t * kNumClasses + k];
+        for (int64_t k0 = 0; k0 < n; k0 += kPairsPerTile[k])
+          for (int i0 = 0; i0 < bd[t].q; i0 += kPointTile) {
+            Tile tl;
+            tl.batch = t;
+            tl.k0 = (int)(base + k0);
+            tl.k1 = (int)(base + std::min<int64_t>(n, k0 + kPairsPerTile[k]));
+            tl.i0 = i0;
+            htiles.push_back(tl);
+          }
+      }
+      std::stable_sort(htiles.begin() + first, htiles.end(), [&](const Tile& x, const Tile& y) {
+        int64_t cx = (int64_t)(x.k1 - x.k0) * std::min(kPointTile, bd[x.batch].q - x.i0);
+        int64_t cy = (int64_t)(y.k1 - y.k0) * std::min(kPointTile, bd[y.batch].q - y.i0);
+        return cx > cy;
+      });
+      ch.tile_n[k] = (int64_t)htiles.size() - ch.tile_off[k];
+    }
+  if (htiles.empty()) htiles.push_back(Tile{0, 0, 0, 0});
+  SNK_CK(c, upload(c->tiles, htiles, st));
+  SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumClasses + 1));
+  SNK_CK(c, c->Khat.ensure((size_t)nf * nf));
+  SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
+  SNK_CK(c, cudaStreamSynchronize(st));
+
+  c->st.n_batches = nb;
+  c->st.pairs_kept = kept;
+  c->st.pair_points = pair_points;
+  c->st.integrals = integrals;
+  c->st.integral_flops = iflops;
+  c->st.gemm_flops = gflops;
+  for (int k = 0; k < kNumClasses; ++k) {
+    c->st.integrals_class[k] = icls[k];
+    c->st.flops_class[k] = fcls[k];
+  }
+  c->st.n_chunks = (int64_t)c->chunks.size();
+  c->st.workspace_bytes = (int64_t)(c->ws.n * 8);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev_screen0, c->ev_screen1);
+  c->st.ms_screen = ms;
+  c->have_density = true;
+  c->built = false;
+  return SNK_OK;
+}
+
+int build(snk_ctx* c, double* dK) {
+  if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_build_K called before snk_set_density");
+  Setup& s = c->s;
+  const cudaStream_t st = c->stream;
+  const int nf = s.nf;
+  const size_t nev = c->chunks.size() * kPhaseEvents + 2;
+  if (int rc = ensure_events(c, nev)) return rc;
+  c->launches_build = 0;
+  int ev = 0;
+  SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)nf * nf, st));
+  SNK_CK(c, cudaMemsetAsync(c->tickets.p, 0, sizeof(int) * c->tickets.n, st));
+  for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
+    const auto& ch = c->chunks[ci];
+    const int nbc = ch.b1 - ch.b0;
+    const BatchDesc* db = c->batch.p + ch.b0;
+    // X_j, Eq. (collocation)
+    SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
+                                 dev_basis(c), c->ws.p));
+    ++c->launches_build;
+    SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    // F_j = X_j P (w and component factors folded in), Eq. (batch_local_exx)
+    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nf, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
+                           c->ws.p));
+    ++c->launches_build;
+    SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
+    SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, class by class
+    for (int k = 0; k < kNumClasses; ++k) {
+      IntegralArgs a;
+      a.tiles = c->tiles.p + ch.tile_off[k];
+      a.n_tiles = (int)ch.tile_n[k];
+      a.ticket = c->tickets.p + ci * kNumClasses + k;
+      a.batches = c->batch.p;
+      a.pairlist = c->list.p;
+      a.pairs = c->pairs.p;
+      a.prims = c->prims.p;
+      a.colmap = c->colmap.p;
+      a.ns = s.ns;
+      a.xyz = c->xyz.p;
+      a.boys = c->boys.p;
+      a.ws = c->ws.p;
+      if (a.n_tiles > 0) {
+        int grid = std::min<int64_t>(c->max_ctas[k], a.n_tiles);
+        SNK_CK(c, launch_integrals(st, k, a, grid));
+        ++c->launches_build;
+      }
+      SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    }
+    // Kt += G_j^T X_j, Eq. (usym_k)
+    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, nf, c->ws.p, c->Khat.p));
+    ++c->launches_build;
+    SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  }
+  // K = (Kt + Kt^T) / 2, Eq. (sn_k)
+  SNK_CK(c, launch_finish(st, c->Khat.p, c->fcomp.p, nf, dK));
+  ++c->launches_build;
+  SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  c->built = true;
+  return SNK_OK;
+}
+
+void collect_times(snk_ctx* c) {
+  if (!c->built) return;
+  const int last = (int)c->chunks.size() * kPhaseEvents + 1;  // the event after the finish kernel
+  if (cudaEventSynchronize(c->events[last]) != cudaSuccess) return;
+  auto el = [&](int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->events[a], c->events[b]);
+    return (double)ms;
+  };
+  snk_stats& st = c->st;
+  st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = 0.0;
+  for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = 0.0;
+  int ev = 0;
+  for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
+    int e0 = ev;  // previous boundary
+    st.ms_collocation += el(e0, e0 + 1);
+    st.ms_fgemm += el(e0 + 1, e0 + 2);
+    for (int k = 0; k < kNumClasses; ++k) {
+      double t = el(e0 + 2 + k, e0 + 3 + k);
+      st.ms_integrals_class[k] += t;
+      st.ms_integrals += t;
+    }
+    st.ms_kgemm += el(e0 + 2 + kNumClasses, e0 + 3 + kNumClasses);
+    ev = e0 + 3 + kNumClasses;
+  }
+  st.ms_finish = el(ev, ev + 1);
+  st.ms_build = el(0, ev + 1);
+  st.kernel_launches = c->launches_density + c->launches_build;
+}
+
+}  // namespace
+
+extern "C" {
+
+void snk_options_default(snk_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps_basis = 1e-12;
+  o->eps_E = 1e-12;
+  o->eps_K = 1e-12;
+  o->batch_max = 4096;
+  o->precision = SNK_PREC_FP64;
+  o->screen = SNK_SCREEN_LINK;
+  o->fp32_bound = 1e-6;
+  o->workspace_bytes = 0;
+}
+
+const char* snk_status_string(int status) {
+  switch (status) {
+    case SNK_OK: return "ok";
+    case SNK_ERR_INVALID_ARG: return "invalid argument";
+    case SNK_ERR_UNSUPPORTED: return "unsupported input";
+    case SNK_ERR_NOT_SYMMETRIC: return "density matrix not symmetric";
+    case SNK_ERR_BAD_STATE: return "bad call order";
+    case SNK_ERR_OOM: return "out of memory";
+    case SNK_ERR_CUDA: return "CUDA error";
+    case SNK_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, snk_ctx** out) {
+  if (!out) return SNK_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<snk_ctx> c(new (std::nothrow) snk_ctx());
+  if (!c) return SNK_ERR_OOM;
+  if (opt)
+    c->opt = *opt;
+  else
+    snk_options_default(&c->opt);
+  if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
+  int rc = build_setup(basis, grid, &c->opt, &c->s, &c->err);
+  if (rc != SNK_OK) return rc;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return SNK_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) return SNK_ERR_CUDA;
+  if (cudaEventCreate(&c->ev_screen0) != cudaSuccess || cudaEventCreate(&c->ev_screen1) != cudaSuccess)
+    return SNK_ERR_CUDA;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return SNK_ERR_CUDA;
+  c->ws_budget = c->opt.workspace_bytes > 0 ? c->opt.workspace_bytes : (int64_t)(fr / 2);
+  Setup& s = c->s;
+  c->nbatch = (int)s.bstart.size() - 1;
+  // local X columns of the B_j shells
+  s.bshell_col.resize(s.bshell.size());
+  for (int j = 0; j < c->nbatch; ++j) {
+    int col = 0;
+    for (int t = s.bshell_off[j]; t < s.bshell_off[j + 1]; ++t) {
+      s.bshell_col[t] = col;
+      col += ncart(s.l[s.bshell[t]]);
+    }
+  }
+  snk_ctx* cp = c.get();
+  const cudaStream_t st = cp->stream;
+  std::vector<int> nprim(s.nprim);
+  std::vector<int> poff(s.poff.begin(), s.poff.end()), foff(s.foff.begin(), s.foff.end());
+  if ((rc = [&]() -> int {
+         SNK_CK(cp, upload(cp->l, s.l, st));
+         SNK_CK(cp, upload(cp->poff, poff, st));
+         SNK_CK(cp, upload(cp->nprim, nprim, st));
+         SNK_CK(cp, upload(cp->foff, foff, st));
+         SNK_CK(cp, upload(cp->fshell, s.fshell, st));
+         SNK_CK(cp, upload(cp->center, s.center, st));
+         SNK_CK(cp, upload(cp->exps, s.exps, st));
+         SNK_CK(cp, upload(cp->d, s.d, st));
+         SNK_CK(cp, upload(cp->fcomp, s.fcomp, st));
+         SNK_CK(cp, upload(cp->pairs, s.pairs, st));
+         SNK_CK(cp, upload(cp->prims, s.prims, st));
+         SNK_CK(cp, upload(cp->bound, s.bound, st));
+         SNK_CK(cp, upload(cp->xyz, s.xyz, st));
+         SNK_CK(cp, upload(cp->w, s.w, st));
+         SNK_CK(cp, upload(cp->bshell, s.bshell, st));
+         SNK_CK(cp, upload(cp->bshell_col, s.bshell_col, st));
+         SNK_CK(cp, upload(cp->xfunc, s.xfunc, st));
+         SNK_CK(cp, upload(cp->boys, s.boys, st));
+         SNK_CK(cp, cudaStreamSynchronize(st));
+         return SNK_OK;
+       }()) != SNK_OK)
+    return rc;
+  if ((rc = geometry_screen(cp)) != SNK_OK) return rc;
+  for (int k = 0; k < kNumClasses; ++k) cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms);
+  std::memset(&cp->st, 0, sizeof(cp->st));
+  cp->st.n_points = s.npts;
+  cp->st.n_batches = cp->nbatch;
+  cp->st.n_shells = s.ns;
+  cp->st.n_functions = s.nf;
+  cp->st.n_pairs = (int64_t)s.pairs.size();
+  *out = c.release();
+  return SNK_OK;
+}
+
+int snk_set_density(snk_ctx* c, const double* P) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!P) return fail(c, SNK_ERR_INVALID_ARG, "NULL density");
+  const size_t n = (size_t)c->s.nf * c->s.nf;
+  c->have_density = false;
+  SNK_CK(c, c->P.ensure(n));
+  SNK_CK(c, cudaMemcpyAsync(c->P.p, P, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  return screen_and_plan(c);
+}
+
+int snk_set_density_device(snk_ctx* c, const double* dP) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!dP) return fail(c, SNK_ERR_INVALID_ARG, "NULL density");
+  const size_t n = (size_t)c->s.nf * c->s.nf;
+  c->have_density = false;
+  SNK_CK(c, c->P.ensure(n));
+  SNK_CK(c, cudaMemcpyAsync(c->P.p, dP, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  return screen_and_plan(c);
+}
+
+int snk_build_K_device(snk_ctx* c, double* dK) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!dK) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
+  return build(c, dK);
+}
+
+int snk_build_K(snk_ctx* c, double* K) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!K) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
+  const size_t n = (size_t)c->s.nf * c->s.nf;
+  SNK_CK(c, c->K.ensure(n));
+  int rc = build(c, c->K.p);
+  if (rc != SNK_OK) return rc;
+  SNK_CK(c, cudaMemcpyAsync(K, c->K.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  return SNK_OK;
+}
+
+int snk_set_stream(snk_ctx* c, void* stream) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return SNK_OK;
+}
+
+int snk_get_stats(const snk_ctx* c, snk_stats* out) {
+  if (!c || !out) return SNK_ERR_INVALID_ARG;
+  snk_ctx* m = const_cast<snk_ctx*>(c);
+  collect_times(m);
+  *out = m->st;
+  return SNK_OK;
+}
+
+int64_t snk_n_functions(const snk_ctx* c) { return c ? c->s.nf : -1; }
+
+const char* snk_last_error(const snk_ctx* c) { return c ? c->err.c_str() : "NULL handle"; }
+
+void snk_destroy(snk_ctx* c) { delete c; }
+
+int snk_debug_boys(int64_t n, const double* T, int nmax, double* out) {
+  if (n < 0 || (n > 0 && (!T || !out)) || nmax < 0 || nmax > kBoysLMax) return SNK_ERR_INVALID_ARG;
+  if (n == 0) return SNK_OK;
+  // the same table the integral kernel uses
+  std::vector<double> tab((size_t)(kBoysLMax + 1) * kBoysRows * kBoysCols);
+  double F[kBoysLMax + kBoysTerms + 1], invfact = 1.0;
+  for (int k = 0; k < kBoysRows; ++k) {
+    double Tk = k * kBoysH;
+    host_boys(kBoysLMax + kBoysTerms, Tk, F);
+    for (int L = 0; L <= kBoysLMax; ++L) {
+      double* row = &tab[((size_t)L * kBoysRows + k) * kBoysCols];
+      invfact = 1.0;
+      for (int m = 0; m < kBoysTerms; ++m) {
+        if (m > 0) invfact /= m;
+        row[m] = F[L + m] * invfact;
+      }
+      row[kBoysTerms] = std::exp(-Tk);
+      row[kBoysTerms + 1] = Tk;
+    }
+  }
+  DevBuf<double> dtab, dT, dout;
+  if (dtab.ensure(tab.size()) || dT.ensure(n) || dout.ensure((size_t)n * (nmax + 1))) return SNK_ERR_OOM;
+  if (cudaMemcpy(dtab.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(dT.p, T, sizeof(double) * n, cudaMemcpyHostToDevice))
+    return SNK_ERR_CUDA;
+  if (launch_debug_boys(0, dtab.p, n, dT.p, nmax, dout.p) != cudaSuccess) return SNK_ERR_CUDA;
+  if (cudaMemcpy(out, dout.p, sizeof(double) * n * (nmax + 1), cudaMemcpyDeviceToHost)) return SNK_ERR_CUDA;
+  return SNK_OK;
+}
+
+int snk_debug_shell_A(snk_ctx* c, int32_t sa, int32_t sb, int64_t n, const double* xyz, double* out) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  Setup& s = c->s;
+  if (sa < 0 || sb < 0 || sa >= s.ns || sb >= s.ns || n < 0 || (n > 0 && (!xyz || !out)))
+    return fail(c, SNK_ERR_INVALID_ARG, "bad shell index or buffer");
+  const int na = ncart(s.l[sa]), nb = ncart(s.l[sb]);
+  const int p = s.pair_index[(size_t)sa * s.ns + sb];
+  if (n == 0) return SNK_OK;
+  if (p < 0) {
+    std::fill(out, out + (size_t)n * na * nb, 0.0);
+    return SNK_OK;
+  }
+  const PairHdr& h = s.pairs[p];
+  const int ca = ncart(s.l[h.sa]), cb = ncart(s.l[h.sb]);
+  DevBuf<double> dxyz, dxi;
+  SNK_CK(c, dxyz.ensure(3 * n));
+  SNK_CK(c, dxi.ensure((size_t)n * ca * cb));
+  SNK_CK(c, cudaMemcpyAsync(dxyz.p, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+  SNK_CK(c, launch_debug_A(c->stream, s.pair_class[p], c->pairs.p + p, c->prims.p, c->boys.p, n, dxyz.p, dxi.p));
+  std::vector<double> xi((size_t)n * ca * cb);
+  SNK_CK(c, cudaMemcpyAsync(xi.data(), dxi.p, sizeof(double) * xi.size(), cudaMemcpyDeviceToHost, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  const bool swap = h.sa != sa;
+  for (int64_t i = 0; i < n; ++i)
+    for (int u = 0; u < na; ++u)
+      for (int v = 0; v < nb; ++v) {
+        double x = swap ? xi[(size_t)i * ca * cb + v * cb + u] : xi[(size_t)i * ca * cb + u * cb + v];
+        out[(size_t)i * na * nb + u * nb + v] = x * s.fcomp[s.foff[sa] + u] * s.fcomp[s.foff[sb] + v];
+      }
+  return SNK_OK;
+}
+
+int snk_debug_pair_bound(snk_ctx* c, int32_t sa, int32_t sb, double* bound) {
+  if (!c || !bound || sa < 0 || sb < 0 || sa >= c->s.ns || sb >= c->s.ns) return SNK_ERR_INVALID_ARG;
+  *bound = pair_bound(c->s, sa, sb);
+  return SNK_OK;
+}
+
+int snk_debug_batches(snk_ctx* c, int64_t* n_batches, int32_t* counts, int64_t counts_cap, int64_t* perm) {
+  if (!c || !n_batches) return SNK_ERR_INVALID_ARG;
+  *n_batches = c->nbatch;
+  if (counts) {
+    if (counts_cap < c->nbatch) return fail(c, SNK_ERR_INVALID_ARG, "counts buffer too small");
+    for (int j = 0; j < c->nbatch; ++j) counts[j] = (int32_t)(c->s.bstart[j + 1] - c->s.bstart[j]);
+  }
+  if (perm) std::copy(c->s.perm.begin(), c->s.perm.end(), perm);
+  return SNK_OK;
+}
+
+}  // extern "C"

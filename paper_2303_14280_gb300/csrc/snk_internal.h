@@ -1,0 +1,171 @@
+// Internal declarations of libsnk (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/snk.h"
+
+namespace snk {
+
+constexpr int kLMax = 2;
+constexpr int kNumClasses = 6;  // (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+constexpr int kPointTile = 128;  // grid points per integral tile (one per thread)
+constexpr int kLdqAlign = 128;   // leading-dimension padding of batch matrices
+
+// Boys table: rows T_k = k * kBoysH, k = 0..kBoysRows-1; for T >= kBoysTMax the
+// asymptotic form is used.  One table per L = 0..4 with kBoysCols doubles per
+// row: F_{L+m}(T_k)/m! for m = 0..7, exp(-T_k), T_k.
+constexpr double kBoysH = 0.1;
+constexpr double kBoysTMax = 50.0;
+constexpr int kBoysRows = 502;
+constexpr int kBoysTerms = 8;
+constexpr int kBoysCols = kBoysTerms + 2;
+constexpr int kBoysLMax = 2 * kLMax;
+
+inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+inline int class_of(int la, int lb) {  // la >= lb
+  return la * (la + 1) / 2 + lb;
+}
+
+// Per primitive pair data used by the integral kernel (12 doubles).
+struct PrimPair {
+  double zeta;          // zeta_a + zeta_b
+  double Px, Py, Pz;    // Gaussian product centre R_p
+  double PAx, PAy, PAz; // R_p - R_a
+  double pref;          // 2 pi / zeta * exp(-zeta_a zeta_b |AB|^2 / zeta) * d_a d_b
+  double pref_far;      // pref * sqrt(pi) / 2  (large-T seed)
+  double k1, k2, k3;    // 1, 2, 3 times 1 / (2 zeta)
+};
+
+// Shell pair header.
+struct PairHdr {
+  int32_t sa, sb;       // shells; l(sa) >= l(sb)
+  int32_t pp_off, pp_n; // primitive pairs
+  double ABx, ABy, ABz; // R_a - R_b
+  double pad;
+};
+
+// Per grid batch, per build chunk.
+struct BatchDesc {
+  int64_t p0;        // first point in batch order
+  int32_t q;         // number of points
+  int32_t ldq;       // padded leading dimension of X, F, G
+  int32_t nB;        // X columns (functions of B_j)
+  int32_t nS;        // F / G columns (functions of the shells in V_j)
+  int64_t xoff;      // offsets (doubles) into the chunk workspace
+  int64_t foff;
+  int64_t goff;
+  int32_t xfunc_off; // CSR offsets into xfunc / sfunc / bshell
+  int32_t sfunc_off;
+  int32_t bshell_off;
+  int32_t nBshell;
+};
+
+// Integral-kernel tile: batch, pair-list range, first point.
+struct Tile {
+  int32_t batch, k0, k1, i0;
+};
+
+// ---------------------------------------------------------------- host setup
+
+struct Setup {
+  int ns = 0, nf = 0, nprim_total = 0;
+  std::vector<int> l, nprim, poff, foff, atom;
+  std::vector<double> center, exps, d, fcomp, rcut;
+  std::vector<int> fshell;  // shell of each function
+
+  // shell pairs sorted by class, then a, then b
+  std::vector<PairHdr> pairs;
+  std::vector<PrimPair> prims;
+  std::vector<double> bound;          // rigorous max_r |A| per pair
+  std::vector<int> pair_class;
+  int class_begin[kNumClasses + 1] = {0};
+  std::vector<int> pair_index;        // dense ns x ns -> pair id or -1
+
+  // grid, in batch order
+  int64_t npts = 0;
+  std::vector<double> xyz, w;
+  std::vector<int64_t> perm;          // batch order -> input order
+  std::vector<int64_t> bstart;        // n_batches + 1
+  std::vector<double> bcenter, bradius;
+  std::vector<int> bshell_off, bshell;  // B_j as shell lists (CSR)
+  std::vector<int> bshell_col;          // local X column of each B_j shell
+  std::vector<int> bnf;               // |B_j| in functions
+  std::vector<int> xfunc_off, xfunc;  // B_j as function lists (CSR)
+
+  std::vector<double> boys;           // (kBoysLMax+1) x kBoysRows x kBoysCols
+};
+
+// Validates and normalises the basis and grid; returns an snk_status and fills msg.
+int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, Setup* s,
+                std::string* msg);
+double pair_bound(const Setup& s, int sa, int sb);
+void host_boys(int nmax, double T, double* F);
+
+// ---------------------------------------------------------------- kernels
+
+struct DeviceBasis {
+  const int* l;
+  const int* poff;
+  const int* nprim;
+  const double* center;
+  const double* exps;
+  const double* d;
+  const double* fcomp;
+  const int* foff;
+};
+
+cudaError_t launch_collocation(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq,
+                               int max_nBshell, const int* bshell, const int* bshell_col, const double* xyz,
+                               DeviceBasis basis, double* ws);
+cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nB,
+                               const double* ws, const double* w, const int* xfunc, int nf,
+                               double* phit_f, double* phit_b);
+cudaError_t launch_ftilde(cudaStream_t st, const double* P, const double* phit_f, int nf,
+                          int nbatch, const int* fshell, int ns, double* ft_shell);
+cudaError_t launch_pair_count(cudaStream_t st, const PairHdr* pairs, const double* bound,
+                              const int* class_begin_host, const double* ft_shell, const double* phit_b,
+                              int ns, int nbatch, double eps_E, double eps_K, int screen,
+                              int* counts, unsigned char* sflag);
+cudaError_t launch_pair_write(cudaStream_t st, const PairHdr* pairs, const double* bound,
+                              const int* class_begin_host, const double* ft_shell, const double* phit_b,
+                              int ns, int nbatch, double eps_E, double eps_K, int screen,
+                              const int64_t* list_off, int* list);
+cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
+                         const double* P, int nf, const int* xfunc, const int* sfunc,
+                         const double* fcomp, const double* w, double* ws);
+cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
+                         const int* xfunc, const int* sfunc, int nf, const double* ws, double* Khat);
+cudaError_t launch_finish(cudaStream_t st, const double* Khat, const double* fcomp, int nf, double* K);
+cudaError_t launch_symcheck(cudaStream_t st, const double* P, int nf, double* out2);
+
+struct IntegralArgs {
+  const Tile* tiles;
+  int n_tiles;
+  int* ticket;
+  const BatchDesc* batches;
+  const int* pairlist;
+  const PairHdr* pairs;
+  const PrimPair* prims;
+  const int* colmap;  // nbatch x ns, local F/G column of each shell or -1
+  int ns;
+  const double* xyz;  // batch order
+  const double* boys; // device table, all L
+  double* ws;
+};
+
+cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
+int integral_max_ctas(int cls, int num_sms);
+cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const PrimPair* prims,
+                           const double* boys, int64_t n, const double* xyz, double* xi);
+cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, const double* T,
+                              int nmax, double* out);
+
+// FP64 operation counts of the integral kernel per class (from the generator).
+void class_flops(int cls, int nprim_pairs, double* flops_per_point);
+
+}  // namespace snk

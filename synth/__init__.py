@@ -312,6 +312,12 @@ def cluster96(device=None) -> Problem:
     return cluster(96, 102, n_occ=200, device=device)
 
 
+def cluster24(device=None) -> Problem:
+    """24 atoms (8 O-like, 16 H-like), 248 functions, 192,000 points: a small
+    case of the 96-atom workload's shape for kernel profiles."""
+    return cluster(24, 124, device=device)
+
+
 def cluster256(device=None) -> Problem:
     return cluster(256, 103, device=device)
 

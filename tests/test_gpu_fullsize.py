@@ -1,0 +1,45 @@
+"""Full-size parity on the 96-atom workload (992 functions, 768,000 points) in
+the launch configuration bench.py times (default options): sampled entries
+against the stored oracle values, plus properties that hold at any size."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster96_K_entries.txt")
+
+
+@pytest.fixture(scope="module")
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2303_14280_gb300 as snk
+    p = synth.cluster96(device="cuda")
+    eng = snk.Engine(p.basis, p.grid)
+    eng.set_density(p.P)
+    K = eng.build_K()
+    st = eng.stats()
+    eng.close()
+    return p, K, st
+
+
+def test_sampled_entries_match_oracle(built):
+    p, K, st = built
+    d = np.loadtxt(GOLDEN)
+    mu, nu, ref = d[:, 0].astype(int), d[:, 1].astype(int), d[:, 2]
+    err = np.max(np.abs(K[mu, nu] - ref))
+    assert err <= 1e-10, err
+
+
+def test_fullsize_properties(built):
+    p, K, st = built
+    assert np.max(np.abs(K - K.T)) == 0.0            # Eq. (sn_k) symmetrises exactly
+    assert np.trace(K @ p.P) > 0.0                   # exchange energy has a definite sign
+    assert np.all(np.isfinite(K))
+    assert st["n_points"] == 768000 and st["n_functions"] == 992
+    assert 0 < st["pairs_kept"] <= st["n_pairs"] * st["n_batches"]

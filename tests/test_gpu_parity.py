@@ -1,0 +1,163 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerance: max|dK| <= 1e-10 Eh (the accuracy target of the plain FP64 build);
+unit checks of the Boys function and of the 3c-CP blocks use relative bounds
+derived from the device Boys interpolation (8-term Taylor, |dT| <= 0.05:
+truncation ~1e-15 relative) and FP64 rounding of the recursions.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_K = 1e-10
+
+
+@pytest.fixture(scope="module")
+def snk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2303_14280_gb300 as m
+    m.lib()
+    return m
+
+
+def test_boys_device_matches_oracle(snk):
+    T = np.concatenate([np.linspace(0, 60, 6001), [1e-12, 0.05, 0.0499999, 49.95, 49.9999999, 50.0, 50.0000001,
+                                                   75.0, 300.0, 1e4]])
+    for nmax in range(5):
+        d = snk.debug_boys(T, nmax)
+        ref = np.array([oracle.boys(nmax, t) for t in T])
+        rel = np.max(np.abs(d - ref) / ref)
+        assert rel <= 2e-14, (nmax, rel)
+
+
+@pytest.mark.parametrize("recipe", ["small", "scale"])
+def test_shell_blocks_match_oracle(snk, recipe):
+    """Every class (ss ... dd), points at the pair centre (T = 0), near and far."""
+    mol = synth.make_cluster_molecule(6, 31)
+    basis = synth.make_basis(mol, recipe, 31)
+    grid = synth.make_grid(mol, 6, 2, 4)
+    eng = snk.Engine(basis, grid)
+    rng = np.random.default_rng(5)
+    seen = set()
+    for sa in range(basis.n_shells):
+        for sb in range(basis.n_shells):
+            cls = (max(basis.l[sa], basis.l[sb]), min(basis.l[sa], basis.l[sb]))
+            if (cls, sa == sb) in seen and rng.random() > 0.15:
+                continue
+            seen.add((cls, sa == sb))
+            mid = 0.5 * (basis.center[sa] + basis.center[sb])
+            pts = np.concatenate([mid[None], basis.center[[sa]], mid + rng.normal(size=(6, 3)) * 0.7,
+                                  mid + rng.normal(size=(4, 3)) * 6.0, mid + np.array([[40.0, 3.0, -2.0]])])
+            dev = eng.debug_shell_A(sa, sb, pts)
+            ref = np.stack([oracle.shell_A(basis, sa, sb, r) for r in pts])
+            # per point relative, floored at 1e-3 of the pair's largest value: blocks
+            # that vanish by symmetry (an s-p pair at its own centre) are pure FP64
+            # rounding of cancelling O(max) terms, ~1e-16 max on both sides
+            scale = np.maximum(np.max(np.abs(ref), axis=(1, 2), keepdims=True), 1e-3 * np.max(np.abs(ref)))
+            assert np.max(np.abs(dev - ref) / scale) <= 1e-12, (sa, sb)
+    eng.close()
+
+
+def _gpu_K(snk, p, P=None, **opts):
+    eng = snk.Engine(p.basis, p.grid, **opts)
+    eng.set_density(p.P if P is None else P)
+    K = eng.build_K()
+    st = eng.stats()
+    eng.close()
+    return K, st
+
+
+def test_chain4_unscreened_matches_oracle(snk, chain4):
+    Kref = oracle.snk_K(chain4.basis, chain4.grid, chain4.P)
+    K, st = _gpu_K(snk, chain4, screen="none", eps_basis=0.0)
+    assert st["pairs_kept"] == st["n_batches"] * st["n_pairs"]
+    assert np.max(np.abs(K - Kref)) <= TOL_K
+    assert np.max(np.abs(K - K.T)) == 0.0
+
+
+def test_chain4_screened_matches_oracle(snk, chain4):
+    Kref = oracle.snk_K(chain4.basis, chain4.grid, chain4.P)
+    K, st = _gpu_K(snk, chain4)
+    assert np.max(np.abs(K - Kref)) <= TOL_K
+
+
+def test_many_ragged_batches_and_chunks(snk):
+    """12-atom cluster, scale basis: small batches (ragged 128-point tails), several
+    workspace chunks (Alg. 1 loop), screened and unscreened, against the full oracle."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    for opts in (dict(batch_max=300, workspace_bytes=6 << 20), dict(batch_max=4096, screen="none", eps_basis=0.0),
+                 dict(batch_max=97, workspace_bytes=1 << 20)):
+        K, st = _gpu_K(snk, p, **opts)
+        assert st["n_batches"] >= 12
+        assert np.max(np.abs(K - Kref)) <= TOL_K, opts
+    assert st["n_chunks"] > 1
+
+
+def test_linearity_in_the_density(snk, chain4):
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=chain4.P.shape)
+    P2 = 0.05 * (X + X.T)
+    K1, _ = _gpu_K(snk, chain4, screen="none")
+    K2, _ = _gpu_K(snk, chain4, P=P2, screen="none")
+    K12, _ = _gpu_K(snk, chain4, P=chain4.P + P2, screen="none")
+    assert np.max(np.abs(K12 - K1 - K2)) <= 1e-12
+
+
+def test_device_resident_path_matches_host_path(snk, chain4):
+    import torch
+    eng = snk.Engine(chain4.basis, chain4.grid)
+    eng.set_stream(torch.cuda.current_stream())
+    eng.set_density(chain4.P)
+    Kh = eng.build_K()
+    Pd = torch.from_numpy(chain4.P).cuda()
+    eng.set_density(Pd)
+    Kd = torch.zeros_like(Pd)
+    eng.build_K(out=Kd)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(Kd.cpu().numpy() - Kh)) <= 1e-14
+    eng.close()
+
+
+def test_edge_cases(snk):
+    # one atom, one s shell; batch_max = 1 makes every point its own batch
+    basis = synth.Basis(l=np.array([0], dtype=np.int32), nprim=np.array([1], dtype=np.int32),
+                        atom=np.array([0], dtype=np.int32), center=np.zeros((1, 3)),
+                        exps=np.array([0.7]), coefs=np.array([1.0]))
+    mol = synth.Molecule(Z=np.array([8], dtype=np.int32), xyz=np.zeros((1, 3)))
+    grid = synth.make_grid(mol, 5, 2, 3)
+    P = np.ones((1, 1))
+    p = synth.Problem("one", mol, basis, grid, P)
+    K, st = _gpu_K(snk, p, batch_max=1)
+    assert st["n_batches"] == grid.n_points
+    assert abs(K[0, 0] - oracle.snk_K(basis, grid, P)[0, 0]) <= 1e-13
+    # empty grid: K = 0
+    empty = synth.Grid(xyz=np.zeros((0, 3)), w=np.zeros(0), atom=np.zeros(0, dtype=np.int32))
+    K, st = _gpu_K(snk, synth.Problem("e", mol, basis, empty, P))
+    assert st["n_batches"] == 0 and K[0, 0] == 0.0
+
+
+def test_errors_leave_the_handle_usable(snk, chain4):
+    eng = snk.Engine(chain4.basis, chain4.grid)
+    with pytest.raises(snk.SnkError) as e:
+        eng.build_K()
+    assert e.value.status == -4                      # build before set_density
+    Pbad = chain4.P.copy()
+    Pbad[0, 1] += 1e-6
+    with pytest.raises(snk.SnkError) as e:
+        eng.set_density(Pbad)
+    assert e.value.status == -3
+    Pnan = chain4.P.copy()
+    Pnan[2, 2] = np.nan
+    with pytest.raises(snk.SnkError):
+        eng.set_density(Pnan)
+    eng.set_density(chain4.P)                        # recovers
+    K = eng.build_K()
+    assert np.max(np.abs(K - oracle.snk_K(chain4.basis, chain4.grid, chain4.P))) <= TOL_K
+    eng.close()
