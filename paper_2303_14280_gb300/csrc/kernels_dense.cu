@@ -331,7 +331,8 @@ __global__ void finish_kernel(const double* __restrict__ Khat, const double* __r
   const int64_t n = (int64_t)nf * nf;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int mu = (int)(e / nf), nu = (int)(e % nf);
-    K[e] = 0.5 * (fcomp[mu] * Khat[e] + fcomp[nu] * Khat[(int64_t)nu * nf + mu]);
+    // explicit rounding of both products keeps K exactly symmetric (no FMA contraction)
+    K[e] = 0.5 * __dadd_rn(__dmul_rn(fcomp[mu], Khat[e]), __dmul_rn(fcomp[nu], Khat[(int64_t)nu * nf + mu]));
   }
 }
 
