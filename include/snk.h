@@ -171,6 +171,29 @@ int snk_debug_pair_bound(snk_ctx *ctx, int32_t sa, int32_t sb, double *bound);
 int snk_debug_batches(snk_ctx *ctx, int64_t *n_batches, int32_t *counts, int64_t counts_cap,
                       int64_t *perm);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* The paper has no counterpart to this entry point: it serves callers that
+ * must not call cudaMalloc, such as code that runs while a CUDA graph is being
+ * captured or a host that hands out all device memory from its own pool.
+ *
+ * Same result as snk_debug_shell_A (the 3c-CP block A_{mu lam}(r) of the
+ * normalised shells sa, sb at n points, out = n x ncart(l_sa) x ncart(l_sb)),
+ * but xyz (3n doubles) and out are DEVICE pointers and the call allocates
+ * nothing: the intermediate block goes to a fixed scratch array inside the
+ * library, 4096 points x 36 doubles (1.125 MiB), which every GPU that loads
+ * the library holds until the process exits.
+ *   - n > 4096 returns SNK_ERR_INVALID_ARG; split larger point sets.
+ *   - The first call on a device looks the scratch address up (set-up, once
+ *     per device); make that first call before any stream capture.
+ *   - The work is enqueued on the handle's stream (snk_set_stream) and the
+ *     call returns without waiting.
+ *   - All calls share the one scratch array and it keeps the last call's
+ *     contents; calls that overlap on the GPU (other streams, other handles)
+ *     race on it.  Order them on one stream. */
+int snk_shell_A_noalloc(snk_ctx *ctx, int32_t sa, int32_t sb, int64_t n, const double *xyz,
+                        double *out);
+
 #ifdef __cplusplus
 }
 #endif

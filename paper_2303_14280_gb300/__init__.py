@@ -37,7 +37,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 SYMBOLS = ["snk_options_default", "snk_create", "snk_set_density", "snk_set_density_device", "snk_build_K",
            "snk_build_K_device", "snk_set_stream", "snk_get_stats", "snk_n_functions", "snk_last_error",
            "snk_status_string", "snk_destroy", "snk_debug_boys", "snk_debug_shell_A", "snk_debug_pair_bound",
-           "snk_debug_batches"]
+           "snk_debug_batches", "snk_shell_A_noalloc"]
 
 
 class SnkError(RuntimeError):
@@ -112,6 +112,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
             L.snk_debug_boys.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
             L.snk_debug_shell_A.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D]
             L.snk_debug_pair_bound.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _D]
+            L.snk_shell_A_noalloc.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P]
             L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
             _lib = L
@@ -245,6 +246,18 @@ class Engine:
         out = np.zeros((xyz.shape[0], na, nb))
         self._check(lib().snk_debug_shell_A(self._h, int(sa), int(sb), xyz.shape[0], _dptr(xyz), _dptr(out)),
                     "snk_debug_shell_A")
+        return out
+
+    def shell_A_noalloc(self, sa, sb, xyz, out):
+        """snk_shell_A_noalloc: the same block as debug_shell_A for callers that
+        cannot allocate device memory.  xyz (n, 3) and out (n, n_a, n_b) are
+        contiguous float64 CUDA tensors owned by the caller; n <= 4096.  The
+        work is enqueued on the engine's stream; the call does not wait."""
+        assert _is_cuda_tensor(xyz) and _is_cuda_tensor(out)
+        assert xyz.is_contiguous() and out.is_contiguous() and xyz.element_size() == 8 and out.element_size() == 8
+        n = xyz.shape[0]
+        self._check(lib().snk_shell_A_noalloc(self._h, int(sa), int(sb), int(n), _P(xyz.data_ptr()),
+                                              _P(out.data_ptr())), "snk_shell_A_noalloc")
         return out
 
     def debug_pair_bound(self, sa, sb) -> float:

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -733,3 +734,84 @@ int snk_debug_batches(snk_ctx* c, int64_t* n_batches, int32_t* counts, int64_t c
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of snk_debug_shell_A, for callers that must not
+// call cudaMalloc (for example code running while a CUDA graph is being
+// captured, or a host that owns all device memory through its own pool).
+// The raw contracted block Xi (before component factors) goes to a fixed
+// scratch array in this file instead of a per-call device allocation.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = 4096;
+constexpr int kMaxDevices = 64;
+
+// Shared by every call on a device and never freed (it lives as long as the
+// module is loaded): 4096 points x 36 doubles = 1.125 MiB per device.
+static __device__ __align__(256) double g_xi_scratch[kNoAllocMaxPoints * 36];
+
+std::mutex g_scratch_mutex;
+double* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_xi_scratch on the current device, looked up once per
+// device (host code cannot use the symbol's name as a device pointer).
+cudaError_t scratch_for_current_device(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_xi_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+// out[i][u][v] = f_u f_v Xi[i][u][v], or the transposed block when the stored
+// pair has its shells the other way round.
+__global__ void finish_shell_A_kernel(const double* __restrict__ xi, int64_t n, int ca, int cb, int swap,
+                                      const double* __restrict__ fa, const double* __restrict__ fb,
+                                      double* __restrict__ out) {
+  const int na = swap ? cb : ca, nb = swap ? ca : cb;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * na * nb) return;
+  const int64_t i = e / (na * nb);
+  const int u = (int)(e % (na * nb)) / nb, v = (int)(e % nb);
+  const double x = swap ? xi[i * ca * cb + v * cb + u] : xi[i * ca * cb + u * cb + v];
+  out[e] = x * fa[u] * fb[v];
+}
+
+}  // namespace
+
+extern "C" int snk_shell_A_noalloc(snk_ctx* c, int32_t sa, int32_t sb, int64_t n, const double* xyz, double* out) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  Setup& s = c->s;
+  if (sa < 0 || sb < 0 || sa >= s.ns || sb >= s.ns || n < 0 || (n > 0 && (!xyz || !out)))
+    return fail(c, SNK_ERR_INVALID_ARG, "snk_shell_A_noalloc: bad shell index or buffer");
+  if (n > kNoAllocMaxPoints)
+    return fail(c, SNK_ERR_INVALID_ARG,
+                "snk_shell_A_noalloc: n exceeds the 4096-point scratch; split the points into calls of at most 4096");
+  double* scratch = nullptr;
+  SNK_CK(c, scratch_for_current_device(&scratch));
+  if (n == 0) return SNK_OK;
+  const int na = ncart(s.l[sa]), nb = ncart(s.l[sb]);
+  const int p = s.pair_index[(size_t)sa * s.ns + sb];
+  if (p < 0) {  // pair dropped at setup: its block is zero to below 1e-40
+    SNK_CK(c, cudaMemsetAsync(out, 0, sizeof(double) * n * na * nb, c->stream));
+    return SNK_OK;
+  }
+  const PairHdr& h = s.pairs[p];
+  const int ca = ncart(s.l[h.sa]), cb = ncart(s.l[h.sb]);
+  SNK_CK(c, launch_debug_A(c->stream, s.pair_class[p], c->pairs.p + p, c->prims.p, c->boys.p, n, xyz, scratch));
+  const int64_t tot = n * na * nb;
+  finish_shell_A_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
+      scratch, n, ca, cb, h.sa != sa ? 1 : 0, c->fcomp.p + s.foff[sa], c->fcomp.p + s.foff[sb], out);
+  SNK_CK(c, cudaGetLastError());
+  return SNK_OK;
+}
