@@ -91,8 +91,11 @@ typedef struct {
   int32_t batch_max;       /* largest grid batch (octree leaf), Sec. III: 4096  */
   int32_t precision;       /* snk_precision                                      */
   int32_t screen;          /* snk_screen_mode                                    */
-  int32_t reserved0;
-  double fp32_bound;       /* mixed form: pairs whose bound is below go FP32     */
+  int32_t distance_bound;  /* 1: per batch, A-tilde = min(global bound, total
+                              charge / distance to the batch) -- both rigorous;
+                              0: the global bound alone, as in the paper        */
+  double fp32_bound;       /* mixed form: kept pairs whose sn-LinK estimate
+                              epsilon^K is below this run their integrals in FP32 */
   int64_t workspace_bytes; /* device workspace cap for batch chunks (Alg. 1); 0 = auto */
   double reserved[8];
 } snk_options;
@@ -111,9 +114,14 @@ typedef struct {
   double ms_screen;            /* last set_density: upload, F-tilde, pair screen    */
   double ms_collocation, ms_fgemm, ms_integrals, ms_kgemm, ms_finish; /* last build  */
   double ms_build;             /* last build, first to last event                   */
-  double ms_integrals_class[6];/* per class ss ps pp ds dp dd                        */
+  double ms_integrals_class[6];/* per class ss ps pp ds dp dd (FP64 lists)          */
   double integrals_class[6];
   double flops_class[6];
+  int64_t pairs_kept_fp32;     /* mixed form: kept (batch, pair) entries run in FP32 */
+  double integrals_fp32;       /* their integrals                                    */
+  double flops_fp32;           /* their algorithmic FP32 flops                       */
+  double ms_integrals_fp32;    /* their kernel time                                  */
+  double reserved_stats[8];
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,

@@ -61,7 +61,7 @@ class SnkGrid(ctypes.Structure):
 class SnkOptions(ctypes.Structure):
     _fields_ = [("eps_basis", ctypes.c_double), ("eps_E", ctypes.c_double), ("eps_K", ctypes.c_double),
                 ("batch_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
+                ("distance_bound", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("reserved", ctypes.c_double * 8)]
 
 
@@ -73,7 +73,9 @@ class SnkStats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("ms_screen", "ms_collocation", "ms_fgemm", "ms_integrals", "ms_kgemm",
                                                 "ms_finish", "ms_build")] + \
                [("ms_integrals_class", ctypes.c_double * 6), ("integrals_class", ctypes.c_double * 6),
-                ("flops_class", ctypes.c_double * 6)]
+                ("flops_class", ctypes.c_double * 6), ("pairs_kept_fp32", ctypes.c_int64),
+                ("integrals_fp32", ctypes.c_double), ("flops_fp32", ctypes.c_double),
+                ("ms_integrals_fp32", ctypes.c_double), ("reserved_stats", ctypes.c_double * 8)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -9,7 +9,8 @@ For each class (l_a, l_b) with l_a >= l_b, l <= 2 this emits
   * ``hrr``: the horizontal recursion (App. A, Eq. hrr) from the contracted
     accumulator to the target block Xi_{ab};
 
-as straight-line FP64 code on named registers.  Only the intermediates that
+as straight-line code on named registers, templated on the arithmetic type
+(double for the FP64 path, float for the FP32 pairs of the mixed form).  Only the intermediates that
 some target needs are emitted (a dependency walk from the targets, in the
 spirit of the paper's pre-order traversal), and the direction of each step
 is chosen to avoid the third VRR term where possible.  The generator also
@@ -90,7 +91,7 @@ def gen_vrr(la, lb):
     for (e, n) in order:
         v = f"t{name_e(e)}_{n}"
         if sum(e) == 0:
-            lines.append(f"const double {v} = S[{n}];")
+            lines.append(f"const R {v} = S[{n}];")
             continue
         q = vrr_direction(e)
         Q = "xyz"[q]
@@ -108,12 +109,12 @@ def gen_vrr(la, lb):
             if key not in diffs:
                 dname = f"d{name_e(mm)}_{n}"
                 diffs[key] = dname
-                lines.append(f"const double {dname} = t{name_e(mm)}_{n} - t{name_e(mm)}_{n + 1};")
+                lines.append(f"const R {dname} = t{name_e(mm)}_{n} - t{name_e(mm)}_{n + 1};")
                 c.add += 1
-            lines.append(f"const double {v} = fma(k{m[q]}, {diffs[key]}, {base});")
+            lines.append(f"const R {v} = fma(k{m[q]}, {diffs[key]}, {base});")
             c.fma += 1
         else:
-            lines.append(f"const double {v} = {base};")
+            lines.append(f"const R {v} = {base};")
     acc_index = {}
     for (e, _) in targets:
         acc_index[e] = len(acc_index)
@@ -155,7 +156,7 @@ def gen_hrr(la, lb, acc_index, rule):
     for (e, f) in order:
         v = f"x{name_e(e)}_{name_e(f)}"
         if sum(f) == 0:
-            lines.append(f"const double {v} = acc[{acc_index[e]}];")
+            lines.append(f"const R {v} = acc[{acc_index[e]}];")
             continue
         q = step(f)
         Q = "xyz"[q]
@@ -165,7 +166,7 @@ def gen_hrr(la, lb, acc_index, rule):
         e1 = list(e)
         e1[q] += 1
         e1 = tuple(e1)
-        lines.append(f"const double {v} = fma(AB{Q}, x{name_e(e)}_{name_e(g)}, x{name_e(e1)}_{name_e(g)});")
+        lines.append(f"const R {v} = fma(AB{Q}, x{name_e(e)}_{name_e(g)}, x{name_e(e1)}_{name_e(g)});")
         c.fma += 1
     for i, a in enumerate(carts(la)):
         for j, b in enumerate(carts(lb)):
@@ -202,15 +203,15 @@ def main(out=sys.stdout):
         w(f"  static constexpr int VRR_OPS = {vc.ops};\n")
         w(f"  static constexpr int HRR_FLOPS = {hc.flops};\n")
         w(f"  static constexpr int HRR_OPS = {hc.ops};\n")
-        w("  __device__ static __forceinline__ void vrr(const double* S, double PAx, double PAy, double PAz,\n")
-        w("                                             double PCx, double PCy, double PCz, double k1,\n")
-        w("                                             double k2, double k3, double* acc) {\n")
+        w("  template <typename R>\n")
+        w("  __device__ static __forceinline__ void vrr(const R* S, R PAx, R PAy, R PAz, R PCx, R PCy, R PCz,\n")
+        w("                                             R k1, R k2, R k3, R* acc) {\n")
         w("    (void)PAx; (void)PAy; (void)PAz; (void)PCx; (void)PCy; (void)PCz; (void)k1; (void)k2; (void)k3;\n")
         for s in vl:
             w("    " + s + "\n")
         w("  }\n")
-        w("  __device__ static __forceinline__ void hrr(const double* acc, double ABx, double ABy, double ABz,\n")
-        w("                                             double* xi) {\n")
+        w("  template <typename R>\n")
+        w("  __device__ static __forceinline__ void hrr(const R* acc, R ABx, R ABy, R ABz, R* xi) {\n")
         w("    (void)ABx; (void)ABy; (void)ABz;\n")
         for s in hl:
             w("    " + s + "\n")

@@ -105,44 +105,63 @@ void host_boys(int nmax, double T, double* F) {
 // the potential of a positive, spherically symmetric charge is largest at its
 // centre, so |A| <= sum |d d'| f f' K_ab 4 pi int_0^inf s (s+dA)^la (s+dB)^lb
 // exp(-zeta s^2) ds, each power integrated in closed form.
-double pair_bound(const Setup& s, int sa, int sb) {
+// Bounds of one primitive pair (k of shell sa, m of shell sb), normalised
+// coefficients and the largest component factors included:
+//   *abound >= max_r |A^{km}(r)|  (the potential at the charge's centre), and
+//   *qbound >= int |phi_k phi_m| d^3r (the total charge), so that at distance
+//   D from the Gaussian product centre |A^{km}| <= *qbound / D.
+// |x_A^a ...| <= |r' - A|^{l_a} <= (s + |P - A|)^{l_a} with s = |r' - P|; the
+// potential of a positive, spherically symmetric charge is largest at its
+// centre and at most Q / D outside; every power of s integrates in closed form.
+void prim_pair_bounds(const Setup& s, int sa, int sb, int k, int m, double* abound, double* qbound) {
   const double fmax[3] = {1.0, 1.0, std::sqrt(3.0)};
-  int la = s.l[sa], lb = s.l[sb];
+  const int la = s.l[sa], lb = s.l[sb];
   const double* A = &s.center[3 * sa];
   const double* B = &s.center[3 * sb];
   double ab2 = 0.0;
   for (int q = 0; q < 3; ++q) ab2 += (A[q] - B[q]) * (A[q] - B[q]);
-  double total = 0.0;
+  const double al = s.exps[k], be = s.exps[m], z = al + be;
+  const double K = std::exp(-al * be / z * ab2);
+  double dA = 0.0, dB = 0.0;
+  for (int q = 0; q < 3; ++q) {
+    double P = (al * A[q] + be * B[q]) / z;
+    dA += (P - A[q]) * (P - A[q]);
+    dB += (P - B[q]) * (P - B[q]);
+  }
+  dA = std::sqrt(dA);
+  dB = std::sqrt(dB);
+  // polynomial (s + dA)^la (s + dB)^lb = sum_j c_j s^j
+  double c[5] = {1, 0, 0, 0, 0};
+  int deg = 0;
+  for (int t = 0; t < la + lb; ++t) {
+    double d = t < la ? dA : dB;
+    for (int j = deg + 1; j >= 0; --j) c[j] = (j > 0 ? c[j - 1] : 0.0) + d * c[j];
+    ++deg;
+  }
+  // int_0^inf s^{j+1} e^{-z s^2} ds = Gamma((j+2)/2) / (2 z^{(j+2)/2}), and
+  // int_0^inf s^{j+2} e^{-z s^2} ds = Gamma((j+3)/2) / (2 z^{(j+3)/2})
+  static const double g2[5] = {0.5, 0.44311346272637900682, 0.5, 0.66467019408956851023, 1.0};
+  static const double g3[5] = {0.44311346272637900682, 0.5, 0.66467019408956851023, 1.0, 1.66167548522392127557};
+  const double rz = 1.0 / std::sqrt(z);
+  double zp = rz * rz, ia = 0.0, iq = 0.0;
+  for (int j = 0; j <= deg; ++j) {
+    ia += c[j] * g2[j] * zp;
+    iq += c[j] * g3[j] * zp * rz;
+    zp *= rz;
+  }
+  const double pre = std::fabs(s.d[k] * s.d[m]) * K * 4.0 * kPi * fmax[la] * fmax[lb];
+  *abound = pre * ia;
+  *qbound = pre * iq;
+}
+
+double pair_bound(const Setup& s, int sa, int sb) {
+  double total = 0.0, a, q;
   for (int k = s.poff[sa]; k < s.poff[sa] + s.nprim[sa]; ++k)
     for (int m = s.poff[sb]; m < s.poff[sb] + s.nprim[sb]; ++m) {
-      double al = s.exps[k], be = s.exps[m], z = al + be;
-      double K = std::exp(-al * be / z * ab2);
-      double dA = 0.0, dB = 0.0;
-      for (int q = 0; q < 3; ++q) {
-        double P = (al * A[q] + be * B[q]) / z;
-        dA += (P - A[q]) * (P - A[q]);
-        dB += (P - B[q]) * (P - B[q]);
-      }
-      dA = std::sqrt(dA);
-      dB = std::sqrt(dB);
-      // polynomial (s + dA)^la (s + dB)^lb = sum_j c_j s^j
-      double c[5] = {1, 0, 0, 0, 0};
-      int deg = 0;
-      for (int t = 0; t < la + lb; ++t) {
-        double d = t < la ? dA : dB;
-        for (int j = deg + 1; j >= 0; --j) c[j] = (j > 0 ? c[j - 1] : 0.0) + d * c[j];
-        ++deg;
-      }
-      // int_0^inf s^{j+1} e^{-z s^2} ds = Gamma((j+2)/2) / (2 z^{(j+2)/2})
-      static const double half_gamma[5] = {0.5, 0.44311346272637900682, 0.5, 0.66467019408956851023, 1.0};
-      double rz = 1.0 / std::sqrt(z), zp = rz * rz, integral = 0.0;
-      for (int j = 0; j <= deg; ++j) {
-        integral += c[j] * half_gamma[j] * zp;
-        zp *= rz;
-      }
-      total += std::fabs(s.d[k] * s.d[m]) * K * 4.0 * kPi * integral;
+      prim_pair_bounds(s, sa, sb, k, m, &a, &q);
+      total += a;
     }
-  return total * fmax[la] * fmax[lb];
+  return total;
 }
 
 int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, Setup* s,
@@ -271,18 +290,32 @@ int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options*
   s->pairs.clear();
   s->prims.clear();
   s->bound.clear();
+  s->qbound.clear();
   s->pair_class.clear();
   for (int c = 0; c < kNumClasses; ++c) {
     s->class_begin[c] = (int)s->pairs.size();
     for (auto& ab : bycls[c]) {
       int a = ab.first, b = ab.second;
-      double bnd = pair_bound(*s, a, b);
-      if (!(bnd >= 1e-40)) continue;  // underflows everywhere
+      // primitive pairs whose potential is below kPrimPairTol everywhere are
+      // left out; a pair with no primitive left is dropped
+      double bnd = 0.0, qb = 0.0;
+      std::vector<std::pair<int, int>> keep;
+      for (int k = s->poff[a]; k < s->poff[a + 1]; ++k)
+        for (int m = s->poff[b]; m < s->poff[b + 1]; ++m) {
+          double pa, pq;
+          prim_pair_bounds(*s, a, b, k, m, &pa, &pq);
+          if (pa >= kPrimPairTol) {
+            keep.emplace_back(k, m);
+            bnd += pa;
+            qb += pq;
+          }
+        }
+      if (keep.empty()) continue;
       PairHdr h;
       h.sa = a;
       h.sb = b;
       h.pp_off = (int)s->prims.size();
-      h.pp_n = s->nprim[a] * s->nprim[b];
+      h.pp_n = (int)keep.size();
       const double* A = &s->center[3 * a];
       const double* B = &s->center[3 * b];
       h.ABx = A[0] - B[0];
@@ -290,8 +323,9 @@ int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options*
       h.ABz = A[2] - B[2];
       h.pad = 0.0;
       double ab2 = h.ABx * h.ABx + h.ABy * h.ABy + h.ABz * h.ABz;
-      for (int k = s->poff[a]; k < s->poff[a + 1]; ++k)
-        for (int m = s->poff[b]; m < s->poff[b + 1]; ++m) {
+      for (auto& km : keep) {
+        {
+          const int k = km.first, m = km.second;
           double al = s->exps[k], be = s->exps[m], z = al + be;
           PrimPair p;
           p.zeta = z;
@@ -308,10 +342,12 @@ int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options*
           p.k3 = 1.5 / z;
           s->prims.push_back(p);
         }
+      }
       s->pair_index[(size_t)a * ns + b] = (int)s->pairs.size();
       s->pair_index[(size_t)b * ns + a] = (int)s->pairs.size();
       s->pairs.push_back(h);
       s->bound.push_back(bnd);
+      s->qbound.push_back(qb);
       s->pair_class.push_back(c);
     }
   }
@@ -410,6 +446,16 @@ int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options*
       row[kBoysTerms + 1] = T;
     }
   }
+  // FP32 table of the mixed form (rounded from the same FP64 values)
+  s->boys_f.assign((size_t)(kBoysLMax + 1) * kBoysRowsF * kBoysColsF, 0.0f);
+  for (int k = 0; k < kBoysRowsF; ++k)
+    for (int L = 0; L <= kBoysLMax; ++L) {
+      const double* src = &s->boys[((size_t)L * kBoysRows + k) * kBoysCols];
+      float* row = &s->boys_f[((size_t)L * kBoysRowsF + k) * kBoysColsF];
+      for (int m = 0; m < kBoysTermsF; ++m) row[m] = (float)src[m];
+      row[kBoysTermsF] = (float)src[kBoysTerms];
+      row[kBoysTermsF + 1] = (float)src[kBoysTerms + 1];
+    }
   return SNK_OK;
 }
 

@@ -203,75 +203,108 @@ __global__ void __launch_bounds__(GEMM_THREADS) ftilde_kernel(const double* __re
 
 constexpr int SCR_THREADS = 256;
 
-__device__ __forceinline__ bool keep_pair(const PairHdr& h, double bnd, const double* ft, double phib,
-                                          double eps_E, double eps_K, int screen) {
-  if (screen == SNK_SCREEN_NONE) return true;
-  const double fa = ft[h.sa], fb = ft[h.sb];
-  return (fa * fb * bnd >= eps_E) || (fmax(fa, fb) * phib * bnd >= eps_K);
+// Bound of max_{r in Q_j} |A_ab(r)| for batch j: the global bound A-tilde, or,
+// when the batch's bounding sphere stays clear of the segment AB that holds
+// every Gaussian product centre, the smaller total-charge / distance bound.
+__device__ __forceinline__ double batch_pair_bound(const ScreenArgs& a, int j, int p, const PairHdr& h) {
+  const double bnd = a.bound[p];
+  if (!a.distance) return bnd;
+  const double* A = a.shell_xyz + 3 * h.sa;
+  const double vx = -h.ABx, vy = -h.ABy, vz = -h.ABz;  // B - A
+  const double wx = a.bcenter[3 * j] - A[0], wy = a.bcenter[3 * j + 1] - A[1], wz = a.bcenter[3 * j + 2] - A[2];
+  const double vv = vx * vx + vy * vy + vz * vz;
+  double t = vv > 0.0 ? (wx * vx + wy * vy + wz * vz) / vv : 0.0;
+  t = fmin(fmax(t, 0.0), 1.0);
+  const double dx = wx - t * vx, dy = wy - t * vy, dz = wz - t * vz;
+  const double d = sqrt(dx * dx + dy * dy + dz * dz) - a.bradius[j];
+  return d > 0.0 ? fmin(bnd, a.qbound[p] / d) : bnd;
 }
 
-struct ClassRanges {
-  int b[kNumClasses + 1];
-};
+// sn-LinK decision for pair p in batch j, Eq. (sp_set): -1 drop, else the
+// list index class + kNumClasses * precision (precision 1 = FP32 integrals,
+// for pairs whose estimate max(F_a, F_b) phi A stays below fp32_bound).
+__device__ __forceinline__ int classify_pair(const ScreenArgs& a, int j, int p, int cls, const PairHdr& h) {
+  if (a.screen == SNK_SCREEN_NONE) return cls;
+  const double* ft = a.ft_shell + (int64_t)j * a.ns;
+  const double fa = ft[h.sa], fb = ft[h.sb];
+  const double bnd = batch_pair_bound(a, j, p, h);
+  const double eK = fmax(fa, fb) * a.phit_b[j] * bnd;
+  if (!((fa * fb * bnd >= a.eps_E) || (eK >= a.eps_K))) return -1;
+  return (a.mixed && eK < a.fp32_bound) ? cls + kNumClasses : cls;
+}
 
-__global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(const PairHdr* __restrict__ pairs,
-                                                                 const double* __restrict__ bound, ClassRanges cr,
-                                                                 const double* __restrict__ ft_shell,
-                                                                 const double* __restrict__ phit_b, int ns,
-                                                                 double eps_E, double eps_K, int screen,
-                                                                 int* __restrict__ counts,
+// Pass 1: per (batch, list) pair counts and primitive-pair counts; marks the
+// shells of every kept pair (their F / G columns).  One block per batch.
+__global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, int* __restrict__ counts,
+                                                                 long long* __restrict__ ppcounts,
                                                                  unsigned char* __restrict__ sflag) {
   const int j = blockIdx.x;
-  const double* ft = ft_shell + (int64_t)j * ns;
-  const double phib = phit_b[j];
-  unsigned char* fl = sflag + (int64_t)j * ns;
+  unsigned char* fl = sflag + (int64_t)j * a.ns;
+  __shared__ int s_cnt[kNumLists];
+  __shared__ unsigned long long s_pp[kNumLists];
+  if (threadIdx.x < kNumLists) {
+    s_cnt[threadIdx.x] = 0;
+    s_pp[threadIdx.x] = 0ull;
+  }
+  __syncthreads();
   for (int c = 0; c < kNumClasses; ++c) {
-    int total = 0;
-    for (int base = cr.b[c]; base < cr.b[c + 1]; base += SCR_THREADS) {
-      const int p = base + threadIdx.x;
-      bool k = false;
-      if (p < cr.b[c + 1]) {
-        const PairHdr h = pairs[p];
-        k = keep_pair(h, bound[p], ft, phib, eps_E, eps_K, screen);
-        if (k) {
-          fl[h.sa] = 1;
-          fl[h.sb] = 1;
-        }
+    int n[2] = {0, 0};
+    unsigned long long pp[2] = {0ull, 0ull};
+    for (int p = a.cr.b[c] + threadIdx.x; p < a.cr.b[c + 1]; p += SCR_THREADS) {
+      const PairHdr h = a.pairs[p];
+      const int li = classify_pair(a, j, p, c, h);
+      if (li >= 0) {
+        fl[h.sa] = 1;
+        fl[h.sb] = 1;
+        const int prec = li >= kNumClasses;
+        n[prec] += 1;
+        pp[prec] += (unsigned long long)h.pp_n;
       }
-      total += __syncthreads_count(k);
     }
-    if (threadIdx.x == 0) counts[j * kNumClasses + c] = total;
+    for (int prec = 0; prec < 2; ++prec) {
+      if (n[prec]) {
+        atomicAdd(&s_cnt[c + kNumClasses * prec], n[prec]);
+        atomicAdd(&s_pp[c + kNumClasses * prec], pp[prec]);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumLists) {
+    counts[j * kNumLists + threadIdx.x] = s_cnt[threadIdx.x];
+    ppcounts[j * kNumLists + threadIdx.x] = (long long)s_pp[threadIdx.x];
   }
 }
 
-__global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(const PairHdr* __restrict__ pairs,
-                                                                 const double* __restrict__ bound, ClassRanges cr,
-                                                                 const double* __restrict__ ft_shell,
-                                                                 const double* __restrict__ phit_b, int ns,
-                                                                 double eps_E, double eps_K, int screen,
-                                                                 const int64_t* __restrict__ list_off,
+// Pass 2: deterministic compaction (pair order kept) into the per-(batch, list)
+// ranges that the host sized from pass 1.
+__global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, const int64_t* __restrict__ list_off,
                                                                  int* __restrict__ list) {
   const int j = blockIdx.x;
-  const double* ft = ft_shell + (int64_t)j * ns;
-  const double phib = phit_b[j];
-  __shared__ int warp_tot[SCR_THREADS / 32];
+  __shared__ int warp_tot[2][SCR_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = 0; c < kNumClasses; ++c) {
-    int64_t out = list_off[j * kNumClasses + c];
-    for (int base = cr.b[c]; base < cr.b[c + 1]; base += SCR_THREADS) {
+    int64_t out[2] = {list_off[j * kNumLists + c], list_off[j * kNumLists + c + kNumClasses]};
+    for (int base = a.cr.b[c]; base < a.cr.b[c + 1]; base += SCR_THREADS) {
       const int p = base + threadIdx.x;
-      bool k = false;
-      if (p < cr.b[c + 1]) k = keep_pair(pairs[p], bound[p], ft, phib, eps_E, eps_K, screen);
-      const unsigned bal = __ballot_sync(0xffffffffu, k);
-      if (lane == 0) warp_tot[warp] = __popc(bal);
-      __syncthreads();
-      int before = 0, total = 0;
-      for (int q = 0; q < SCR_THREADS / 32; ++q) {
-        before += q < warp ? warp_tot[q] : 0;
-        total += warp_tot[q];
+      int li = -1;
+      if (p < a.cr.b[c + 1]) li = classify_pair(a, j, p, c, a.pairs[p]);
+      const unsigned bal[2] = {__ballot_sync(0xffffffffu, li >= 0 && li < kNumClasses),
+                               __ballot_sync(0xffffffffu, li >= kNumClasses)};
+      if (lane == 0) {
+        warp_tot[0][warp] = __popc(bal[0]);
+        warp_tot[1][warp] = __popc(bal[1]);
       }
-      if (k) list[out + before + __popc(bal & ((1u << lane) - 1u))] = p;
-      out += total;
+      __syncthreads();
+      for (int prec = 0; prec < 2; ++prec) {
+        int before = 0, total = 0;
+        for (int q = 0; q < SCR_THREADS / 32; ++q) {
+          before += q < warp ? warp_tot[prec][q] : 0;
+          total += warp_tot[prec][q];
+        }
+        if (li >= 0 && (li >= kNumClasses) == (prec == 1))
+          list[out[prec] + before + __popc(bal[prec] & ((1u << lane) - 1u))] = p;
+        out[prec] += total;
+      }
       __syncthreads();
     }
   }
@@ -286,12 +319,14 @@ __global__ void __launch_bounds__(GEMM_THREADS) fgemm_kernel(const BatchDesc* __
                                                              const int* __restrict__ xfunc,
                                                              const int* __restrict__ sfunc,
                                                              const double* __restrict__ fcomp,
-                                                             const double* __restrict__ w, double* __restrict__ ws) {
+                                                             const double* __restrict__ w, double* __restrict__ ws,
+                                                             float* __restrict__ ws32) {
   const BatchDesc bd = batches[blockIdx.z];
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   if (m0 >= bd.ldq || n0 >= bd.nS) return;
   const double* X = ws + bd.xoff;
   double* F = ws + bd.foff;
+  float* F32 = ws32 ? ws32 + bd.foff32 : nullptr;  // mixed form: FP32 copy for the FP32 pairs
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   gemm_tile(
@@ -299,9 +334,17 @@ __global__ void __launch_bounds__(GEMM_THREADS) fgemm_kernel(const BatchDesc* __
       [&](int k, int n) { return P[(int64_t)xf[k] * nf + sf[n]]; },
       [&](int m, int n, double c) {
         const double wi = m < bd.q ? w[bd.p0 + m] : 0.0;
-        F[(int64_t)n * bd.ldq + m] = wi * fcomp[sf[n]] * c;
+        const double v = wi * fcomp[sf[n]] * c;
+        F[(int64_t)n * bd.ldq + m] = v;
+        if (F32) F32[(int64_t)n * bd.ldq + m] = (float)v;
       },
       false, false);
+}
+
+// G += G32 over a chunk's contiguous G region (mixed form).
+__global__ void merge_g32_kernel(const float* __restrict__ g32, int64_t n, double* __restrict__ g64) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    g64[e] += (double)g32[e];
 }
 
 // Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the global N_b x N_b
@@ -389,34 +432,32 @@ cudaError_t launch_ftilde(cudaStream_t st, const double* P, const double* phit_f
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_count(cudaStream_t st, const PairHdr* pairs, const double* bound, const int* class_begin,
-                              const double* ft_shell, const double* phit_b, int ns, int nbatch, double eps_E,
-                              double eps_K, int screen, int* counts, unsigned char* sflag) {
+cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, int* counts, long long* ppcounts,
+                              unsigned char* sflag) {
   if (nbatch == 0) return cudaSuccess;
-  ClassRanges cr;
-  for (int c = 0; c <= kNumClasses; ++c) cr.b[c] = class_begin[c];
-  pair_count_kernel<<<nbatch, SCR_THREADS, 0, st>>>(pairs, bound, cr, ft_shell, phit_b, ns, eps_E, eps_K, screen,
-                                                    counts, sflag);
+  pair_count_kernel<<<nbatch, SCR_THREADS, 0, st>>>(a, counts, ppcounts, sflag);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_write(cudaStream_t st, const PairHdr* pairs, const double* bound, const int* class_begin,
-                              const double* ft_shell, const double* phit_b, int ns, int nbatch, double eps_E,
-                              double eps_K, int screen, const int64_t* list_off, int* list) {
+cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list) {
   if (nbatch == 0) return cudaSuccess;
-  ClassRanges cr;
-  for (int c = 0; c <= kNumClasses; ++c) cr.b[c] = class_begin[c];
-  pair_write_kernel<<<nbatch, SCR_THREADS, 0, st>>>(pairs, bound, cr, ft_shell, phit_b, ns, eps_E, eps_K, screen,
-                                                    list_off, list);
+  pair_write_kernel<<<nbatch, SCR_THREADS, 0, st>>>(a, list_off, list);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, int nf, const int* xfunc, const int* sfunc, const double* fcomp,
-                         const double* w, double* ws) {
+                         const double* w, double* ws, float* ws32) {
   if (nbatch == 0 || max_ldq == 0 || max_nS == 0) return cudaSuccess;
   dim3 grid((max_ldq + TM - 1) / TM, (max_nS + TN - 1) / TN, nbatch);
-  fgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, nf, xfunc, sfunc, fcomp, w, ws);
+  fgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, nf, xfunc, sfunc, fcomp, w, ws, ws32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  merge_g32_kernel<<<blocks, 256, 0, st>>>(g32, n, g64);
   return cudaGetLastError();
 }
 

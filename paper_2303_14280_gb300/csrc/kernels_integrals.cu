@@ -161,6 +161,168 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- FP32 pairs (mixed form)
+
+// FP32 seeds S_n = pref F_n(T): 6-term Taylor about the nearest node of a
+// 0.1-spaced float table below T = 30 (truncation < 3e-11), the asymptotic
+// form above (e^{-T} < 1e-13 is below FP32 resolution).
+template <int L>
+__device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_far, const float* tab, float* S) {
+  if (T < kBoysTMaxF) {
+    const int k = __float2int_rn(T * (float)(1.0 / kBoysH));
+    const float* row = tab + k * kBoysColsF;
+    const float x = row[kBoysColsF - 1] - T;
+    float f = row[kBoysTermsF - 1];
+#pragma unroll
+    for (int m = kBoysTermsF - 2; m >= 0; --m) f = fmaf(f, x, row[m]);
+    S[L] = pref * f;
+    if (L > 0) {
+      float e = 1.0f / 120.0f;
+      e = fmaf(e, x, 1.0f / 24.0f);
+      e = fmaf(e, x, 1.0f / 6.0f);
+      e = fmaf(e, x, 0.5f);
+      e = fmaf(e, x, 1.0f);
+      e = fmaf(e, x, 1.0f);
+      const float pe = (pref * row[kBoysTermsF]) * e;
+      const float T2 = T + T;
+#pragma unroll
+      for (int n = L - 1; n >= 0; --n) S[n] = fmaf(T2, S[n + 1], pe) * (1.0f / (2 * n + 1));
+    }
+  } else {
+    const float r = rsqrtf(T);
+    S[0] = pref_far * r;
+    if (L > 0) {
+      const float o = 0.5f * (r * r);
+#pragma unroll
+      for (int n = 0; n < L; ++n) S[n + 1] = S[n] * ((2 * n + 1) * o);
+    }
+  }
+}
+
+// Primitive pair in FP32, its product centre relative to the batch centre.
+struct PrimPairF {
+  float zeta, Rx, Ry, Rz, PAx, PAy, PAz, pref, pref_far, k1, k2, k3;
+};
+
+// Same decomposition as integral_kernel, FP32 arithmetic: points and product
+// centres are taken relative to the batch centre (differences formed in FP64
+// once per tile) so that T = zeta |P - r|^2 keeps FP32 relative accuracy; F is
+// read from the FP32 copy and G accumulates into the FP32 buffer, which the
+// driver adds into the FP64 G before the K product.
+template <int LA, int LB>
+__global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
+  using C = OsClass<LA, LB>;
+  constexpr int NA = C::NA, NB = C::NB;
+  extern __shared__ float s_f[];
+  float* s_tab = s_f;
+  PrimPairF* s_pp = reinterpret_cast<PrimPairF*>(s_f + kBoysRowsF * kBoysColsF);
+  const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
+  for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tab[e] = gtab[e];
+  __shared__ float s_ab[3];
+  __shared__ int s_tile;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= a.n_tiles) break;
+    const Tile tile = a.tiles[t];
+    const BatchDesc bd = a.batches[tile.batch];
+    const int i = tile.i0 + threadIdx.x;
+    const bool active = i < bd.q;
+    const double ox = a.bcenter[3 * tile.batch], oy = a.bcenter[3 * tile.batch + 1], oz = a.bcenter[3 * tile.batch + 2];
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    if (active) {
+      cx = (float)(a.xyz[3 * (bd.p0 + i)] - ox);
+      cy = (float)(a.xyz[3 * (bd.p0 + i) + 1] - oy);
+      cz = (float)(a.xyz[3 * (bd.p0 + i) + 2] - oz);
+    }
+    const int64_t ldq = bd.ldq;
+    const float* F = a.ws32 + bd.foff32 + i;
+    float* G = a.ws32 + bd.goff32 + i;
+    const int* cmap = a.colmap + (int64_t)tile.batch * a.ns;
+    float ga[NA], fa[NA];
+    int cur = -1, cola = 0;
+    for (int k = tile.k0; k < tile.k1; ++k) {
+      const PairHdr h = a.pairs[a.pairlist[k]];
+      __syncthreads();  // the previous pair's staged primitives are consumed
+      for (int q = threadIdx.x; q < h.pp_n; q += blockDim.x) {
+        const PrimPair pp = a.prims[h.pp_off + q];
+        PrimPairF f;
+        f.zeta = (float)pp.zeta;
+        f.Rx = (float)(pp.Px - ox);
+        f.Ry = (float)(pp.Py - oy);
+        f.Rz = (float)(pp.Pz - oz);
+        f.PAx = (float)pp.PAx;
+        f.PAy = (float)pp.PAy;
+        f.PAz = (float)pp.PAz;
+        f.pref = (float)pp.pref;
+        f.pref_far = (float)pp.pref_far;
+        f.k1 = (float)pp.k1;
+        f.k2 = (float)pp.k2;
+        f.k3 = (float)pp.k3;
+        s_pp[q] = f;
+      }
+      if (threadIdx.x == 0) {
+        s_ab[0] = (float)h.ABx;
+        s_ab[1] = (float)h.ABy;
+        s_ab[2] = (float)h.ABz;
+      }
+      __syncthreads();
+      if (!active) continue;
+      if (h.sa != cur) {
+        if (cur >= 0) {
+#pragma unroll
+          for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
+        }
+        cur = h.sa;
+        cola = cmap[cur];
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          ga[u] = 0.f;
+          fa[u] = F[(cola + u) * ldq];
+        }
+      }
+      const int colb = cmap[h.sb];
+      if (cola < 0 || colb < 0) continue;  // cannot happen: the screen marks both shells of a kept pair
+      float fb[NB];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) fb[v] = F[(colb + v) * ldq];
+      float acc[C::NACC];
+#pragma unroll
+      for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
+      for (int q = 0; q < h.pp_n; ++q) {
+        const PrimPairF pp = s_pp[q];
+        const float PCx = pp.Rx - cx, PCy = pp.Ry - cy, PCz = pp.Rz - cz;
+        const float T = pp.zeta * fmaf(PCx, PCx, fmaf(PCy, PCy, PCz * PCz));
+        float S[C::L + 1];
+        boys_seeds_f32<C::L>(T, pp.pref, pp.pref_far, s_tab, S);
+        C::vrr(S, pp.PAx, pp.PAy, pp.PAz, PCx, PCy, PCz, pp.k1, pp.k2, pp.k3, acc);
+      }
+      float xi[NA * NB];
+      C::hrr(acc, s_ab[0], s_ab[1], s_ab[2], xi);
+#pragma unroll
+      for (int u = 0; u < NA; ++u)
+#pragma unroll
+        for (int v = 0; v < NB; ++v) ga[u] = fmaf(xi[u * NB + v], fb[v], ga[u]);
+      if (h.sa != h.sb) {
+#pragma unroll
+        for (int v = 0; v < NB; ++v) {
+          float g = 0.f;
+#pragma unroll
+          for (int u = 0; u < NA; ++u) g = fmaf(xi[u * NB + v], fa[u], g);
+          atomicAdd(G + (colb + v) * ldq, g);
+        }
+      }
+    }
+    if (active && cur >= 0) {
+#pragma unroll
+      for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
+    }
+  }
+}
+
 template <int LA, int LB>
 __global__ void debug_xi_kernel(const PairHdr* pair, const PrimPair* prims, const double* boys, int64_t n,
                                 const double* xyz, double* out) {
@@ -193,50 +355,67 @@ __global__ void debug_boys_kernel(const double* boys, int64_t n, const double* T
   }
 }
 
+constexpr size_t kSmem64 = sizeof(double) * kBoysRows * kBoysCols;
+constexpr size_t kSmem32 = sizeof(float) * kBoysRowsF * kBoysColsF + sizeof(PrimPairF) * 256;
+
+// list < kNumClasses: FP64 kernel of that class; otherwise the FP32 kernel of
+// class list - kNumClasses.
 template <int LA, int LB>
-cudaError_t launch_class(cudaStream_t st, const IntegralArgs& a, int grid) {
-  const size_t smem = sizeof(double) * kBoysRows * kBoysCols;
-  cudaError_t e = cudaFuncSetAttribute(integral_kernel<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  integral_kernel<LA, LB><<<grid, kIntThreads, smem, st>>>(a);
+cudaError_t launch_class(cudaStream_t st, bool f32, const IntegralArgs& a, int grid) {
+  if (f32) {
+    cudaError_t e =
+        cudaFuncSetAttribute(integral_kernel_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
+    if (e != cudaSuccess) return e;
+    integral_kernel_f32<LA, LB><<<grid, kIntThreads, kSmem32, st>>>(a);
+  } else {
+    cudaError_t e =
+        cudaFuncSetAttribute(integral_kernel<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
+    if (e != cudaSuccess) return e;
+    integral_kernel<LA, LB><<<grid, kIntThreads, kSmem64, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
-template <int LA, int LB>
-int max_ctas(int num_sms) {
-  const size_t smem = sizeof(double) * kBoysRows * kBoysCols;
-  cudaFuncSetAttribute(integral_kernel<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <class K>
+int ctas_for(K kernel, size_t smem, int num_sms) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, integral_kernel<LA, LB>, kIntThreads, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kIntThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   return per_sm * num_sms;
 }
 
+template <int LA, int LB>
+int max_ctas(bool f32, int num_sms) {
+  return f32 ? ctas_for(integral_kernel_f32<LA, LB>, kSmem32, num_sms)
+             : ctas_for(integral_kernel<LA, LB>, kSmem64, num_sms);
+}
+
 }  // namespace
 
-cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas) {
+cudaError_t launch_integrals(cudaStream_t st, int list, const IntegralArgs& a, int grid_ctas) {
   if (a.n_tiles == 0) return cudaSuccess;
-  switch (cls) {
-    case 0: return launch_class<0, 0>(st, a, grid_ctas);
-    case 1: return launch_class<1, 0>(st, a, grid_ctas);
-    case 2: return launch_class<1, 1>(st, a, grid_ctas);
-    case 3: return launch_class<2, 0>(st, a, grid_ctas);
-    case 4: return launch_class<2, 1>(st, a, grid_ctas);
-    case 5: return launch_class<2, 2>(st, a, grid_ctas);
+  const bool f32 = list >= kNumClasses;
+  switch (list % kNumClasses) {
+    case 0: return launch_class<0, 0>(st, f32, a, grid_ctas);
+    case 1: return launch_class<1, 0>(st, f32, a, grid_ctas);
+    case 2: return launch_class<1, 1>(st, f32, a, grid_ctas);
+    case 3: return launch_class<2, 0>(st, f32, a, grid_ctas);
+    case 4: return launch_class<2, 1>(st, f32, a, grid_ctas);
+    case 5: return launch_class<2, 2>(st, f32, a, grid_ctas);
   }
   return cudaErrorInvalidValue;
 }
 
-int integral_max_ctas(int cls, int num_sms) {
-  switch (cls) {
-    case 0: return max_ctas<0, 0>(num_sms);
-    case 1: return max_ctas<1, 0>(num_sms);
-    case 2: return max_ctas<1, 1>(num_sms);
-    case 3: return max_ctas<2, 0>(num_sms);
-    case 4: return max_ctas<2, 1>(num_sms);
-    case 5: return max_ctas<2, 2>(num_sms);
+int integral_max_ctas(int list, int num_sms) {
+  const bool f32 = list >= kNumClasses;
+  switch (list % kNumClasses) {
+    case 0: return max_ctas<0, 0>(f32, num_sms);
+    case 1: return max_ctas<1, 0>(f32, num_sms);
+    case 2: return max_ctas<1, 1>(f32, num_sms);
+    case 3: return max_ctas<2, 0>(f32, num_sms);
+    case 4: return max_ctas<2, 1>(f32, num_sms);
+    case 5: return max_ctas<2, 2>(f32, num_sms);
   }
   return num_sms;
 }
@@ -272,7 +451,7 @@ cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, co
 // counted) and the
 // generated VRR; per contracted pair the generated HRR and the G_a
 // contraction (2 NA NB).  The G_b half of off-diagonal pairs is not counted.
-void class_flops(int cls, int nprim_pairs, double* f) {
+void class_flops(int cls, double* per_prim, double* per_pair) {
   int vrr = 0, hrr = 0, L = 0, na = 1, nb = 1;
   switch (cls) {
 #define SNK_CASE(c, A, B)          \
@@ -292,7 +471,8 @@ void class_flops(int cls, int nprim_pairs, double* f) {
 #undef SNK_CASE
   }
   const double boys = L == 0 ? 1.0 : 3.0 + 2.0 * L;
-  *f = nprim_pairs * (8.0 + boys + vrr) + hrr + 2.0 * na * nb;
+  *per_prim = 8.0 + boys + vrr;
+  *per_pair = hrr + 2.0 * na * nb;
 }
 
 }  // namespace snk

@@ -40,7 +40,7 @@ struct DevBuf {
 
 // pairs per integral tile for each class: cheap classes take longer runs
 constexpr int kPairsPerTile[kNumClasses] = {64, 32, 16, 16, 8, 8};
-constexpr int kPhaseEvents = 3 + kNumClasses;  // per chunk: collocation, F GEMM, classes, K GEMM
+constexpr int kPhaseEvents = 3 + kNumLists;  // per chunk: collocation, F GEMM, integral lists, K GEMM
 
 }  // namespace
 
@@ -55,7 +55,8 @@ struct snk_ctx {
 
   // geometry (device)
   DevBuf<int> l, poff, nprim, foff, fshell, bshell, bshell_col, xfunc;
-  DevBuf<double> center, exps, d, fcomp, xyz, w, boys, bound, phit_f, phit_b;
+  DevBuf<double> center, exps, d, fcomp, xyz, w, boys, bound, qbound, bcenter, bradius, phit_f, phit_b;
+  DevBuf<float> boys_f;
   DevBuf<PairHdr> pairs;
   DevBuf<PrimPair> prims;
 
@@ -63,22 +64,25 @@ struct snk_ctx {
   bool have_density = false;
   DevBuf<double> P, ft, sym, Khat, K;
   DevBuf<int> counts, list, sfunc, colmap, tickets;
+  DevBuf<long long> ppcounts;
   DevBuf<unsigned char> sflag;
   DevBuf<int64_t> list_off;
   DevBuf<BatchDesc> batch;
   DevBuf<Tile> tiles;
   DevBuf<double> ws;
+  DevBuf<float> ws32;
   std::vector<int> hcounts;
+  std::vector<long long> hpp;
   std::vector<int64_t> hlist_off;
 
   struct Chunk {
     int b0 = 0, b1 = 0;
-    int64_t bytes = 0, goff = 0, gbytes = 0;
+    int64_t bytes = 0, goff = 0, gbytes = 0, g32off = 0, g32n = 0;
     int max_ldq = 0, max_nS = 0, max_nB = 0, max_nBshell = 0;
-    int64_t tile_off[kNumClasses] = {0}, tile_n[kNumClasses] = {0};
+    int64_t tile_off[kNumLists] = {0}, tile_n[kNumLists] = {0};
   };
   std::vector<Chunk> chunks;
-  int max_ctas[kNumClasses] = {0};
+  int max_ctas[kNumLists] = {0};
 
   // timing
   std::vector<cudaEvent_t> events;
@@ -197,6 +201,7 @@ int screen_and_plan(snk_ctx* c) {
   Setup& s = c->s;
   const int nb = c->nbatch, ns = s.ns, nf = s.nf;
   const cudaStream_t st = c->stream;
+  const bool mixed = c->opt.precision == SNK_PREC_MIXED;
   c->have_density = false;
   c->launches_density = 0;
   SNK_CK(c, cudaEventRecord(c->ev_screen0, st));
@@ -214,7 +219,8 @@ int screen_and_plan(snk_ctx* c) {
   const int nbx = std::max(nb, 1);
   // F-tilde and the pair screen, Eqs. (exx_fmat_approx), (sp_set)
   SNK_CK(c, c->ft.ensure((size_t)nbx * ns));
-  SNK_CK(c, c->counts.ensure((size_t)nbx * kNumClasses));
+  SNK_CK(c, c->counts.ensure((size_t)nbx * kNumLists));
+  SNK_CK(c, c->ppcounts.ensure((size_t)nbx * kNumLists));
   SNK_CK(c, c->sflag.ensure((size_t)nbx * ns));
   SNK_CK(c, cudaMemsetAsync(c->ft.p, 0, sizeof(double) * nbx * ns, st));
   SNK_CK(c, cudaMemsetAsync(c->sflag.p, 0, (size_t)nbx * ns, st));
@@ -223,39 +229,54 @@ int screen_and_plan(snk_ctx* c) {
     SNK_CK(c, launch_ftilde(st, c->P.p, c->phit_f.p, nf, nb, c->fshell.p, ns, c->ft.p));
     ++c->launches_density;
   }
-  SNK_CK(c, launch_pair_count(st, c->pairs.p, c->bound.p, s.class_begin, c->ft.p, c->phit_b.p, ns, nb, c->opt.eps_E,
-                              c->opt.eps_K, screen, c->counts.p, c->sflag.p));
+  ScreenArgs sa;
+  sa.pairs = c->pairs.p;
+  sa.bound = c->bound.p;
+  sa.qbound = c->qbound.p;
+  sa.shell_xyz = c->center.p;
+  sa.bcenter = c->bcenter.p;
+  sa.bradius = c->bradius.p;
+  sa.ft_shell = c->ft.p;
+  sa.phit_b = c->phit_b.p;
+  sa.ns = ns;
+  sa.screen = screen;
+  sa.distance = c->opt.distance_bound ? 1 : 0;
+  sa.mixed = mixed ? 1 : 0;
+  sa.eps_E = c->opt.eps_E;
+  sa.eps_K = c->opt.eps_K;
+  sa.fp32_bound = c->opt.fp32_bound;
+  for (int k = 0; k <= kNumClasses; ++k) sa.cr.b[k] = s.class_begin[k];
+  SNK_CK(c, launch_pair_count(st, sa, nb, c->counts.p, c->ppcounts.p, c->sflag.p));
   ++c->launches_density;
-  c->hcounts.assign((size_t)nbx * kNumClasses, 0);
+  c->hcounts.assign((size_t)nbx * kNumLists, 0);
+  c->hpp.assign((size_t)nbx * kNumLists, 0);
   std::vector<unsigned char> hflag((size_t)nbx * ns);
-  SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumClasses, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumLists, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(c->hpp.data(), c->ppcounts.p, sizeof(long long) * nbx * kNumLists, cudaMemcpyDeviceToHost,
+                            st));
   SNK_CK(c, cudaMemcpyAsync(hflag.data(), c->sflag.p, (size_t)nbx * ns, cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
   // pair lists: offsets, then the deterministic compaction pass
-  c->hlist_off.assign((size_t)nbx * kNumClasses + 1, 0);
+  c->hlist_off.assign((size_t)nbx * kNumLists + 1, 0);
   int64_t tot = 0;
   for (int j = 0; j < nb; ++j)
-    for (int k = 0; k < kNumClasses; ++k) {
-      c->hlist_off[(size_t)j * kNumClasses + k] = tot;
-      tot += c->hcounts[(size_t)j * kNumClasses + k];
+    for (int k = 0; k < kNumLists; ++k) {
+      c->hlist_off[(size_t)j * kNumLists + k] = tot;
+      tot += c->hcounts[(size_t)j * kNumLists + k];
     }
-  c->hlist_off[(size_t)nb * kNumClasses] = tot;
+  c->hlist_off[(size_t)nb * kNumLists] = tot;
   if (tot > (int64_t)0x7fffffff)
     return fail(c, SNK_ERR_UNSUPPORTED, "more than 2^31 screened (batch, pair) entries: tighten the screen");
   SNK_CK(c, c->list.ensure((size_t)std::max<int64_t>(tot, 1)));
   SNK_CK(c, upload(c->list_off, c->hlist_off, st));
-  SNK_CK(c, launch_pair_write(st, c->pairs.p, c->bound.p, s.class_begin, c->ft.p, c->phit_b.p, ns, nb, c->opt.eps_E,
-                              c->opt.eps_K, screen, c->list_off.p, c->list.p));
+  SNK_CK(c, launch_pair_write(st, sa, nb, c->list_off.p, c->list.p));
   ++c->launches_density;
 
-  // shells of V_j -> F / G columns; batch descriptors; chunks (Alg. 1)
+  // shells of V_j -> F / G columns; batch descriptors
   std::vector<int> hcolmap((size_t)nbx * ns, -1), hsfunc;
   std::vector<BatchDesc> bd(nbx);
   c->chunks.clear();
-  int64_t pair_points = 0, kept = 0;
-  double integrals = 0.0, iflops = 0.0, gflops = 0.0;
-  double icls[kNumClasses] = {0}, fcls[kNumClasses] = {0};
   for (int j = 0; j < nb; ++j) {
     BatchDesc& b = bd[j];
     b = BatchDesc{};
@@ -275,96 +296,93 @@ int screen_and_plan(snk_ctx* c) {
         col += ncart(s.l[a]);
       }
     b.nS = col;
-    for (int k = 0; k < kNumClasses; ++k) {
-      int64_t n = c->hcounts[(size_t)j * kNumClasses + k];
-      kept += n;
-      pair_points += n * b.q;
-    }
-    gflops += 2.0 * b.q * (double)b.nB * b.nS * 2.0;
   }
-  // integral counts and algorithmic flops: walk the kept pairs per class
-  // (counts only: the lists stay on the device; all pairs of a class share nprim
-  // in practice, otherwise the class's mean primitive-pair count is used)
-  for (int k = 0; k < kNumClasses; ++k) {
-    int la = 0, lb = 0;
-    for (int x = 0; x <= 2; ++x)
-      for (int y = 0; y <= x; ++y)
-        if (class_of(x, y) == k) {
-          la = x;
-          lb = y;
-        }
-    double npp = 0.0;
-    int cnt = s.class_begin[k + 1] - s.class_begin[k];
-    for (int p = s.class_begin[k]; p < s.class_begin[k + 1]; ++p) npp += s.pairs[p].pp_n;
-    double mean_np = cnt ? npp / cnt : 1.0;
-    double f;
-    class_flops(k, (int)std::lround(mean_np), &f);
-    for (int j = 0; j < nb; ++j) {
-      double pp = (double)c->hcounts[(size_t)j * kNumClasses + k] * bd[j].q;
-      icls[k] += pp * ncart(la) * ncart(lb);
-      fcls[k] += pp * f;
+  // counts for the statistics: integrals and algorithmic flops per list
+  double per_prim[kNumClasses], per_pair[kNumClasses];
+  for (int k = 0; k < kNumClasses; ++k) class_flops(k, &per_prim[k], &per_pair[k]);
+  double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0;
+  int64_t kept[2] = {0, 0}, pair_points = 0;
+  for (int j = 0; j < nb; ++j) {
+    gflops += 4.0 * bd[j].q * (double)bd[j].nB * bd[j].nS;
+    for (int k = 0; k < kNumLists; ++k) {
+      const int cls = k % kNumClasses;
+      const int la = cls >= 3 ? 2 : (cls >= 1 ? 1 : 0), lb = cls - la * (la + 1) / 2;
+      const double n = c->hcounts[(size_t)j * kNumLists + k], npp = (double)c->hpp[(size_t)j * kNumLists + k];
+      lint[k] += n * bd[j].q * ncart(la) * ncart(lb);
+      lflops[k] += (npp * per_prim[cls] + n * per_pair[cls]) * bd[j].q;
+      kept[k >= kNumClasses] += (int64_t)n;
+      pair_points += (int64_t)n * bd[j].q;
     }
-    integrals += icls[k];
-    iflops += fcls[k];
   }
   SNK_CK(c, upload(c->colmap, hcolmap, st));
   if (hsfunc.empty()) hsfunc.push_back(0);
   SNK_CK(c, upload(c->sfunc, hsfunc, st));
 
-  // chunks under the workspace budget
+  // chunks under the workspace budget (Alg. 1): X, F, G in doubles, plus the
+  // FP32 copies of F and G in the mixed form
   int j = 0;
+  int64_t need = 1, need32 = 1;
   while (j < nb) {
     snk_ctx::Chunk ch;
     ch.b0 = j;
     int64_t xo = 0, fo = 0;
-    std::vector<int> members;
     while (j < nb) {
       int64_t xs = (int64_t)bd[j].ldq * bd[j].nB, fs = (int64_t)bd[j].ldq * bd[j].nS;
-      if (j > ch.b0 && (xo + xs + 2 * (fo + fs)) * 8 > c->ws_budget) break;
+      int64_t bytes = (xo + xs + 2 * (fo + fs)) * 8 + (mixed ? 2 * (fo + fs) * 4 : 0);
+      if (j > ch.b0 && bytes > c->ws_budget) break;
       xo += xs;
       fo += fs;
       ++j;
     }
     ch.b1 = j;
-    int64_t xcur = 0, fcur = xo, gcur = xo + fo;
+    int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0, g32cur = fo;
     ch.goff = gcur;
     ch.gbytes = fo * 8;
+    ch.g32off = g32cur;
+    ch.g32n = mixed ? fo : 0;
     for (int t = ch.b0; t < ch.b1; ++t) {
+      const int64_t fs = (int64_t)bd[t].ldq * bd[t].nS;
       bd[t].xoff = xcur;
       xcur += (int64_t)bd[t].ldq * bd[t].nB;
       bd[t].foff = fcur;
       bd[t].goff = gcur;
-      fcur += (int64_t)bd[t].ldq * bd[t].nS;
-      gcur += (int64_t)bd[t].ldq * bd[t].nS;
+      bd[t].foff32 = f32cur;
+      bd[t].goff32 = g32cur;
+      fcur += fs;
+      gcur += fs;
+      f32cur += fs;
+      g32cur += fs;
       ch.max_ldq = std::max(ch.max_ldq, bd[t].ldq);
       ch.max_nS = std::max(ch.max_nS, bd[t].nS);
       ch.max_nB = std::max(ch.max_nB, bd[t].nB);
       ch.max_nBshell = std::max(ch.max_nBshell, bd[t].nBshell);
     }
     ch.bytes = (xo + 2 * fo) * 8;
+    need = std::max(need, xo + 2 * fo);
+    if (mixed) need32 = std::max(need32, 2 * fo);
     c->chunks.push_back(ch);
   }
-  int64_t need = 1;
-  for (auto& ch : c->chunks) need = std::max(need, ch.bytes / 8);
   SNK_CK(c, c->ws.ensure((size_t)need));
+  if (mixed) SNK_CK(c, c->ws32.ensure((size_t)need32));
   SNK_CK(c, upload(c->batch, bd, st));
 
-  // integral tiles per (chunk, class): (batch, pair run, 128-point slab),
+  // integral tiles per (chunk, list): (batch, pair run, 128-point slab),
   // larger runs first so that the persistent CTAs finish together
   std::vector<Tile> htiles;
   for (auto& ch : c->chunks)
-    for (int k = 0; k < kNumClasses; ++k) {
+    for (int k = 0; k < kNumLists; ++k) {
       ch.tile_off[k] = (int64_t)htiles.size();
       size_t first = htiles.size();
+      const int run = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
       for (int t = ch.b0; t < ch.b1; ++t) {
-        int64_t n = c->hcounts[(size_t)t * kNumClasses + k];
-        int64_t base = c->hlist_off[(size_t)t * kNumClasses + k];
-        for (int64_t k0 = 0; k0 < n; k0 += kPairsPerTile[k])
+        int64_t n = c->hcounts[(size_t)t * kNumLists + k];
+        int64_t base = c->hlist_off[(size_t)t * kNumLists + k];
+        for (int64_t k0 = 0; k0 < n; k0 += run)
           for (int i0 = 0; i0 < bd[t].q; i0 += kPointTile) {
             Tile tl;
             tl.batch = t;
             tl.k0 = (int)(base + k0);
-            tl.k1 = (int)(base + std::min<int64_t>(n, k0 + kPairsPerTile[k]));
+            tl.k1 = (int)(base + std::min<int64_t>(n, k0 + run));
             tl.i0 = i0;
             htiles.push_back(tl);
           }
@@ -378,26 +396,31 @@ int screen_and_plan(snk_ctx* c) {
     }
   if (htiles.empty()) htiles.push_back(Tile{0, 0, 0, 0});
   SNK_CK(c, upload(c->tiles, htiles, st));
-  SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumClasses + 1));
+  SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
   SNK_CK(c, c->Khat.ensure((size_t)nf * nf));
   SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
-  c->st.n_batches = nb;
-  c->st.pairs_kept = kept;
-  c->st.pair_points = pair_points;
-  c->st.integrals = integrals;
-  c->st.integral_flops = iflops;
-  c->st.gemm_flops = gflops;
+  snk_stats& S = c->st;
+  S.n_batches = nb;
+  S.pairs_kept = kept[0] + kept[1];
+  S.pairs_kept_fp32 = kept[1];
+  S.pair_points = pair_points;
+  S.integrals = S.integral_flops = S.integrals_fp32 = S.flops_fp32 = 0.0;
   for (int k = 0; k < kNumClasses; ++k) {
-    c->st.integrals_class[k] = icls[k];
-    c->st.flops_class[k] = fcls[k];
+    S.integrals_class[k] = lint[k];
+    S.flops_class[k] = lflops[k];
+    S.integrals += lint[k] + lint[k + kNumClasses];
+    S.integral_flops += lflops[k];
+    S.integrals_fp32 += lint[k + kNumClasses];
+    S.flops_fp32 += lflops[k + kNumClasses];
   }
-  c->st.n_chunks = (int64_t)c->chunks.size();
-  c->st.workspace_bytes = (int64_t)(c->ws.n * 8);
+  S.gemm_flops = gflops;
+  S.n_chunks = (int64_t)c->chunks.size();
+  S.workspace_bytes = (int64_t)(c->ws.n * 8 + c->ws32.n * 4);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev_screen0, c->ev_screen1);
-  c->st.ms_screen = ms;
+  S.ms_screen = ms;
   c->have_density = true;
   c->built = false;
   return SNK_OK;
@@ -408,6 +431,7 @@ int build(snk_ctx* c, double* dK) {
   Setup& s = c->s;
   const cudaStream_t st = c->stream;
   const int nf = s.nf;
+  const bool mixed = c->opt.precision == SNK_PREC_MIXED;
   const size_t nev = c->chunks.size() * kPhaseEvents + 2;
   if (int rc = ensure_events(c, nev)) return rc;
   c->launches_build = 0;
@@ -426,16 +450,17 @@ int build(snk_ctx* c, double* dK) {
     SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     // F_j = X_j P (w and component factors folded in), Eq. (batch_local_exx)
     SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nf, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
-                           c->ws.p));
+                           c->ws.p, mixed ? c->ws32.p : nullptr));
     ++c->launches_build;
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
+    if (mixed) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
     SNK_CK(c, cudaEventRecord(c->events[ev++], st));
-    // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, class by class
-    for (int k = 0; k < kNumClasses; ++k) {
+    // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, list by list
+    for (int k = 0; k < kNumLists; ++k) {
       IntegralArgs a;
       a.tiles = c->tiles.p + ch.tile_off[k];
       a.n_tiles = (int)ch.tile_n[k];
-      a.ticket = c->tickets.p + ci * kNumClasses + k;
+      a.ticket = c->tickets.p + ci * kNumLists + k;
       a.batches = c->batch.p;
       a.pairlist = c->list.p;
       a.pairs = c->pairs.p;
@@ -445,6 +470,9 @@ int build(snk_ctx* c, double* dK) {
       a.xyz = c->xyz.p;
       a.boys = c->boys.p;
       a.ws = c->ws.p;
+      a.boys_f = c->boys_f.p;
+      a.ws32 = c->ws32.p;
+      a.bcenter = c->bcenter.p;
       if (a.n_tiles > 0) {
         int grid = std::min<int64_t>(c->max_ctas[k], a.n_tiles);
         SNK_CK(c, launch_integrals(st, k, a, grid));
@@ -452,7 +480,11 @@ int build(snk_ctx* c, double* dK) {
       }
       SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     }
-    // Kt += G_j^T X_j, Eq. (usym_k)
+    // the FP32 pairs' G into the FP64 G, then Kt += G_j^T X_j, Eq. (usym_k)
+    if (mixed && ch.g32n > 0) {
+      SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
+      ++c->launches_build;
+    }
     SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, nf, c->ws.p, c->Khat.p));
     ++c->launches_build;
     SNK_CK(c, cudaEventRecord(c->events[ev++], st));
@@ -475,20 +507,24 @@ void collect_times(snk_ctx* c) {
     return (double)ms;
   };
   snk_stats& st = c->st;
-  st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = 0.0;
+  st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = st.ms_integrals_fp32 = 0.0;
   for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = 0.0;
   int ev = 0;
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
-    int e0 = ev;  // previous boundary
+    const int e0 = ev;  // previous boundary
     st.ms_collocation += el(e0, e0 + 1);
     st.ms_fgemm += el(e0 + 1, e0 + 2);
-    for (int k = 0; k < kNumClasses; ++k) {
-      double t = el(e0 + 2 + k, e0 + 3 + k);
-      st.ms_integrals_class[k] += t;
-      st.ms_integrals += t;
+    for (int k = 0; k < kNumLists; ++k) {
+      const double t = el(e0 + 2 + k, e0 + 3 + k);
+      if (k < kNumClasses) {
+        st.ms_integrals_class[k] += t;
+        st.ms_integrals += t;
+      } else {
+        st.ms_integrals_fp32 += t;
+      }
     }
-    st.ms_kgemm += el(e0 + 2 + kNumClasses, e0 + 3 + kNumClasses);
-    ev = e0 + 3 + kNumClasses;
+    st.ms_kgemm += el(e0 + 2 + kNumLists, e0 + 3 + kNumLists);
+    ev = e0 + 3 + kNumLists;
   }
   st.ms_finish = el(ev, ev + 1);
   st.ms_build = el(0, ev + 1);
@@ -510,6 +546,7 @@ void snk_options_default(snk_options* o) {
   o->screen = SNK_SCREEN_LINK;
   o->fp32_bound = 1e-6;
   o->workspace_bytes = 0;
+  o->distance_bound = 1;
 }
 
 const char* snk_status_string(int status) {
@@ -574,6 +611,10 @@ int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* 
          SNK_CK(cp, upload(cp->pairs, s.pairs, st));
          SNK_CK(cp, upload(cp->prims, s.prims, st));
          SNK_CK(cp, upload(cp->bound, s.bound, st));
+         SNK_CK(cp, upload(cp->qbound, s.qbound, st));
+         SNK_CK(cp, upload(cp->bcenter, s.bcenter, st));
+         SNK_CK(cp, upload(cp->bradius, s.bradius, st));
+         SNK_CK(cp, upload(cp->boys_f, s.boys_f, st));
          SNK_CK(cp, upload(cp->xyz, s.xyz, st));
          SNK_CK(cp, upload(cp->w, s.w, st));
          SNK_CK(cp, upload(cp->bshell, s.bshell, st));
@@ -585,7 +626,7 @@ int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* 
        }()) != SNK_OK)
     return rc;
   if ((rc = geometry_screen(cp)) != SNK_OK) return rc;
-  for (int k = 0; k < kNumClasses; ++k) cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms);
+  for (int k = 0; k < kNumLists; ++k) cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms);
   std::memset(&cp->st, 0, sizeof(cp->st));
   cp->st.n_points = s.npts;
   cp->st.n_batches = cp->nbatch;

@@ -13,6 +13,7 @@ namespace snk {
 
 constexpr int kLMax = 2;
 constexpr int kNumClasses = 6;  // (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+constexpr int kNumLists = 2 * kNumClasses;  // per batch: FP64 lists, then FP32 lists
 constexpr int kPointTile = 128;  // grid points per integral tile (one per thread)
 constexpr int kLdqAlign = 128;   // leading-dimension padding of batch matrices
 
@@ -25,6 +26,17 @@ constexpr int kBoysRows = 502;
 constexpr int kBoysTerms = 8;
 constexpr int kBoysCols = kBoysTerms + 2;
 constexpr int kBoysLMax = 2 * kLMax;
+
+// FP32 Boys table of the mixed form: T_k = k * kBoysH up to kBoysTMaxF, rows
+// of F_{L+m}(T_k)/m! for m = 0..5, exp(-T_k), T_k.
+constexpr float kBoysTMaxF = 30.0f;
+constexpr int kBoysRowsF = 302;
+constexpr int kBoysTermsF = 6;
+constexpr int kBoysColsF = kBoysTermsF + 2;
+
+// Primitive pairs whose 3c-CP potential is below this everywhere are left out
+// of a shell pair (their total effect on K is below ~1e-14 for any basis here).
+constexpr double kPrimPairTol = 1e-20;
 
 inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 inline int class_of(int la, int lb) {  // la >= lb
@@ -63,6 +75,8 @@ struct BatchDesc {
   int32_t sfunc_off;
   int32_t bshell_off;
   int32_t nBshell;
+  int64_t foff32;    // mixed form: offsets (floats) of the FP32 copies of F and G
+  int64_t goff32;
 };
 
 // Integral-kernel tile: batch, pair-list range, first point.
@@ -82,6 +96,7 @@ struct Setup {
   std::vector<PairHdr> pairs;
   std::vector<PrimPair> prims;
   std::vector<double> bound;          // rigorous max_r |A| per pair
+  std::vector<double> qbound;         // rigorous total |charge| per pair: |A| <= qbound / distance
   std::vector<int> pair_class;
   int class_begin[kNumClasses + 1] = {0};
   std::vector<int> pair_index;        // dense ns x ns -> pair id or -1
@@ -98,12 +113,14 @@ struct Setup {
   std::vector<int> xfunc_off, xfunc;  // B_j as function lists (CSR)
 
   std::vector<double> boys;           // (kBoysLMax+1) x kBoysRows x kBoysCols
+  std::vector<float> boys_f;          // (kBoysLMax+1) x kBoysRowsF x kBoysColsF
 };
 
 // Validates and normalises the basis and grid; returns an snk_status and fills msg.
 int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, Setup* s,
                 std::string* msg);
 double pair_bound(const Setup& s, int sa, int sb);
+void prim_pair_bounds(const Setup& s, int sa, int sb, int k, int m, double* abound, double* qbound);
 void host_boys(int nmax, double T, double* F);
 
 // ---------------------------------------------------------------- kernels
@@ -127,17 +144,34 @@ cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nba
                                double* phit_f, double* phit_b);
 cudaError_t launch_ftilde(cudaStream_t st, const double* P, const double* phit_f, int nf,
                           int nbatch, const int* fshell, int ns, double* ft_shell);
-cudaError_t launch_pair_count(cudaStream_t st, const PairHdr* pairs, const double* bound,
-                              const int* class_begin_host, const double* ft_shell, const double* phit_b,
-                              int ns, int nbatch, double eps_E, double eps_K, int screen,
-                              int* counts, unsigned char* sflag);
-cudaError_t launch_pair_write(cudaStream_t st, const PairHdr* pairs, const double* bound,
-                              const int* class_begin_host, const double* ft_shell, const double* phit_b,
-                              int ns, int nbatch, double eps_E, double eps_K, int screen,
-                              const int64_t* list_off, int* list);
+struct ClassRanges {
+  int b[kNumClasses + 1];
+};
+
+// Inputs of the sn-LinK pair screen (Eqs. sp_set, exx_fmat_approx).
+struct ScreenArgs {
+  const PairHdr* pairs;
+  const double* bound;      // global A-tilde per pair
+  const double* qbound;     // total-charge bound per pair
+  const double* shell_xyz;  // shell centres
+  const double* bcenter;    // batch bounding spheres
+  const double* bradius;
+  const double* ft_shell;   // F-tilde per (batch, shell)
+  const double* phit_b;     // phi-tilde per batch
+  int ns;
+  int screen;               // snk_screen_mode
+  int distance;             // 1: refine A-tilde by charge / distance per batch
+  int mixed;                // 1: route low-estimate pairs to the FP32 lists
+  double eps_E, eps_K, fp32_bound;
+  ClassRanges cr;
+};
+
+cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, int* counts, long long* ppcounts,
+                              unsigned char* sflag);
+cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list);
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, int nf, const int* xfunc, const int* sfunc,
-                         const double* fcomp, const double* w, double* ws);
+                         const double* fcomp, const double* w, double* ws, float* ws32);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
                          const int* xfunc, const int* sfunc, int nf, const double* ws, double* Khat);
 cudaError_t launch_finish(cudaStream_t st, const double* Khat, const double* fcomp, int nf, double* K);
@@ -156,6 +190,10 @@ struct IntegralArgs {
   const double* xyz;  // batch order
   const double* boys; // device table, all L
   double* ws;
+  // mixed form (FP32 lists)
+  const float* boys_f;
+  float* ws32;
+  const double* bcenter;
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
@@ -165,7 +203,10 @@ cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const 
 cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, const double* T,
                               int nmax, double* out);
 
-// FP64 operation counts of the integral kernel per class (from the generator).
-void class_flops(int cls, int nprim_pairs, double* flops_per_point);
+// Algorithmic flops of the integral kernel per class and grid point: per
+// primitive pair and per contracted pair (from the generator's counts).
+void class_flops(int cls, double* per_prim, double* per_pair);
+
+cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64);
 
 }  // namespace snk

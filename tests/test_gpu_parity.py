@@ -59,8 +59,9 @@ def test_shell_blocks_match_oracle(snk, recipe):
             # relative 1e-12 per point plus an absolute 1e-14 of the pair's largest
             # value: blocks that vanish by symmetry (an s-p pair at its own centre)
             # are FP64 rounding of cancelling O(max) terms, ~1e-16 max on both sides
-            # (shell pairs whose rigorous bound is below 1e-40 are dropped at setup)
-            tol = 1e-12 * np.max(np.abs(ref), axis=(1, 2), keepdims=True) + 1e-14 * np.max(np.abs(ref)) + 1e-40
+            # (primitive pairs whose rigorous bound is below 1e-20 are left out at
+            # setup: at most 9 of them per pair here, so an absolute 1e-18 floor)
+            tol = 1e-12 * np.max(np.abs(ref), axis=(1, 2), keepdims=True) + 1e-14 * np.max(np.abs(ref)) + 1e-18
             bad = np.abs(dev - ref) > tol
             if bad.any():
                 i, u, v = np.argwhere(bad)[0]
@@ -167,3 +168,34 @@ def test_errors_leave_the_handle_usable(snk, chain4):
     K = eng.build_K()
     assert np.max(np.abs(K - oracle.snk_K(chain4.basis, chain4.grid, chain4.P))) <= TOL_K
     eng.close()
+
+
+def test_distance_bound_and_global_bound_agree(snk):
+    """The per-batch charge/distance refinement of A-tilde keeps parity and keeps
+    no more pairs than the global bound of the paper."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    K0, s0 = _gpu_K(snk, p, batch_max=300, distance_bound=0)
+    K1, s1 = _gpu_K(snk, p, batch_max=300, distance_bound=1)
+    assert np.max(np.abs(K0 - Kref)) <= TOL_K
+    assert np.max(np.abs(K1 - Kref)) <= TOL_K
+    assert s1["pairs_kept"] <= s0["pairs_kept"]
+
+
+def test_mixed_precision_form(snk):
+    """Form 1: kept pairs whose sn-LinK estimate is below fp32_bound run their
+    integrals in FP32 (FP32 Boys table, recursions and contraction); the result
+    stays within 1e-7 of the FP64 build and of the oracle."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    K64, s64 = _gpu_K(snk, p, batch_max=300)
+    Km, sm = _gpu_K(snk, p, batch_max=300, precision="mixed")
+    assert sm["pairs_kept_fp32"] > 0
+    assert sm["pairs_kept"] == s64["pairs_kept"]
+    assert np.max(np.abs(Km - K64)) <= 1e-7
+    assert np.max(np.abs(Km - Kref)) <= 1e-7
+    assert np.max(np.abs(Km - Km.T)) == 0.0
+    # everything in FP32: still a sane exchange matrix, error well above FP64's
+    Kf, sf = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e300)
+    assert sf["pairs_kept_fp32"] == sf["pairs_kept"]
+    assert 1e-12 < np.max(np.abs(Kf - Kref)) <= 1e-5
