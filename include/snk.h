@@ -97,7 +97,14 @@ typedef struct {
   double fp32_bound;       /* mixed form: kept pairs whose sn-LinK estimate
                               epsilon^K is below this run their integrals in FP32 */
   int64_t workspace_bytes; /* device workspace cap for batch chunks (Alg. 1); 0 = auto */
-  double reserved[8];
+  int32_t tensor_gemms;    /* mixed form: bit 0 runs F = X P, bit 1 runs Kt = G^T X on
+                              the tensor cores (3xTF32, FP32 accumulation); default 0:
+                              both in FP64, because cancellation in X P amplifies the
+                              ~1e-7 split error to ~1e-5 in K on the 96-atom workload */
+  int32_t graph;           /* 1: snk_build_K* capture the whole build in a CUDA graph
+                              on first use (per density and output buffer) and
+                              replay it; phase times are then not reported      */
+  double reserved[7];
 } snk_options;
 
 /* Per-build counters and phase times (CUDA events on the library stream). */
@@ -135,19 +142,42 @@ void snk_options_default(snk_options *opt);
 int snk_create(const snk_basis *basis, const snk_grid *grid, const snk_options *opt,
                snk_ctx **out);
 
-/* Load a density matrix (N_b x N_b, row-major, symmetric to 1e-12 relative)
- * and run the density-dependent sn-LinK screen: F-tilde (Eq. exx_fmat_approx)
- * and the pair lists V_j (Eq. sp_set).  P is a host pointer. */
-int snk_set_density(snk_ctx *ctx, const double *P);
-/* Same with P in device memory. */
-int snk_set_density_device(snk_ctx *ctx, const double *dP);
+/* Several independent molecules in one handle (the batched form): molecule m
+ * has bases[m] and grids[m].  All later work runs over the batches of every
+ * molecule in the same launches; each molecule keeps its own N_b,m x N_b,m
+ * density and exchange block.  Shell indices of the debug calls are global
+ * (molecule after molecule).  snk_create is the case n_mol = 1. */
+int snk_create_batch(int32_t n_mol, const snk_basis *bases, const snk_grid *grids, const snk_options *opt,
+                     snk_ctx **out);
+int32_t snk_n_molecules(const snk_ctx *ctx);
+int64_t snk_molecule_functions(const snk_ctx *ctx, int32_t m);
 
-/* Build K for the loaded density (Alg. 1 on one GPU).  K is host memory,
- * N_b x N_b row-major; the call returns when K is written. */
+/* Load the density (symmetric to 1e-12 relative) and run the density-
+ * dependent sn-LinK screen: F-tilde (Eq. exx_fmat_approx) and the pair lists
+ * V_j (Eq. sp_set).  P is a host pointer to the packed blocks: molecule after
+ * molecule, each N_b,m x N_b,m row-major (for one molecule simply the
+ * N_b x N_b matrix). */
+int snk_set_density(snk_ctx *ctx, const double *P);
+/* Same with the packed P in device memory. */
+int snk_set_density_device(snk_ctx *ctx, const double *dP);
+/* Same from one host pointer per molecule (P[m] is N_b,m x N_b,m). */
+int snk_set_density_batch(snk_ctx *ctx, const double *const *P);
+
+/* Build K for the loaded density (Alg. 1 on one GPU).  K is host memory in the
+ * packed layout of snk_set_density; the call returns when K is written. */
 int snk_build_K(snk_ctx *ctx, double *K);
-/* Same, writing into device memory; returns once the work is enqueued on the
- * library stream (synchronise that stream before reading dK). */
+/* Same, writing the packed blocks into device memory; returns once the work
+ * is enqueued on the library stream (synchronise it before reading dK). */
 int snk_build_K_device(snk_ctx *ctx, double *dK);
+/* Same into one host buffer per molecule. */
+int snk_build_K_batch(snk_ctx *ctx, double *const *K);
+
+/* Autotuner of the integral kernels (after snk_set_density): for every
+ * (class, precision) list, times the kernel on the batches of the last
+ * workspace chunk for runs of 2..128 shell pairs per 128-point tile and keeps
+ * the fastest; the choice holds for later builds and densities of the handle.
+ * runs (optional, 12 entries: FP64 ss ps pp ds dp dd, then FP32) receives it. */
+int snk_autotune(snk_ctx *ctx, int32_t *runs);
 
 /* Stream for all later work on this handle (a cudaStream_t; NULL = the legacy
  * default stream). */

@@ -8,6 +8,10 @@ if the library is missing or no GPU is present the calls raise.
     eng.set_density(P)                 # snk_set_density (NumPy) / _device (torch CUDA tensor)
     K = eng.build_K()                  # snk_build_K -> NumPy, or build_K(out=cuda_tensor)
 
+    batch = Engine([b0, b1, ...], [g0, g1, ...])   # snk_create_batch: many molecules, shared launches
+    batch.set_density([P0, P1, ...])
+    Ks = batch.build_K()               # list of NumPy arrays
+
 ``basis`` needs the attributes l, nprim, atom, center, exps, coefs and
 ``grid`` the attributes xyz, w, atom (NumPy arrays), as produced by the
 ``synth`` generators.
@@ -32,12 +36,14 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported input", -3: "density
           -4: "bad call order", -5: "out of memory", -6: "CUDA error", -7: "device wait timed out"}
 SCREEN = {"none": 0, "link": 1, "learned": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
+LISTS = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
 # every entry point declared in include/snk.h
-SYMBOLS = ["snk_options_default", "snk_create", "snk_set_density", "snk_set_density_device", "snk_build_K",
-           "snk_build_K_device", "snk_set_stream", "snk_get_stats", "snk_n_functions", "snk_last_error",
-           "snk_status_string", "snk_destroy", "snk_debug_boys", "snk_debug_shell_A", "snk_debug_pair_bound",
-           "snk_debug_batches", "snk_shell_A_noalloc"]
+SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molecules", "snk_molecule_functions",
+           "snk_set_density", "snk_set_density_device", "snk_set_density_batch", "snk_build_K",
+           "snk_build_K_device", "snk_build_K_batch", "snk_autotune", "snk_set_stream", "snk_get_stats",
+           "snk_n_functions", "snk_last_error", "snk_status_string", "snk_destroy", "snk_debug_boys",
+           "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc"]
 
 
 class SnkError(RuntimeError):
@@ -62,7 +68,8 @@ class SnkOptions(ctypes.Structure):
     _fields_ = [("eps_basis", ctypes.c_double), ("eps_E", ctypes.c_double), ("eps_K", ctypes.c_double),
                 ("batch_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("distance_bound", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_int64), ("reserved", ctypes.c_double * 8)]
+                ("workspace_bytes", ctypes.c_int64), ("tensor_gemms", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("reserved", ctypes.c_double * 7)]
 
 
 class SnkStats(ctypes.Structure):
@@ -79,6 +86,7 @@ class SnkStats(ctypes.Structure):
 
 
 _D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
 _P = ctypes.c_void_p
 
 
@@ -99,8 +107,16 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
             L.snk_options_default.restype = None
             L.snk_create.argtypes = [ctypes.POINTER(SnkBasis), ctypes.POINTER(SnkGrid), ctypes.POINTER(SnkOptions),
                                      ctypes.POINTER(_P)]
-            for name in ("snk_set_density", "snk_set_density_device", "snk_build_K", "snk_build_K_device"):
+            L.snk_create_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(SnkBasis), ctypes.POINTER(SnkGrid),
+                                           ctypes.POINTER(SnkOptions), ctypes.POINTER(_P)]
+            L.snk_n_molecules.argtypes = [_P]
+            L.snk_n_molecules.restype = ctypes.c_int32
+            L.snk_molecule_functions.argtypes = [_P, ctypes.c_int32]
+            L.snk_molecule_functions.restype = ctypes.c_int64
+            for name in ("snk_set_density", "snk_set_density_device", "snk_build_K", "snk_build_K_device",
+                         "snk_set_density_batch", "snk_build_K_batch"):
                 getattr(L, name).argtypes = [_P, _P]
+            L.snk_autotune.argtypes = [_P, _I32]
             L.snk_set_stream.argtypes = [_P, _P]
             L.snk_get_stats.argtypes = [_P, ctypes.POINTER(SnkStats)]
             L.snk_n_functions.argtypes = [_P]
@@ -114,9 +130,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
             L.snk_debug_boys.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
             L.snk_debug_shell_A.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D]
             L.snk_debug_pair_bound.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _D]
+            L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), _I32, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_int64)]
             L.snk_shell_A_noalloc.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P]
-            L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
-                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
             _lib = L
     return _lib
 
@@ -154,33 +170,53 @@ def _is_cuda_tensor(x) -> bool:
     return hasattr(x, "is_cuda") and x.is_cuda
 
 
+def _basis_struct(basis, keep):
+    arrs = [np.ascontiguousarray(basis.l, dtype=np.int32), np.ascontiguousarray(basis.nprim, dtype=np.int32),
+            np.ascontiguousarray(basis.atom, dtype=np.int32), np.ascontiguousarray(basis.center, dtype=np.float64),
+            np.ascontiguousarray(basis.exps, dtype=np.float64), np.ascontiguousarray(basis.coefs, dtype=np.float64)]
+    keep += arrs
+    return SnkBasis(int(arrs[0].shape[0]), arrs[0].ctypes.data_as(_I32), arrs[1].ctypes.data_as(_I32),
+                    arrs[2].ctypes.data_as(_I32), _dptr(arrs[3]), _dptr(arrs[4]), _dptr(arrs[5]))
+
+
+def _grid_struct(grid, keep):
+    arrs = [np.ascontiguousarray(grid.xyz, dtype=np.float64), np.ascontiguousarray(grid.w, dtype=np.float64),
+            np.ascontiguousarray(grid.atom, dtype=np.int32)]
+    keep += arrs
+    return SnkGrid(int(arrs[1].shape[0]), _dptr(arrs[0]), _dptr(arrs[1]), arrs[2].ctypes.data_as(_I32))
+
+
 class Engine:
-    """One sn-K problem (basis + grid) on the current CUDA device."""
+    """One sn-K problem (basis + grid), or a batch of independent molecules
+    (lists of bases and grids), on the current CUDA device."""
 
     def __init__(self, basis, grid, **opts):
         L = lib()
-        self._keep = []
-        l = np.ascontiguousarray(basis.l, dtype=np.int32)
-        nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
-        atom = np.ascontiguousarray(basis.atom, dtype=np.int32)
-        center = np.ascontiguousarray(basis.center, dtype=np.float64)
-        exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
-        coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
-        gxyz = np.ascontiguousarray(grid.xyz, dtype=np.float64)
-        gw = np.ascontiguousarray(grid.w, dtype=np.float64)
-        gatom = np.ascontiguousarray(grid.atom, dtype=np.int32)
-        i32 = ctypes.POINTER(ctypes.c_int32)
-        b = SnkBasis(int(l.shape[0]), l.ctypes.data_as(i32), nprim.ctypes.data_as(i32), atom.ctypes.data_as(i32),
-                     _dptr(center), _dptr(exps), _dptr(coefs))
-        g = SnkGrid(int(gw.shape[0]), _dptr(gxyz), _dptr(gw), gatom.ctypes.data_as(i32))
+        self._h = None
+        keep = []
+        self.batched = isinstance(basis, (list, tuple))
+        bases = list(basis) if self.batched else [basis]
+        grids = list(grid) if self.batched else [grid]
+        if len(bases) != len(grids) or not bases:
+            raise ValueError("need one grid per basis")
         self.opts = options(**opts)
         h = _P()
-        rc = L.snk_create(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(h))
+        if self.batched:
+            b = (SnkBasis * len(bases))(*[_basis_struct(x, keep) for x in bases])
+            g = (SnkGrid * len(grids))(*[_grid_struct(x, keep) for x in grids])
+            rc = L.snk_create_batch(len(bases), b, g, ctypes.byref(self.opts), ctypes.byref(h))
+        else:
+            b = _basis_struct(basis, keep)
+            g = _grid_struct(grid, keep)
+            rc = L.snk_create(ctypes.byref(b), ctypes.byref(g), ctypes.byref(self.opts), ctypes.byref(h))
         if rc != SNK_OK:
             raise SnkError(rc, "snk_create")
         self._h = h
-        self._l = l
+        self._l = np.concatenate([np.asarray(x.l, dtype=np.int32) for x in bases])
+        self.n_mol = int(L.snk_n_molecules(h))
+        self.nfs = [int(L.snk_molecule_functions(h, m)) for m in range(self.n_mol)]
         self.nf = int(L.snk_n_functions(h))
+        self.packed = sum(n * n for n in self.nfs)
         self._stream = None
 
     # -- plumbing ---------------------------------------------------------
@@ -208,27 +244,47 @@ class Engine:
 
     # -- the sn-K build ---------------------------------------------------
     def set_density(self, P):
-        """P: NumPy (host) array or torch CUDA tensor, N_b x N_b float64, symmetric."""
-        if _is_cuda_tensor(P):
+        """P: NumPy array (N_b x N_b, or the packed blocks), a list of NumPy
+        arrays (one per molecule), or a torch CUDA tensor (packed), float64,
+        symmetric."""
+        if isinstance(P, (list, tuple)):
+            arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in P]
+            assert [a.shape for a in arrs] == [(n, n) for n in self.nfs]
+            ptrs = (_P * len(arrs))(*[a.ctypes.data for a in arrs])
+            self._check(lib().snk_set_density_batch(self._h, ptrs), "snk_set_density_batch")
+        elif _is_cuda_tensor(P):
             assert P.dtype.is_floating_point and P.element_size() == 8 and P.is_contiguous()
-            assert tuple(P.shape) == (self.nf, self.nf)
+            assert P.numel() == self.packed
             self._check(lib().snk_set_density_device(self._h, _P(P.data_ptr())), "snk_set_density_device")
         else:
             Pn = np.ascontiguousarray(P, dtype=np.float64)
-            assert Pn.shape == (self.nf, self.nf)
+            assert Pn.size == self.packed
             self._check(lib().snk_set_density(self._h, _P(Pn.ctypes.data)), "snk_set_density")
 
     def build_K(self, out=None):
-        """Host K (NumPy) by default; with out = a CUDA tensor the build writes there
-        and returns it once the work is enqueued on the engine's stream."""
+        """Host K (NumPy; a list of per-molecule arrays for a batch) by default;
+        with out = a CUDA tensor (packed blocks) the build writes there and
+        returns it once the work is enqueued on the engine's stream."""
         if out is not None and _is_cuda_tensor(out):
-            assert out.element_size() == 8 and out.is_contiguous() and tuple(out.shape) == (self.nf, self.nf)
+            assert out.element_size() == 8 and out.is_contiguous() and out.numel() == self.packed
             self._check(lib().snk_build_K_device(self._h, _P(out.data_ptr())), "snk_build_K_device")
             return out
+        if self.batched and out is None:
+            Ks = [np.empty((n, n)) for n in self.nfs]
+            ptrs = (_P * len(Ks))(*[k.ctypes.data for k in Ks])
+            self._check(lib().snk_build_K_batch(self._h, ptrs), "snk_build_K_batch")
+            return Ks
         K = out if out is not None else np.empty((self.nf, self.nf))
-        assert K.dtype == np.float64 and K.flags.c_contiguous and K.shape == (self.nf, self.nf)
+        assert K.dtype == np.float64 and K.flags.c_contiguous and K.size == self.packed
         self._check(lib().snk_build_K(self._h, _P(K.ctypes.data)), "snk_build_K")
         return K
+
+    def autotune(self) -> dict:
+        """snk_autotune: pairs per tile chosen for each integral list."""
+        runs = (ctypes.c_int32 * 12)()
+        self._check(lib().snk_autotune(self._h, runs), "snk_autotune")
+        names = [f"fp64_{n}" for n in LISTS] + [f"fp32_{n}" for n in LISTS]
+        return dict(zip(names, list(runs)))
 
     def stats(self) -> dict:
         s = SnkStats()
@@ -272,7 +328,7 @@ class Engine:
         self._check(lib().snk_debug_batches(self._h, ctypes.byref(n), None, 0, None), "snk_debug_batches")
         counts = np.zeros(max(n.value, 1), dtype=np.int32)
         perm = np.zeros(int(self.stats()["n_points"]), dtype=np.int64)
-        self._check(lib().snk_debug_batches(self._h, ctypes.byref(n), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                            counts.shape[0], perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+        self._check(lib().snk_debug_batches(self._h, ctypes.byref(n), counts.ctypes.data_as(_I32), counts.shape[0],
+                                            perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                     "snk_debug_batches")
         return counts[:n.value], perm

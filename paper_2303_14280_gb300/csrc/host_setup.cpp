@@ -164,8 +164,11 @@ double pair_bound(const Setup& s, int sa, int sb) {
   return total;
 }
 
-int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, Setup* s,
-                std::string* msg) {
+namespace {
+
+// Setup of one molecule (indices local to it).
+int build_setup_one(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, Setup* s,
+                    std::string* msg) {
   if (!basis || !grid || !opt) {
     *msg = "NULL basis, grid or options";
     return SNK_ERR_INVALID_ARG;
@@ -429,7 +432,13 @@ int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options*
   }
   s->bshell_off[nb] = (int)s->bshell.size();
   s->xfunc_off[nb] = (int)s->xfunc.size();
+  return SNK_OK;
+}
 
+}  // namespace
+
+// Boys interpolation tables of the FP64 and FP32 integral kernels.
+void build_boys_tables(Setup* s) {
   // Boys table per L: F_{L+m}(T_k)/m!, exp(-T_k), T_k
   s->boys.assign((size_t)(kBoysLMax + 1) * kBoysRows * kBoysCols, 0.0);
   double F[kBoysLMax + kBoysTerms + 1];
@@ -456,6 +465,106 @@ int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options*
       row[kBoysTermsF] = (float)src[kBoysTerms];
       row[kBoysTermsF + 1] = (float)src[kBoysTerms + 1];
     }
+}
+
+// Several independent molecules in one handle: each is set up on its own
+// (normalisation, pairs, octree batches, basis screen), then everything is
+// concatenated.  Shell, pair and batch indices become global; function
+// indices inside the X / F / G column lists stay local to their molecule,
+// whose P and K blocks are packed one after another (row-major, N_b,m^2 each).
+int build_setup(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_options* opt, Setup* s,
+                std::string* msg) {
+  if (n_mol < 1 || !bases || !grids || !opt) {
+    *msg = "need at least one molecule and non-NULL basis, grid and options arrays";
+    return SNK_ERR_INVALID_ARG;
+  }
+  *s = Setup();
+  s->n_mol = n_mol;
+  int64_t pk = 0, pi = 0, npts = 0;
+  for (int m = 0; m < n_mol; ++m) {
+    Setup one;
+    std::string err;
+    int rc = build_setup_one(&bases[m], &grids[m], opt, &one, &err);
+    if (rc != SNK_OK) {
+      *msg = (n_mol > 1 ? "molecule " + std::to_string(m) + ": " : std::string()) + err;
+      return rc;
+    }
+    Setup::Mol mol;
+    mol.ms0 = s->ns;
+    mol.ns = one.ns;
+    mol.mf0 = s->nf;
+    mol.nf = one.nf;
+    mol.mb0 = (int)s->bcenter.size() / 3;
+    mol.nb = (int)one.bstart.size() - 1;
+    mol.pk_off = pk;
+    mol.pi_off = pi;
+    mol.p0 = npts;
+    mol.npts = one.npts;
+    const int pp0 = (int)s->prims.size(), np0 = s->nprim_total, pr0 = (int)s->pairs.size();
+    for (int c = 0; c <= kNumClasses; ++c) mol.cr[c] = pr0 + one.class_begin[c];
+    pk += (int64_t)one.nf * one.nf;
+    pi += (int64_t)one.ns * one.ns;
+    // shells and functions
+    for (int a = 0; a < one.ns; ++a) {
+      s->l.push_back(one.l[a]);
+      s->nprim.push_back(one.nprim[a]);
+      s->poff.push_back(one.poff[a] + np0);
+      s->foff.push_back(one.foff[a] + s->nf);
+      s->atom.push_back(one.atom[a]);
+      s->rcut.push_back(one.rcut[a]);
+      for (int q = 0; q < 3; ++q) s->center.push_back(one.center[3 * a + q]);
+    }
+    s->exps.insert(s->exps.end(), one.exps.begin(), one.exps.end());
+    s->d.insert(s->d.end(), one.d.begin(), one.d.end());
+    s->fcomp.insert(s->fcomp.end(), one.fcomp.begin(), one.fcomp.end());
+    for (int f : one.fshell) s->fshell.push_back(f + mol.ms0);
+    // pairs (class-major within the molecule)
+    for (size_t p = 0; p < one.pairs.size(); ++p) {
+      PairHdr h = one.pairs[p];
+      h.sa += mol.ms0;
+      h.sb += mol.ms0;
+      h.pp_off += pp0;
+      s->pairs.push_back(h);
+    }
+    s->prims.insert(s->prims.end(), one.prims.begin(), one.prims.end());
+    s->bound.insert(s->bound.end(), one.bound.begin(), one.bound.end());
+    s->qbound.insert(s->qbound.end(), one.qbound.begin(), one.qbound.end());
+    s->pair_class.insert(s->pair_class.end(), one.pair_class.begin(), one.pair_class.end());
+    for (int v : one.pair_index) s->pair_index.push_back(v < 0 ? -1 : v + pr0);
+    // grid and batches
+    for (int64_t v : one.perm) s->perm.push_back(v + npts);
+    s->xyz.insert(s->xyz.end(), one.xyz.begin(), one.xyz.end());
+    s->w.insert(s->w.end(), one.w.begin(), one.w.end());
+    for (int j = 0; j < mol.nb; ++j) {
+      s->bstart.push_back(one.bstart[j] + npts);
+      s->bmol.push_back(m);
+      s->bradius.push_back(one.bradius[j]);
+      for (int q = 0; q < 3; ++q) s->bcenter.push_back(one.bcenter[3 * j + q]);
+      s->bshell_off.push_back((int)s->bshell.size() + one.bshell_off[j]);
+      s->xfunc_off.push_back((int)s->xfunc.size() + one.xfunc_off[j]);
+      s->bnf.push_back(one.bnf[j]);
+      s->cm_off.push_back(s->cm_total);
+      s->phf_off.push_back(s->phf_total);
+      s->cm_total += one.ns;
+      s->phf_total += one.nf;
+    }
+    for (int a : one.bshell) s->bshell.push_back(a + mol.ms0);
+    s->xfunc.insert(s->xfunc.end(), one.xfunc.begin(), one.xfunc.end());  // local function indices
+    s->ns += one.ns;
+    s->nf += one.nf;
+    s->nprim_total += one.nprim_total;
+    npts += one.npts;
+    s->mols.push_back(mol);
+  }
+  s->poff.push_back(s->nprim_total);
+  s->foff.push_back(s->nf);
+  s->bstart.push_back(npts);
+  s->bshell_off.push_back((int)s->bshell.size());
+  s->xfunc_off.push_back((int)s->xfunc.size());
+  s->npts = npts;
+  s->packed = pk;
+  for (int c = 0; c <= kNumClasses; ++c) s->class_begin[c] = c == kNumClasses ? (int)s->pairs.size() : 0;
+  build_boys_tables(s);
   return SNK_OK;
 }
 

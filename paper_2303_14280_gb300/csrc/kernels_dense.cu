@@ -2,12 +2,17 @@
 //   collocation X_j (Eq. collocation), the geometry-only batch maxima of
 //   Eq. (exx_fmat_approx), F-tilde = |P| Phi-tilde (Eq. exx_fmat_approx) as
 //   a GEMM over batches, the sn-LinK pair screen with per-batch compaction
-//   (Eq. sp_set), the FP64 products F_j = X_j P (Eq. batch_local_exx) and
-//   Kt += G_j^T X_j (Eq. usym_k), and the symmetrisation of Eq. (sn_k).
+//   (Eq. sp_set), the products F_j = X_j P (Eq. batch_local_exx) and
+//   Kt += G_j^T X_j (Eq. usym_k) in FP64 or as split-TF32 tensor-core
+//   products, and the symmetrisation of Eq. (sn_k).
+//
+// Several molecules can share one handle: every batch knows its molecule, P
+// and K are packed per molecule (row-major N_b,m^2 blocks), and column lists
+// hold molecule-local function indices.
 //
 // FP64 on GB300 issues at 2 DFMA per SM per clock, so a 64 x 64 x 16 tile
 // step is ~32k cycles of DFMA against 2k doubles of shared-memory staging:
-// the GEMMs are FP64-pipe bound with plain shared-memory tiling.
+// the FP64 GEMMs are FP64-pipe bound with plain shared-memory tiling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +29,20 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// ---------------------------------------------------------------- GEMM tile
+// molecule of a packed-block element (the blocks are in pk_off order)
+__device__ __forceinline__ int mol_of_packed(const MolDesc* mols, int n_mol, int64_t e) {
+  int lo = 0, hi = n_mol - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (mols[mid].pk_off <= e)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- FP64 GEMM tile
 
 constexpr int TM = 64, TN = 64, TK = 16, GEMM_THREADS = 256;
 
@@ -93,6 +111,122 @@ __device__ __forceinline__ void gemm_tile(int m0, int n0, int mdim, int ndim, in
     }
 }
 
+// ---------------------------------------------------------------- split-TF32 tensor-core tile (mixed form)
+
+// 3xTF32: a = a_hi + a_lo with both parts rounded to TF32, and
+// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, each on the tensor cores with FP32
+// accumulation (the dropped A_lo B_lo is ~2^-22 relative).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int TC_THREADS = 128, TC_M = 64, TC_N = 64, TC_K = 16, TC_PAD = 4;
+
+// C[m][n] = sum_k A(m,k) B(k,n) over the 64 x 64 tile at (m0, n0); four warps
+// in 2 x 2, each 32 x 32 = 2 x 4 m16n8k8 tiles; st(m, n, c) stores.
+template <class LA, class LB, class ST>
+__device__ __forceinline__ void tf32x3_tile(int m0, int n0, int mdim, int ndim, int kdim, LA la, LB lb, ST st,
+                                            bool a_k_fast, bool b_k_fast) {
+  __shared__ uint32_t Ah[TC_M][TC_K + TC_PAD], Al[TC_M][TC_K + TC_PAD];
+  __shared__ uint32_t Bh[TC_K][TC_N + 2 * TC_PAD], Bl[TC_K][TC_N + 2 * TC_PAD];  // row stride = 8 banks
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  for (int k0 = 0; k0 < kdim; k0 += TC_K) {
+#pragma unroll
+    for (int r = 0; r < (TC_M * TC_K) / TC_THREADS; ++r) {
+      const int e = tid + r * TC_THREADS;
+      int kk, mm;
+      if (a_k_fast) {
+        kk = e % TC_K;
+        mm = e / TC_K;
+      } else {
+        mm = e % TC_M;
+        kk = e / TC_M;
+      }
+      const int m = m0 + mm, k = k0 + kk;
+      const float v = (m < mdim && k < kdim) ? (float)la(m, k) : 0.f;
+      const uint32_t h = to_tf32(v);
+      Ah[mm][kk] = h;
+      Al[mm][kk] = to_tf32(v - __uint_as_float(h));
+      int nn;
+      if (b_k_fast) {
+        kk = e % TC_K;
+        nn = e / TC_K;
+      } else {
+        nn = e % TC_N;
+        kk = e / TC_N;
+      }
+      const int n = n0 + nn, k2 = k0 + kk;
+      const float u = (n < ndim && k2 < kdim) ? (float)lb(k2, n) : 0.f;
+      const uint32_t hb = to_tf32(u);
+      Bh[kk][nn] = hb;
+      Bl[kk][nn] = to_tf32(u - __uint_as_float(hb));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < TC_K; ks += 8) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r0 = wm + i * 16 + g;
+        ah[i][0] = Ah[r0][ks + t];
+        ah[i][1] = Ah[r0 + 8][ks + t];
+        ah[i][2] = Ah[r0][ks + t + 4];
+        ah[i][3] = Ah[r0 + 8][ks + t + 4];
+        al[i][0] = Al[r0][ks + t];
+        al[i][1] = Al[r0 + 8][ks + t];
+        al[i][2] = Al[r0][ks + t + 4];
+        al[i][3] = Al[r0 + 8][ks + t + 4];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c0 = wn + j * 8 + g;
+        bh[j][0] = Bh[ks + t][c0];
+        bh[j][1] = Bh[ks + t + 4][c0];
+        bl[j][0] = Bl[ks + t][c0];
+        bl[j][1] = Bl[ks + t + 4][c0];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          mma_tf32(acc[i][j], al[i], bh[j]);
+          mma_tf32(acc[i][j], ah[i], bl[j]);
+          mma_tf32(acc[i][j], ah[i], bh[j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + 2 * t + (r & 1);
+        if (m < mdim && n < ndim) st(m, n, (double)acc[i][j][r]);
+      }
+}
+
 // ---------------------------------------------------------------- collocation
 
 constexpr int COL_THREADS = 128, COL_SHELLS = 8;
@@ -151,7 +285,7 @@ __global__ void __launch_bounds__(COL_THREADS) collocation_kernel(const BatchDes
 
 // Phi-tilde_nu^(j) = max_i |sqrt(w_i) Phi_{nu i}|, one thread per function.
 __global__ void phit_f_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ ws,
-                              const double* __restrict__ w, const int* __restrict__ xfunc, int nf,
+                              const double* __restrict__ w, const int* __restrict__ xfunc,
                               double* __restrict__ phit_f) {
   const BatchDesc bd = batches[blockIdx.y];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,7 +293,7 @@ __global__ void phit_f_kernel(const BatchDesc* __restrict__ batches, const doubl
   const double* X = ws + bd.xoff + (int64_t)c * bd.ldq;
   double m = 0.0;
   for (int i = 0; i < bd.q; ++i) m = fmax(m, sqrt(fabs(w[bd.p0 + i])) * fabs(X[i]));
-  phit_f[(int64_t)blockIdx.y * nf + xfunc[bd.xfunc_off + c]] = m;
+  phit_f[bd.phf_off + xfunc[bd.xfunc_off + c]] = m;
 }
 
 // phi-tilde^(j) = max_i sqrt(w_i) sum_{mu in B_j} |Phi_{mu i}|, one block per batch.
@@ -186,17 +320,30 @@ __global__ void phit_b_kernel(const BatchDesc* __restrict__ batches, const doubl
 
 // ---------------------------------------------------------------- F-tilde
 
-// ft_shell[j][a] = max_{mu in a} sum_nu |P_{mu nu}| Phi-tilde_nu^(j): a GEMM over
-// (mu, batch) with the shell maximum folded into the store.
-__global__ void __launch_bounds__(GEMM_THREADS) ftilde_kernel(const double* __restrict__ P,
-                                                              const double* __restrict__ phit_f, int nf,
-                                                              int nbatch, const int* __restrict__ fshell,
-                                                              int ns, double* __restrict__ ft_shell) {
+// For molecule blockIdx.z: F-tilde_a^(j) = max_{mu in a} sum_nu |P_{mu nu}|
+// Phi-tilde_nu^(j) over its functions mu and batches j, a GEMM whose store takes
+// the shell maximum.  The molecule's batch rows are consecutive (stride N_b,m
+// in Phi-tilde, N_shell,m in F-tilde).
+__global__ void __launch_bounds__(GEMM_THREADS) ftilde_kernel(const MolDesc* __restrict__ mols,
+                                                              const BatchDesc* __restrict__ batches,
+                                                              const double* __restrict__ P,
+                                                              const double* __restrict__ phit_f,
+                                                              const int* __restrict__ fshell,
+                                                              double* __restrict__ ft_shell) {
+  const MolDesc md = mols[blockIdx.z];
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= md.nf || n0 >= md.nb) return;
+  const double* Pm = P + md.pk_off;
+  const BatchDesc b0 = batches[md.mb0];
+  const double* ph = phit_f + b0.phf_off;
+  double* ft = ft_shell + b0.cm_off;
   gemm_tile(
-      m0, n0, nf, nbatch, nf, [&](int m, int k) { return fabs(P[(int64_t)m * nf + k]); },
-      [&](int k, int n) { return phit_f[(int64_t)n * nf + k]; },
-      [&](int m, int n, double c) { atomic_max_nonneg(&ft_shell[(int64_t)n * ns + fshell[m]], c); }, true, true);
+      m0, n0, md.nf, md.nb, md.nf, [&](int m, int k) { return fabs(Pm[(int64_t)m * md.nf + k]); },
+      [&](int k, int n) { return ph[(int64_t)n * md.nf + k]; },
+      [&](int m, int n, double c) {
+        atomic_max_nonneg(&ft[(int64_t)n * md.ns + (fshell[md.mf0 + m] - md.ms0)], c);
+      },
+      true, true);
 }
 
 // ---------------------------------------------------------------- sn-LinK pair screen
@@ -223,10 +370,11 @@ __device__ __forceinline__ double batch_pair_bound(const ScreenArgs& a, int j, i
 // sn-LinK decision for pair p in batch j, Eq. (sp_set): -1 drop, else the
 // list index class + kNumClasses * precision (precision 1 = FP32 integrals,
 // for pairs whose estimate max(F_a, F_b) phi A stays below fp32_bound).
-__device__ __forceinline__ int classify_pair(const ScreenArgs& a, int j, int p, int cls, const PairHdr& h) {
+__device__ __forceinline__ int classify_pair(const ScreenArgs& a, const BatchDesc& bd, int j, int p, int cls,
+                                             const PairHdr& h) {
   if (a.screen == SNK_SCREEN_NONE) return cls;
-  const double* ft = a.ft_shell + (int64_t)j * a.ns;
-  const double fa = ft[h.sa], fb = ft[h.sb];
+  const double* ft = a.ft_shell + bd.cm_off;
+  const double fa = ft[h.sa - bd.ms0], fb = ft[h.sb - bd.ms0];
   const double bnd = batch_pair_bound(a, j, p, h);
   const double eK = fmax(fa, fb) * a.phit_b[j] * bnd;
   if (!((fa * fb * bnd >= a.eps_E) || (eK >= a.eps_K))) return -1;
@@ -234,12 +382,15 @@ __device__ __forceinline__ int classify_pair(const ScreenArgs& a, int j, int p, 
 }
 
 // Pass 1: per (batch, list) pair counts and primitive-pair counts; marks the
-// shells of every kept pair (their F / G columns).  One block per batch.
+// shells of every kept pair (their F / G columns).  One block per batch, the
+// pairs of the batch's molecule only.
 __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, int* __restrict__ counts,
                                                                  long long* __restrict__ ppcounts,
                                                                  unsigned char* __restrict__ sflag) {
   const int j = blockIdx.x;
-  unsigned char* fl = sflag + (int64_t)j * a.ns;
+  const BatchDesc bd = a.batches[j];
+  const MolDesc md = a.mols[bd.mol];
+  unsigned char* fl = sflag + bd.cm_off;
   __shared__ int s_cnt[kNumLists];
   __shared__ unsigned long long s_pp[kNumLists];
   if (threadIdx.x < kNumLists) {
@@ -250,12 +401,12 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
   for (int c = 0; c < kNumClasses; ++c) {
     int n[2] = {0, 0};
     unsigned long long pp[2] = {0ull, 0ull};
-    for (int p = a.cr.b[c] + threadIdx.x; p < a.cr.b[c + 1]; p += SCR_THREADS) {
+    for (int p = md.cr[c] + threadIdx.x; p < md.cr[c + 1]; p += SCR_THREADS) {
       const PairHdr h = a.pairs[p];
-      const int li = classify_pair(a, j, p, c, h);
+      const int li = classify_pair(a, bd, j, p, c, h);
       if (li >= 0) {
-        fl[h.sa] = 1;
-        fl[h.sb] = 1;
+        fl[h.sa - bd.ms0] = 1;
+        fl[h.sb - bd.ms0] = 1;
         const int prec = li >= kNumClasses;
         n[prec] += 1;
         pp[prec] += (unsigned long long)h.pp_n;
@@ -280,14 +431,16 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
 __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, const int64_t* __restrict__ list_off,
                                                                  int* __restrict__ list) {
   const int j = blockIdx.x;
+  const BatchDesc bd = a.batches[j];
+  const MolDesc md = a.mols[bd.mol];
   __shared__ int warp_tot[2][SCR_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = 0; c < kNumClasses; ++c) {
     int64_t out[2] = {list_off[j * kNumLists + c], list_off[j * kNumLists + c + kNumClasses]};
-    for (int base = a.cr.b[c]; base < a.cr.b[c + 1]; base += SCR_THREADS) {
+    for (int base = md.cr[c]; base < md.cr[c + 1]; base += SCR_THREADS) {
       const int p = base + threadIdx.x;
       int li = -1;
-      if (p < a.cr.b[c + 1]) li = classify_pair(a, j, p, c, a.pairs[p]);
+      if (p < md.cr[c + 1]) li = classify_pair(a, bd, j, p, c, a.pairs[p]);
       const unsigned bal[2] = {__ballot_sync(0xffffffffu, li >= 0 && li < kNumClasses),
                                __ballot_sync(0xffffffffu, li >= kNumClasses)};
       if (lane == 0) {
@@ -313,32 +466,58 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, c
 // ---------------------------------------------------------------- F_j = X_j P, Kt += G_j^T X_j
 
 // F-hat_{s i} = w_i f_s sum_{nu in B_j} X_{nu i} P_{nu s}: the quadrature weight
-// and the Cartesian component factor of the column are folded into F.
-__global__ void __launch_bounds__(GEMM_THREADS) fgemm_kernel(const BatchDesc* __restrict__ batches,
-                                                             const double* __restrict__ P, int nf,
-                                                             const int* __restrict__ xfunc,
-                                                             const int* __restrict__ sfunc,
-                                                             const double* __restrict__ fcomp,
-                                                             const double* __restrict__ w, double* __restrict__ ws,
-                                                             float* __restrict__ ws32) {
+// and the Cartesian component factor of the column are folded into F.  In the
+// mixed form an FP32 copy is written for the FP32 pairs.
+template <bool TENSOR>
+__global__ void __launch_bounds__(TENSOR ? TC_THREADS : GEMM_THREADS)
+    fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P, const int* __restrict__ xfunc,
+                 const int* __restrict__ sfunc, const double* __restrict__ fcomp, const double* __restrict__ w,
+                 double* __restrict__ ws, float* __restrict__ ws32) {
   const BatchDesc bd = batches[blockIdx.z];
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   if (m0 >= bd.ldq || n0 >= bd.nS) return;
   const double* X = ws + bd.xoff;
   double* F = ws + bd.foff;
-  float* F32 = ws32 ? ws32 + bd.foff32 : nullptr;  // mixed form: FP32 copy for the FP32 pairs
+  float* F32 = ws32 ? ws32 + bd.foff32 : nullptr;
+  const double* Pm = P + bd.pk_off;
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
-  gemm_tile(
-      m0, n0, bd.ldq, bd.nS, bd.nB, [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; },
-      [&](int k, int n) { return P[(int64_t)xf[k] * nf + sf[n]]; },
-      [&](int m, int n, double c) {
-        const double wi = m < bd.q ? w[bd.p0 + m] : 0.0;
-        const double v = wi * fcomp[sf[n]] * c;
-        F[(int64_t)n * bd.ldq + m] = v;
-        if (F32) F32[(int64_t)n * bd.ldq + m] = (float)v;
-      },
-      false, false);
+  const double* fc = fcomp + bd.mf0;
+  auto la = [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; };
+  auto lb = [&](int k, int n) { return Pm[(int64_t)xf[k] * bd.nfm + sf[n]]; };
+  auto st = [&](int m, int n, double c) {
+    const double wi = m < bd.q ? w[bd.p0 + m] : 0.0;
+    const double v = wi * fc[sf[n]] * c;
+    F[(int64_t)n * bd.ldq + m] = v;
+    if (F32) F32[(int64_t)n * bd.ldq + m] = (float)v;
+  };
+  if (TENSOR)
+    tf32x3_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+  else
+    gemm_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+}
+
+// Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the molecule's block
+// of the packed accumulator (several batches add to the same entries).
+template <bool TENSOR>
+__global__ void __launch_bounds__(TENSOR ? TC_THREADS : GEMM_THREADS)
+    kgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc, const int* __restrict__ sfunc,
+                 const double* __restrict__ ws, double* __restrict__ Khat) {
+  const BatchDesc bd = batches[blockIdx.z];
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= bd.nS || n0 >= bd.nB) return;
+  const double* X = ws + bd.xoff;
+  const double* G = ws + bd.goff;
+  const int* xf = xfunc + bd.xfunc_off;
+  const int* sf = sfunc + bd.sfunc_off;
+  double* Km = Khat + bd.pk_off;
+  auto la = [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; };
+  auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
+  auto st = [&](int m, int n, double c) { atomicAdd(&Km[(int64_t)sf[m] * bd.nfm + xf[n]], c); };
+  if (TENSOR)
+    tf32x3_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+  else
+    gemm_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
 }
 
 // G += G32 over a chunk's contiguous G region (mixed form).
@@ -347,46 +526,34 @@ __global__ void merge_g32_kernel(const float* __restrict__ g32, int64_t n, doubl
     g64[e] += (double)g32[e];
 }
 
-// Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the global N_b x N_b
-// accumulator (several batches add to the same entries).
-__global__ void __launch_bounds__(GEMM_THREADS) kgemm_kernel(const BatchDesc* __restrict__ batches,
-                                                             const int* __restrict__ xfunc,
-                                                             const int* __restrict__ sfunc, int nf,
-                                                             const double* __restrict__ ws,
-                                                             double* __restrict__ Khat) {
-  const BatchDesc bd = batches[blockIdx.z];
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-  if (m0 >= bd.nS || n0 >= bd.nB) return;
-  const double* X = ws + bd.xoff;
-  const double* G = ws + bd.goff;
-  const int* xf = xfunc + bd.xfunc_off;
-  const int* sf = sfunc + bd.sfunc_off;
-  gemm_tile(
-      m0, n0, bd.nS, bd.nB, bd.q, [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; },
-      [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; },
-      [&](int m, int n, double c) { atomicAdd(&Khat[(int64_t)sf[m] * nf + xf[n]], c); }, true, true);
-}
-
-// K_{mu nu} = (f_mu Kt_{mu nu} + f_nu Kt_{nu mu}) / 2, Eq. (sn_k); the row factor
-// f_mu is the Cartesian component factor that the integral kernel leaves out.
-__global__ void finish_kernel(const double* __restrict__ Khat, const double* __restrict__ fcomp, int nf,
+// K_{mu nu} = (f_mu Kt_{mu nu} + f_nu Kt_{nu mu}) / 2 in every molecule block,
+// Eq. (sn_k); the row factor f_mu is the Cartesian component factor that the
+// integral kernel leaves out.
+__global__ void finish_kernel(const MolDesc* __restrict__ mols, int n_mol, int64_t packed,
+                              const double* __restrict__ Khat, const double* __restrict__ fcomp,
                               double* __restrict__ K) {
-  const int64_t n = (int64_t)nf * nf;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int mu = (int)(e / nf), nu = (int)(e % nf);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < packed; e += (int64_t)gridDim.x * blockDim.x) {
+    const MolDesc md = mols[mol_of_packed(mols, n_mol, e)];
+    const int64_t le = e - md.pk_off;
+    const int mu = (int)(le / md.nf), nu = (int)(le % md.nf);
+    const double a = __dmul_rn(fcomp[md.mf0 + mu], Khat[e]);
+    const double b = __dmul_rn(fcomp[md.mf0 + nu], Khat[md.pk_off + (int64_t)nu * md.nf + mu]);
     // explicit rounding of both products keeps K exactly symmetric (no FMA contraction)
-    K[e] = 0.5 * __dadd_rn(__dmul_rn(fcomp[mu], Khat[e]), __dmul_rn(fcomp[nu], Khat[(int64_t)nu * nf + mu]));
+    K[e] = 0.5 * __dadd_rn(a, b);
   }
 }
 
-// out2[0] = max |P - P^T|, out2[1] = max |P| (out2 zeroed by the caller).
-__global__ void symcheck_kernel(const double* __restrict__ P, int nf, double* __restrict__ out2) {
-  const int64_t n = (int64_t)nf * nf;
+// out2[0] = max |P - P^T|, out2[1] = max |P| over every molecule block (out2
+// zeroed by the caller); a non-finite entry gives +inf.
+__global__ void symcheck_kernel(const MolDesc* __restrict__ mols, int n_mol, int64_t packed,
+                                const double* __restrict__ P, double* __restrict__ out2) {
   double a = 0.0, b = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int mu = (int)(e / nf), nu = (int)(e % nf);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < packed; e += (int64_t)gridDim.x * blockDim.x) {
+    const MolDesc md = mols[mol_of_packed(mols, n_mol, e)];
+    const int64_t le = e - md.pk_off;
+    const int mu = (int)(le / md.nf), nu = (int)(le % md.nf);
     const double v = P[e];
-    a = fmax(a, fabs(v - P[(int64_t)nu * nf + mu]));
+    a = fmax(a, fabs(v - P[md.pk_off + (int64_t)nu * md.nf + mu]));
     b = fmax(b, fabs(v));
     if (!isfinite(v)) a = INFINITY;
   }
@@ -414,21 +581,22 @@ cudaError_t launch_collocation(cudaStream_t st, const BatchDesc* dbatch, int nba
 }
 
 cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nB, const double* ws,
-                               const double* w, const int* xfunc, int nf, double* phit_f, double* phit_b) {
+                               const double* w, const int* xfunc, double* phit_f, double* phit_b) {
   if (nbatch == 0) return cudaSuccess;
   if (max_nB > 0) {
     dim3 grid((max_nB + 127) / 128, nbatch);
-    phit_f_kernel<<<grid, 128, 0, st>>>(dbatch, ws, w, xfunc, nf, phit_f);
+    phit_f_kernel<<<grid, 128, 0, st>>>(dbatch, ws, w, xfunc, phit_f);
   }
   phit_b_kernel<<<nbatch, 256, 0, st>>>(dbatch, ws, w, phit_b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ftilde(cudaStream_t st, const double* P, const double* phit_f, int nf, int nbatch,
-                          const int* fshell, int ns, double* ft_shell) {
-  if (nbatch == 0) return cudaSuccess;
-  dim3 grid((nf + TM - 1) / TM, (nbatch + TN - 1) / TN);
-  ftilde_kernel<<<grid, GEMM_THREADS, 0, st>>>(P, phit_f, nf, nbatch, fshell, ns, ft_shell);
+cudaError_t launch_ftilde(cudaStream_t st, const MolDesc* mols, int n_mol, int max_nf, int max_nb,
+                          const BatchDesc* batches, const double* P, const double* phit_f, const int* fshell,
+                          double* ft_shell) {
+  if (n_mol == 0 || max_nf == 0 || max_nb == 0) return cudaSuccess;
+  dim3 grid((max_nf + TM - 1) / TM, (max_nb + TN - 1) / TN, n_mol);
+  ftilde_kernel<<<grid, GEMM_THREADS, 0, st>>>(mols, batches, P, phit_f, fshell, ft_shell);
   return cudaGetLastError();
 }
 
@@ -446,11 +614,25 @@ cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 }
 
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
-                         const double* P, int nf, const int* xfunc, const int* sfunc, const double* fcomp,
-                         const double* w, double* ws, float* ws32) {
+                         const double* P, const int* xfunc, const int* sfunc, const double* fcomp, const double* w,
+                         double* ws, float* ws32, bool tensor) {
   if (nbatch == 0 || max_ldq == 0 || max_nS == 0) return cudaSuccess;
   dim3 grid((max_ldq + TM - 1) / TM, (max_nS + TN - 1) / TN, nbatch);
-  fgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, nf, xfunc, sfunc, fcomp, w, ws, ws32);
+  if (tensor)
+    fgemm_kernel<true><<<grid, TC_THREADS, 0, st>>>(dbatch, P, xfunc, sfunc, fcomp, w, ws, ws32);
+  else
+    fgemm_kernel<false><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, xfunc, sfunc, fcomp, w, ws, ws32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, bool tensor) {
+  if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
+  dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
+  if (tensor)
+    kgemm_kernel<true><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
+  else
+    kgemm_kernel<false><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
   return cudaGetLastError();
 }
 
@@ -461,27 +643,19 @@ cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, int nf, const double* ws, double* Khat) {
-  if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
-  dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
-  kgemm_kernel<<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, nf, ws, Khat);
+cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* Khat,
+                          const double* fcomp, double* K) {
+  if (packed == 0) return cudaSuccess;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((packed + 255) / 256, 152 * 16));
+  finish_kernel<<<blocks, 256, 0, st>>>(mols, n_mol, packed, Khat, fcomp, K);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(cudaStream_t st, const double* Khat, const double* fcomp, int nf, double* K) {
-  int64_t n = (int64_t)nf * nf;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  if (blocks < 1) blocks = 1;
-  finish_kernel<<<blocks, 256, 0, st>>>(Khat, fcomp, nf, K);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_symcheck(cudaStream_t st, const double* P, int nf, double* out2) {
-  int64_t n = (int64_t)nf * nf;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-  if (blocks < 1) blocks = 1;
-  symcheck_kernel<<<blocks, 256, 0, st>>>(P, nf, out2);
+cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* P,
+                            double* out2) {
+  if (packed == 0) return cudaSuccess;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((packed + 255) / 256, 152 * 8));
+  symcheck_kernel<<<blocks, 256, 0, st>>>(mols, n_mol, packed, P, out2);
   return cudaGetLastError();
 }
 

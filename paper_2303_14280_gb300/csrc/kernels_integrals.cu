@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
     const double cx = a.xyz[3 * (bd.p0 + i)], cy = a.xyz[3 * (bd.p0 + i) + 1], cz = a.xyz[3 * (bd.p0 + i) + 2];
     const double* F = a.ws + bd.foff + i;
     double* G = a.ws + bd.goff + i;
-    const int* cmap = a.colmap + (int64_t)tile.batch * a.ns;
+    const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
     double ga[NA], fa[NA];
     int cur = -1, cola = 0;
     for (int k = tile.k0; k < tile.k1; ++k) {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     const int64_t ldq = bd.ldq;
     const float* F = a.ws32 + bd.foff32 + i;
     float* G = a.ws32 + bd.goff32 + i;
-    const int* cmap = a.colmap + (int64_t)tile.batch * a.ns;
+    const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
     float ga[NA], fa[NA];
     int cur = -1, cola = 0;
     for (int k = tile.k0; k < tile.k1; ++k) {

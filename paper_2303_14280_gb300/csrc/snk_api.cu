@@ -2,6 +2,10 @@
 // screen and the K build driver (Alg. 1 of the paper on one GPU: batches are
 // processed in chunks whose intermediates X, F, G fit a preallocated device
 // workspace; every chunk adds its contribution to one K-tilde accumulator).
+//
+// A handle holds one or several independent molecules.  Their batches share
+// every launch: the screen, the products and the integral kernels run over
+// the batches of all molecules at once, with P and K packed per molecule.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,8 +42,10 @@ struct DevBuf {
   }
 };
 
-// pairs per integral tile for each class: cheap classes take longer runs
+// pairs per integral tile for each class (cheap classes take longer runs);
+// the autotuner replaces these per list
 constexpr int kPairsPerTile[kNumClasses] = {64, 32, 16, 16, 8, 8};
+constexpr int kRunCandidates[] = {2, 4, 8, 16, 32, 64, 128};
 constexpr int kPhaseEvents = 3 + kNumLists;  // per chunk: collocation, F GEMM, integral lists, K GEMM
 
 }  // namespace
@@ -52,6 +58,7 @@ struct snk_ctx {
   std::string err;
   int nbatch = 0;
   int64_t ws_budget = 0;
+  int run[kNumLists];  // pairs per tile, per list
 
   // geometry (device)
   DevBuf<int> l, poff, nprim, foff, fshell, bshell, bshell_col, xfunc;
@@ -59,6 +66,8 @@ struct snk_ctx {
   DevBuf<float> boys_f;
   DevBuf<PairHdr> pairs;
   DevBuf<PrimPair> prims;
+  DevBuf<MolDesc> mols;
+  int max_nf = 0, max_nb = 0;
 
   // density-dependent state
   bool have_density = false;
@@ -74,6 +83,7 @@ struct snk_ctx {
   std::vector<int> hcounts;
   std::vector<long long> hpp;
   std::vector<int64_t> hlist_off;
+  std::vector<BatchDesc> hbatch;
 
   struct Chunk {
     int b0 = 0, b1 = 0;
@@ -84,17 +94,28 @@ struct snk_ctx {
   std::vector<Chunk> chunks;
   int max_ctas[kNumLists] = {0};
 
+  // CUDA graph of the build (options.graph)
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double* gout = nullptr;
+  bool graph_valid = false;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
   // timing
   std::vector<cudaEvent_t> events;
   cudaEvent_t ev_screen0 = nullptr, ev_screen1 = nullptr;
   int64_t launches_density = 0, launches_build = 0;
-  bool built = false;
+  bool built = false, built_graph = false;
   snk_stats st;
 
   ~snk_ctx() {
     for (auto e : events) cudaEventDestroy(e);
     if (ev_screen0) cudaEventDestroy(ev_screen0);
     if (ev_screen1) cudaEventDestroy(ev_screen1);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (gstream) cudaStreamDestroy(gstream);
   }
 };
 
@@ -110,9 +131,9 @@ int cuda_fail(snk_ctx* c, cudaError_t e, const char* where) {
   return fail(c, e == cudaErrorMemoryAllocation ? SNK_ERR_OOM : SNK_ERR_CUDA, m);
 }
 
-#define SNK_CK(ctx, call)                                  \
-  do {                                                     \
-    cudaError_t _e = (call);                               \
+#define SNK_CK(ctx, call)                                    \
+  do {                                                       \
+    cudaError_t _e = (call);                                 \
     if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
   } while (0)
 
@@ -138,33 +159,47 @@ DeviceBasis dev_basis(snk_ctx* c) {
   return b;
 }
 
+// geometry part of a batch descriptor (no workspace offsets)
+BatchDesc geometry_desc(const Setup& s, int j) {
+  BatchDesc b{};
+  const Setup::Mol& m = s.mols[s.bmol[j]];
+  b.p0 = s.bstart[j];
+  b.q = (int)(s.bstart[j + 1] - s.bstart[j]);
+  b.ldq = (int)round_up(std::max(b.q, 1), kLdqAlign);
+  b.nB = s.bnf[j];
+  b.xfunc_off = s.xfunc_off[j];
+  b.bshell_off = s.bshell_off[j];
+  b.nBshell = s.bshell_off[j + 1] - s.bshell_off[j];
+  b.mol = s.bmol[j];
+  b.ms0 = m.ms0;
+  b.mf0 = m.mf0;
+  b.nfm = m.nf;
+  b.pk_off = m.pk_off;
+  b.cm_off = s.cm_off[j];
+  b.phf_off = s.phf_off[j];
+  return b;
+}
+
 // Geometry-only screen maxima Phi-tilde and phi-tilde (Eq. exx_fmat_approx):
 // collocate the batches chunk by chunk and reduce.
 int geometry_screen(snk_ctx* c) {
   Setup& s = c->s;
   const int nb = c->nbatch;
-  SNK_CK(c, c->phit_f.ensure((size_t)std::max(nb, 1) * s.nf));
+  SNK_CK(c, c->phit_f.ensure((size_t)std::max<int64_t>(s.phf_total, 1)));
   SNK_CK(c, c->phit_b.ensure(std::max(nb, 1)));
-  SNK_CK(c, cudaMemsetAsync(c->phit_f.p, 0, sizeof(double) * (size_t)std::max(nb, 1) * s.nf, c->stream));
+  SNK_CK(c, cudaMemsetAsync(c->phit_f.p, 0, sizeof(double) * std::max<int64_t>(s.phf_total, 1), c->stream));
   SNK_CK(c, cudaMemsetAsync(c->phit_b.p, 0, sizeof(double) * std::max(nb, 1), c->stream));
   if (nb == 0) return SNK_OK;
   std::vector<BatchDesc> bd(nb);
+  SNK_CK(c, c->batch.ensure(nb));
   int j = 0;
   while (j < nb) {
     int64_t off = 0;
     int j0 = j, max_ldq = 0, max_nBs = 0, max_nB = 0;
     while (j < nb) {
-      BatchDesc b{};
-      b.p0 = s.bstart[j];
-      b.q = (int)(s.bstart[j + 1] - s.bstart[j]);
-      b.ldq = (int)round_up(std::max(b.q, 1), kLdqAlign);
-      b.nB = s.bnf[j];
-      b.nS = 0;
-      b.xfunc_off = s.xfunc_off[j];
-      b.bshell_off = s.bshell_off[j];
-      b.nBshell = s.bshell_off[j + 1] - s.bshell_off[j];
+      BatchDesc b = geometry_desc(s, j);
       int64_t bytes = (int64_t)b.ldq * b.nB * 8;
-      if (j > j0 && (off + bytes) * 1 > c->ws_budget) break;
+      if (j > j0 && off * 8 + bytes > c->ws_budget) break;
       b.xoff = off;
       off += (int64_t)b.ldq * b.nB;
       bd[j] = b;
@@ -174,14 +209,12 @@ int geometry_screen(snk_ctx* c) {
       ++j;
     }
     SNK_CK(c, c->ws.ensure((size_t)std::max<int64_t>(off, 1)));
-    SNK_CK(c, c->batch.ensure(nb));
     SNK_CK(c, cudaMemcpyAsync(c->batch.p + j0, bd.data() + j0, sizeof(BatchDesc) * (j - j0), cudaMemcpyHostToDevice,
                               c->stream));
     SNK_CK(c, launch_collocation(c->stream, c->batch.p + j0, j - j0, max_ldq, max_nBs, c->bshell.p, c->bshell_col.p,
                                  c->xyz.p, dev_basis(c), c->ws.p));
-    // the phit kernels index phit_f / phit_b by blockIdx relative to batch j0
-    SNK_CK(c, launch_screen_geom(c->stream, c->batch.p + j0, j - j0, max_nB, c->ws.p, c->w.p, c->xfunc.p, s.nf,
-                                 c->phit_f.p + (size_t)j0 * s.nf, c->phit_b.p + j0));
+    SNK_CK(c, launch_screen_geom(c->stream, c->batch.p + j0, j - j0, max_nB, c->ws.p, c->w.p, c->xfunc.p,
+                                 c->phit_f.p, c->phit_b.p + j0));
     SNK_CK(c, cudaStreamSynchronize(c->stream));
   }
   return SNK_OK;
@@ -196,19 +229,53 @@ int ensure_events(snk_ctx* c, size_t n) {
   return SNK_OK;
 }
 
+// Integral tiles per (chunk, list): (batch, run of pairs, 128-point slab),
+// larger tiles first so that the persistent CTAs finish together.
+void make_tiles(snk_ctx* c, std::vector<Tile>& htiles) {
+  htiles.clear();
+  const auto& bd = c->hbatch;
+  for (auto& ch : c->chunks)
+    for (int k = 0; k < kNumLists; ++k) {
+      ch.tile_off[k] = (int64_t)htiles.size();
+      size_t first = htiles.size();
+      const int run = c->run[k];
+      for (int t = ch.b0; t < ch.b1; ++t) {
+        int64_t n = c->hcounts[(size_t)t * kNumLists + k];
+        int64_t base = c->hlist_off[(size_t)t * kNumLists + k];
+        for (int64_t k0 = 0; k0 < n; k0 += run)
+          for (int i0 = 0; i0 < bd[t].q; i0 += kPointTile) {
+            Tile tl;
+            tl.batch = t;
+            tl.k0 = (int)(base + k0);
+            tl.k1 = (int)(base + std::min<int64_t>(n, k0 + run));
+            tl.i0 = i0;
+            htiles.push_back(tl);
+          }
+      }
+      std::stable_sort(htiles.begin() + first, htiles.end(), [&](const Tile& x, const Tile& y) {
+        int64_t cx = (int64_t)(x.k1 - x.k0) * std::min(kPointTile, bd[x.batch].q - x.i0);
+        int64_t cy = (int64_t)(y.k1 - y.k0) * std::min(kPointTile, bd[y.batch].q - y.i0);
+        return cx > cy;
+      });
+      ch.tile_n[k] = (int64_t)htiles.size() - ch.tile_off[k];
+    }
+  if (htiles.empty()) htiles.push_back(Tile{0, 0, 0, 0});
+}
+
 // Density-dependent part of set_density once P is on the device.
 int screen_and_plan(snk_ctx* c) {
   Setup& s = c->s;
-  const int nb = c->nbatch, ns = s.ns, nf = s.nf;
+  const int nb = c->nbatch;
   const cudaStream_t st = c->stream;
   const bool mixed = c->opt.precision == SNK_PREC_MIXED;
   c->have_density = false;
+  c->graph_valid = false;
   c->launches_density = 0;
   SNK_CK(c, cudaEventRecord(c->ev_screen0, st));
-  // symmetry check
+  // symmetry check of every molecule block
   SNK_CK(c, c->sym.ensure(2));
   SNK_CK(c, cudaMemsetAsync(c->sym.p, 0, 2 * sizeof(double), st));
-  SNK_CK(c, launch_symcheck(st, c->P.p, nf, c->sym.p));
+  SNK_CK(c, launch_symcheck(st, c->mols.p, s.n_mol, s.packed, c->P.p, c->sym.p));
   ++c->launches_density;
   double hsym[2];
   SNK_CK(c, cudaMemcpyAsync(hsym, c->sym.p, sizeof(hsym), cudaMemcpyDeviceToHost, st));
@@ -217,19 +284,27 @@ int screen_and_plan(snk_ctx* c) {
     return fail(c, std::isfinite(hsym[0]) ? SNK_ERR_NOT_SYMMETRIC : SNK_ERR_UNSUPPORTED,
                 "density matrix is not symmetric (or not finite)");
   const int nbx = std::max(nb, 1);
+  const size_t cmn = (size_t)std::max<int64_t>(s.cm_total, 1);
   // F-tilde and the pair screen, Eqs. (exx_fmat_approx), (sp_set)
-  SNK_CK(c, c->ft.ensure((size_t)nbx * ns));
+  SNK_CK(c, c->ft.ensure(cmn));
   SNK_CK(c, c->counts.ensure((size_t)nbx * kNumLists));
   SNK_CK(c, c->ppcounts.ensure((size_t)nbx * kNumLists));
-  SNK_CK(c, c->sflag.ensure((size_t)nbx * ns));
-  SNK_CK(c, cudaMemsetAsync(c->ft.p, 0, sizeof(double) * nbx * ns, st));
-  SNK_CK(c, cudaMemsetAsync(c->sflag.p, 0, (size_t)nbx * ns, st));
+  SNK_CK(c, c->sflag.ensure(cmn));
+  SNK_CK(c, cudaMemsetAsync(c->ft.p, 0, sizeof(double) * cmn, st));
+  SNK_CK(c, cudaMemsetAsync(c->sflag.p, 0, cmn, st));
   const int screen = c->opt.screen == SNK_SCREEN_NONE ? SNK_SCREEN_NONE : SNK_SCREEN_LINK;
+  // geometry descriptors for the screen kernels
+  c->hbatch.assign(nbx, BatchDesc{});
+  for (int j = 0; j < nb; ++j) c->hbatch[j] = geometry_desc(s, j);
+  SNK_CK(c, upload(c->batch, c->hbatch, st));
   if (screen != SNK_SCREEN_NONE) {
-    SNK_CK(c, launch_ftilde(st, c->P.p, c->phit_f.p, nf, nb, c->fshell.p, ns, c->ft.p));
+    SNK_CK(c, launch_ftilde(st, c->mols.p, s.n_mol, c->max_nf, c->max_nb, c->batch.p, c->P.p, c->phit_f.p,
+                            c->fshell.p, c->ft.p));
     ++c->launches_density;
   }
   ScreenArgs sa;
+  sa.mols = c->mols.p;
+  sa.batches = c->batch.p;
   sa.pairs = c->pairs.p;
   sa.bound = c->bound.p;
   sa.qbound = c->qbound.p;
@@ -238,23 +313,21 @@ int screen_and_plan(snk_ctx* c) {
   sa.bradius = c->bradius.p;
   sa.ft_shell = c->ft.p;
   sa.phit_b = c->phit_b.p;
-  sa.ns = ns;
   sa.screen = screen;
   sa.distance = c->opt.distance_bound ? 1 : 0;
   sa.mixed = mixed ? 1 : 0;
   sa.eps_E = c->opt.eps_E;
   sa.eps_K = c->opt.eps_K;
   sa.fp32_bound = c->opt.fp32_bound;
-  for (int k = 0; k <= kNumClasses; ++k) sa.cr.b[k] = s.class_begin[k];
   SNK_CK(c, launch_pair_count(st, sa, nb, c->counts.p, c->ppcounts.p, c->sflag.p));
   ++c->launches_density;
   c->hcounts.assign((size_t)nbx * kNumLists, 0);
   c->hpp.assign((size_t)nbx * kNumLists, 0);
-  std::vector<unsigned char> hflag((size_t)nbx * ns);
+  std::vector<unsigned char> hflag(cmn);
   SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumLists, cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaMemcpyAsync(c->hpp.data(), c->ppcounts.p, sizeof(long long) * nbx * kNumLists, cudaMemcpyDeviceToHost,
                             st));
-  SNK_CK(c, cudaMemcpyAsync(hflag.data(), c->sflag.p, (size_t)nbx * ns, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(hflag.data(), c->sflag.p, cmn, cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
   // pair lists: offsets, then the deterministic compaction pass
@@ -273,27 +346,21 @@ int screen_and_plan(snk_ctx* c) {
   SNK_CK(c, launch_pair_write(st, sa, nb, c->list_off.p, c->list.p));
   ++c->launches_density;
 
-  // shells of V_j -> F / G columns; batch descriptors
-  std::vector<int> hcolmap((size_t)nbx * ns, -1), hsfunc;
-  std::vector<BatchDesc> bd(nbx);
+  // shells of V_j -> F / G columns (molecule-local function indices)
+  std::vector<int> hcolmap(cmn, -1), hsfunc;
+  auto& bd = c->hbatch;
   c->chunks.clear();
   for (int j = 0; j < nb; ++j) {
     BatchDesc& b = bd[j];
-    b = BatchDesc{};
-    b.p0 = s.bstart[j];
-    b.q = (int)(s.bstart[j + 1] - s.bstart[j]);
-    b.ldq = (int)round_up(std::max(b.q, 1), kLdqAlign);
-    b.nB = s.bnf[j];
-    b.xfunc_off = s.xfunc_off[j];
-    b.bshell_off = s.bshell_off[j];
-    b.nBshell = s.bshell_off[j + 1] - s.bshell_off[j];
+    const Setup::Mol& m = s.mols[b.mol];
     b.sfunc_off = (int)hsfunc.size();
     int col = 0;
-    for (int a = 0; a < ns; ++a)
-      if (hflag[(size_t)j * ns + a]) {
-        hcolmap[(size_t)j * ns + a] = col;
-        for (int u = 0; u < ncart(s.l[a]); ++u) hsfunc.push_back(s.foff[a] + u);
-        col += ncart(s.l[a]);
+    for (int a = 0; a < m.ns; ++a)
+      if (hflag[(size_t)b.cm_off + a]) {
+        hcolmap[(size_t)b.cm_off + a] = col;
+        const int g = m.ms0 + a;
+        for (int u = 0; u < ncart(s.l[g]); ++u) hsfunc.push_back(s.foff[g] - m.mf0 + u);
+        col += ncart(s.l[g]);
       }
     b.nS = col;
   }
@@ -366,38 +433,11 @@ int screen_and_plan(snk_ctx* c) {
   if (mixed) SNK_CK(c, c->ws32.ensure((size_t)need32));
   SNK_CK(c, upload(c->batch, bd, st));
 
-  // integral tiles per (chunk, list): (batch, pair run, 128-point slab),
-  // larger runs first so that the persistent CTAs finish together
   std::vector<Tile> htiles;
-  for (auto& ch : c->chunks)
-    for (int k = 0; k < kNumLists; ++k) {
-      ch.tile_off[k] = (int64_t)htiles.size();
-      size_t first = htiles.size();
-      const int run = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
-      for (int t = ch.b0; t < ch.b1; ++t) {
-        int64_t n = c->hcounts[(size_t)t * kNumLists + k];
-        int64_t base = c->hlist_off[(size_t)t * kNumLists + k];
-        for (int64_t k0 = 0; k0 < n; k0 += run)
-          for (int i0 = 0; i0 < bd[t].q; i0 += kPointTile) {
-            Tile tl;
-            tl.batch = t;
-            tl.k0 = (int)(base + k0);
-            tl.k1 = (int)(base + std::min<int64_t>(n, k0 + run));
-            tl.i0 = i0;
-            htiles.push_back(tl);
-          }
-      }
-      std::stable_sort(htiles.begin() + first, htiles.end(), [&](const Tile& x, const Tile& y) {
-        int64_t cx = (int64_t)(x.k1 - x.k0) * std::min(kPointTile, bd[x.batch].q - x.i0);
-        int64_t cy = (int64_t)(y.k1 - y.k0) * std::min(kPointTile, bd[y.batch].q - y.i0);
-        return cx > cy;
-      });
-      ch.tile_n[k] = (int64_t)htiles.size() - ch.tile_off[k];
-    }
-  if (htiles.empty()) htiles.push_back(Tile{0, 0, 0, 0});
+  make_tiles(c, htiles);
   SNK_CK(c, upload(c->tiles, htiles, st));
   SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
-  SNK_CK(c, c->Khat.ensure((size_t)nf * nf));
+  SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(s.packed, 1)));
   SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
@@ -426,18 +466,35 @@ int screen_and_plan(snk_ctx* c) {
   return SNK_OK;
 }
 
-int build(snk_ctx* c, double* dK) {
-  if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_build_K called before snk_set_density");
+IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
+  const auto& ch = c->chunks[ci];
+  IntegralArgs a;
+  a.tiles = c->tiles.p + ch.tile_off[k];
+  a.n_tiles = (int)ch.tile_n[k];
+  a.ticket = c->tickets.p + ci * kNumLists + k;
+  a.batches = c->batch.p;
+  a.pairlist = c->list.p;
+  a.pairs = c->pairs.p;
+  a.prims = c->prims.p;
+  a.colmap = c->colmap.p;
+  a.xyz = c->xyz.p;
+  a.boys = c->boys.p;
+  a.ws = c->ws.p;
+  a.boys_f = c->boys_f.p;
+  a.ws32 = c->ws32.p;
+  a.bcenter = c->bcenter.p;
+  return a;
+}
+
+// The build on stream st; timing events only when `timed` (they are left out
+// of a captured graph).
+int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   Setup& s = c->s;
-  const cudaStream_t st = c->stream;
-  const int nf = s.nf;
   const bool mixed = c->opt.precision == SNK_PREC_MIXED;
-  const size_t nev = c->chunks.size() * kPhaseEvents + 2;
-  if (int rc = ensure_events(c, nev)) return rc;
-  c->launches_build = 0;
   int ev = 0;
-  SNK_CK(c, cudaEventRecord(c->events[ev++], st));
-  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)nf * nf, st));
+  c->launches_build = 0;
+  if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)std::max<int64_t>(s.packed, 1), st));
   SNK_CK(c, cudaMemsetAsync(c->tickets.p, 0, sizeof(int) * c->tickets.n, st));
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const auto& ch = c->chunks[ci];
@@ -447,66 +504,106 @@ int build(snk_ctx* c, double* dK) {
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
     ++c->launches_build;
-    SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     // F_j = X_j P (w and component factors folded in), Eq. (batch_local_exx)
-    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nf, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
-                           c->ws.p, mixed ? c->ws32.p : nullptr));
+    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
+                           c->ws.p, mixed ? c->ws32.p : nullptr, mixed && (c->opt.tensor_gemms & 1)));
     ++c->launches_build;
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
     if (mixed) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
-    SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, list by list
     for (int k = 0; k < kNumLists; ++k) {
-      IntegralArgs a;
-      a.tiles = c->tiles.p + ch.tile_off[k];
-      a.n_tiles = (int)ch.tile_n[k];
-      a.ticket = c->tickets.p + ci * kNumLists + k;
-      a.batches = c->batch.p;
-      a.pairlist = c->list.p;
-      a.pairs = c->pairs.p;
-      a.prims = c->prims.p;
-      a.colmap = c->colmap.p;
-      a.ns = s.ns;
-      a.xyz = c->xyz.p;
-      a.boys = c->boys.p;
-      a.ws = c->ws.p;
-      a.boys_f = c->boys_f.p;
-      a.ws32 = c->ws32.p;
-      a.bcenter = c->bcenter.p;
+      IntegralArgs a = integral_args(c, ci, k);
       if (a.n_tiles > 0) {
-        int grid = std::min<int64_t>(c->max_ctas[k], a.n_tiles);
+        int grid = (int)std::min<int64_t>(c->max_ctas[k], a.n_tiles);
         SNK_CK(c, launch_integrals(st, k, a, grid));
         ++c->launches_build;
       }
-      SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+      if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     }
     // the FP32 pairs' G into the FP64 G, then Kt += G_j^T X_j, Eq. (usym_k)
     if (mixed && ch.g32n > 0) {
       SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
       ++c->launches_build;
     }
-    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, nf, c->ws.p, c->Khat.p));
+    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p,
+                           mixed && (c->opt.tensor_gemms & 2)));
     ++c->launches_build;
-    SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
   }
-  // K = (Kt + Kt^T) / 2, Eq. (sn_k)
-  SNK_CK(c, launch_finish(st, c->Khat.p, c->fcomp.p, nf, dK));
+  // K = (Kt + Kt^T) / 2 in every molecule block, Eq. (sn_k)
+  SNK_CK(c, launch_finish(st, c->mols.p, s.n_mol, s.packed, c->Khat.p, c->fcomp.p, dK));
   ++c->launches_build;
-  SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  return SNK_OK;
+}
+
+int build(snk_ctx* c, double* dK) {
+  if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_build_K called before snk_set_density");
+  if (!c->opt.graph) {
+    if (int rc = ensure_events(c, c->chunks.size() * kPhaseEvents + 2)) return rc;
+    if (int rc = enqueue_build(c, c->stream, dK, true)) return rc;
+    c->built = true;
+    c->built_graph = false;
+    return SNK_OK;
+  }
+  // CUDA-graph form: capture the whole build once per plan and output buffer,
+  // replay it afterwards; ordered after / before the caller's stream by events
+  if (int rc = ensure_events(c, 2)) return rc;
+  if (!c->gstream) SNK_CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+  if (!c->ev_in) SNK_CK(c, cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  if (!c->ev_out) SNK_CK(c, cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  if (!c->graph_valid || c->gout != dK) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    SNK_CK(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_build(c, c->gstream, dK, false);
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+    if (rc != SNK_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    c->graph_valid = true;
+    c->gout = dK;
+  }
+  SNK_CK(c, cudaEventRecord(c->events[0], c->stream));
+  SNK_CK(c, cudaEventRecord(c->ev_in, c->stream));
+  SNK_CK(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0));
+  SNK_CK(c, cudaGraphLaunch(c->gexec, c->gstream));
+  SNK_CK(c, cudaEventRecord(c->ev_out, c->gstream));
+  SNK_CK(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+  SNK_CK(c, cudaEventRecord(c->events[1], c->stream));
   c->built = true;
+  c->built_graph = true;
   return SNK_OK;
 }
 
 void collect_times(snk_ctx* c) {
   if (!c->built) return;
-  const int last = (int)c->chunks.size() * kPhaseEvents + 1;  // the event after the finish kernel
-  if (cudaEventSynchronize(c->events[last]) != cudaSuccess) return;
   auto el = [&](int a, int b) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->events[a], c->events[b]);
     return (double)ms;
   };
   snk_stats& st = c->st;
+  st.kernel_launches = c->launches_density + c->launches_build;
+  if (c->built_graph) {
+    if (cudaEventSynchronize(c->events[1]) != cudaSuccess) return;
+    st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = st.ms_integrals_fp32 = st.ms_finish = 0.0;
+    for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = 0.0;
+    st.ms_build = el(0, 1);
+    return;
+  }
+  const int last = (int)c->chunks.size() * kPhaseEvents + 1;  // the event after the finish kernel
+  if (cudaEventSynchronize(c->events[last]) != cudaSuccess) return;
   st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = st.ms_integrals_fp32 = 0.0;
   for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = 0.0;
   int ev = 0;
@@ -528,42 +625,76 @@ void collect_times(snk_ctx* c) {
   }
   st.ms_finish = el(ev, ev + 1);
   st.ms_build = el(0, ev + 1);
-  st.kernel_launches = c->launches_density + c->launches_build;
 }
 
-}  // namespace
-
-extern "C" {
-
-void snk_options_default(snk_options* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->eps_basis = 1e-12;
-  o->eps_E = 1e-12;
-  o->eps_K = 1e-12;
-  o->batch_max = 4096;
-  o->precision = SNK_PREC_FP64;
-  o->screen = SNK_SCREEN_LINK;
-  o->fp32_bound = 1e-6;
-  o->workspace_bytes = 0;
-  o->distance_bound = 1;
-}
-
-const char* snk_status_string(int status) {
-  switch (status) {
-    case SNK_OK: return "ok";
-    case SNK_ERR_INVALID_ARG: return "invalid argument";
-    case SNK_ERR_UNSUPPORTED: return "unsupported input";
-    case SNK_ERR_NOT_SYMMETRIC: return "density matrix not symmetric";
-    case SNK_ERR_BAD_STATE: return "bad call order";
-    case SNK_ERR_OOM: return "out of memory";
-    case SNK_ERR_CUDA: return "CUDA error";
-    case SNK_ERR_TIMEOUT: return "device wait timed out";
+// Autotuner: for every integral list, time the list's kernel on the last
+// chunk's tiles for each candidate run of pairs per tile, keep the fastest.
+// The workspace holds that chunk's X and F after a build; the kernel's G
+// output is garbage afterwards, so the caller's next build recomputes it.
+int autotune(snk_ctx* c, int32_t* runs_out) {
+  if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_autotune called before snk_set_density");
+  if (c->chunks.empty()) {
+    if (runs_out)
+      for (int k = 0; k < kNumLists; ++k) runs_out[k] = c->run[k];
+    return SNK_OK;
   }
-  return "unknown status";
+  const bool graph = c->opt.graph;
+  c->opt.graph = 0;
+  SNK_CK(c, c->K.ensure((size_t)std::max<int64_t>(c->s.packed, 1)));
+  int rc = build(c, c->K.p);
+  c->opt.graph = graph;
+  if (rc != SNK_OK) return rc;
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  const size_t ci = c->chunks.size() - 1;
+  cudaEvent_t e0, e1;
+  SNK_CK(c, cudaEventCreate(&e0));
+  SNK_CK(c, cudaEventCreate(&e1));
+  std::vector<Tile> htiles;
+  for (int k = 0; k < kNumLists; ++k) {
+    if (c->chunks[ci].tile_n[k] == 0) continue;
+    double best = 1e300;
+    int best_run = c->run[k];
+    for (int r : kRunCandidates) {
+      c->run[k] = r;
+      make_tiles(c, htiles);
+      if ((rc = [&]() -> int {
+             SNK_CK(c, upload(c->tiles, htiles, c->stream));
+             double t = 1e300;
+             for (int rep = 0; rep < 2; ++rep) {
+               IntegralArgs a = integral_args(c, ci, k);
+               SNK_CK(c, cudaMemsetAsync(a.ticket, 0, sizeof(int), c->stream));
+               SNK_CK(c, cudaEventRecord(e0, c->stream));
+               SNK_CK(c, launch_integrals(c->stream, k, a, (int)std::min<int64_t>(c->max_ctas[k], a.n_tiles)));
+               SNK_CK(c, cudaEventRecord(e1, c->stream));
+               SNK_CK(c, cudaEventSynchronize(e1));
+               float ms = 0.f;
+               cudaEventElapsedTime(&ms, e0, e1);
+               t = std::min(t, (double)ms);
+             }
+             if (t < best) {
+               best = t;
+               best_run = r;
+             }
+             return SNK_OK;
+           }()) != SNK_OK)
+        break;
+    }
+    c->run[k] = best_run;
+    if (rc != SNK_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SNK_OK) return rc;
+  make_tiles(c, htiles);
+  SNK_CK(c, upload(c->tiles, htiles, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  c->graph_valid = false;
+  if (runs_out)
+    for (int k = 0; k < kNumLists; ++k) runs_out[k] = c->run[k];
+  return SNK_OK;
 }
 
-int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, snk_ctx** out) {
+int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_options* opt, snk_ctx** out) {
   if (!out) return SNK_ERR_INVALID_ARG;
   *out = nullptr;
   std::unique_ptr<snk_ctx> c(new (std::nothrow) snk_ctx());
@@ -573,7 +704,8 @@ int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* 
   else
     snk_options_default(&c->opt);
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
-  int rc = build_setup(basis, grid, &c->opt, &c->s, &c->err);
+  for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
+  int rc = build_setup(n_mol, bases, grids, &c->opt, &c->s, &c->err);
   if (rc != SNK_OK) return rc;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) return SNK_ERR_CUDA;
@@ -594,15 +726,29 @@ int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* 
       col += ncart(s.l[s.bshell[t]]);
     }
   }
+  std::vector<MolDesc> hm(s.n_mol);
+  for (int m = 0; m < s.n_mol; ++m) {
+    const Setup::Mol& M = s.mols[m];
+    MolDesc& d = hm[m];
+    d = MolDesc{};
+    d.pk_off = M.pk_off;
+    d.nf = M.nf;
+    d.ns = M.ns;
+    d.ms0 = M.ms0;
+    d.mf0 = M.mf0;
+    d.mb0 = M.mb0;
+    d.nb = M.nb;
+    for (int k = 0; k <= kNumClasses; ++k) d.cr[k] = M.cr[k];
+    c->max_nf = std::max(c->max_nf, M.nf);
+    c->max_nb = std::max(c->max_nb, M.nb);
+  }
   snk_ctx* cp = c.get();
   const cudaStream_t st = cp->stream;
-  std::vector<int> nprim(s.nprim);
-  std::vector<int> poff(s.poff.begin(), s.poff.end()), foff(s.foff.begin(), s.foff.end());
   if ((rc = [&]() -> int {
          SNK_CK(cp, upload(cp->l, s.l, st));
-         SNK_CK(cp, upload(cp->poff, poff, st));
-         SNK_CK(cp, upload(cp->nprim, nprim, st));
-         SNK_CK(cp, upload(cp->foff, foff, st));
+         SNK_CK(cp, upload(cp->poff, s.poff, st));
+         SNK_CK(cp, upload(cp->nprim, s.nprim, st));
+         SNK_CK(cp, upload(cp->foff, s.foff, st));
          SNK_CK(cp, upload(cp->fshell, s.fshell, st));
          SNK_CK(cp, upload(cp->center, s.center, st));
          SNK_CK(cp, upload(cp->exps, s.exps, st));
@@ -621,6 +767,7 @@ int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* 
          SNK_CK(cp, upload(cp->bshell_col, s.bshell_col, st));
          SNK_CK(cp, upload(cp->xfunc, s.xfunc, st));
          SNK_CK(cp, upload(cp->boys, s.boys, st));
+         SNK_CK(cp, upload(cp->mols, hm, st));
          SNK_CK(cp, cudaStreamSynchronize(st));
          return SNK_OK;
        }()) != SNK_OK)
@@ -637,23 +784,82 @@ int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* 
   return SNK_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+void snk_options_default(snk_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps_basis = 1e-12;
+  o->eps_E = 1e-12;
+  o->eps_K = 1e-12;
+  o->batch_max = 4096;
+  o->precision = SNK_PREC_FP64;
+  o->screen = SNK_SCREEN_LINK;
+  o->fp32_bound = 1e-6;
+  o->workspace_bytes = 0;
+  o->distance_bound = 1;
+  o->tensor_gemms = 0;
+  o->graph = 0;
+}
+
+const char* snk_status_string(int status) {
+  switch (status) {
+    case SNK_OK: return "ok";
+    case SNK_ERR_INVALID_ARG: return "invalid argument";
+    case SNK_ERR_UNSUPPORTED: return "unsupported input";
+    case SNK_ERR_NOT_SYMMETRIC: return "density matrix not symmetric";
+    case SNK_ERR_BAD_STATE: return "bad call order";
+    case SNK_ERR_OOM: return "out of memory";
+    case SNK_ERR_CUDA: return "CUDA error";
+    case SNK_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+int snk_create(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, snk_ctx** out) {
+  if (!basis || !grid) return SNK_ERR_INVALID_ARG;
+  return create(1, basis, grid, opt, out);
+}
+
+int snk_create_batch(int32_t n_mol, const snk_basis* bases, const snk_grid* grids, const snk_options* opt,
+                     snk_ctx** out) {
+  if (n_mol < 1 || !bases || !grids) return SNK_ERR_INVALID_ARG;
+  return create(n_mol, bases, grids, opt, out);
+}
+
 int snk_set_density(snk_ctx* c, const double* P) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!P) return fail(c, SNK_ERR_INVALID_ARG, "NULL density");
-  const size_t n = (size_t)c->s.nf * c->s.nf;
+  const size_t n = (size_t)c->s.packed;
   c->have_density = false;
-  SNK_CK(c, c->P.ensure(n));
-  SNK_CK(c, cudaMemcpyAsync(c->P.p, P, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  SNK_CK(c, c->P.ensure(std::max<size_t>(n, 1)));
+  if (n) SNK_CK(c, cudaMemcpyAsync(c->P.p, P, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
   return screen_and_plan(c);
 }
 
 int snk_set_density_device(snk_ctx* c, const double* dP) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!dP) return fail(c, SNK_ERR_INVALID_ARG, "NULL density");
-  const size_t n = (size_t)c->s.nf * c->s.nf;
+  const size_t n = (size_t)c->s.packed;
   c->have_density = false;
-  SNK_CK(c, c->P.ensure(n));
-  SNK_CK(c, cudaMemcpyAsync(c->P.p, dP, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  SNK_CK(c, c->P.ensure(std::max<size_t>(n, 1)));
+  if (n) SNK_CK(c, cudaMemcpyAsync(c->P.p, dP, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  return screen_and_plan(c);
+}
+
+int snk_set_density_batch(snk_ctx* c, const double* const* P) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!P) return fail(c, SNK_ERR_INVALID_ARG, "NULL density list");
+  c->have_density = false;
+  SNK_CK(c, c->P.ensure(std::max<size_t>((size_t)c->s.packed, 1)));
+  for (int m = 0; m < c->s.n_mol; ++m) {
+    if (!P[m]) return fail(c, SNK_ERR_INVALID_ARG, "NULL density for molecule " + std::to_string(m));
+    const auto& M = c->s.mols[m];
+    SNK_CK(c, cudaMemcpyAsync(c->P.p + M.pk_off, P[m], sizeof(double) * M.nf * M.nf, cudaMemcpyHostToDevice,
+                              c->stream));
+  }
   return screen_and_plan(c);
 }
 
@@ -666,13 +872,35 @@ int snk_build_K_device(snk_ctx* c, double* dK) {
 int snk_build_K(snk_ctx* c, double* K) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!K) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
-  const size_t n = (size_t)c->s.nf * c->s.nf;
-  SNK_CK(c, c->K.ensure(n));
+  const size_t n = (size_t)c->s.packed;
+  SNK_CK(c, c->K.ensure(std::max<size_t>(n, 1)));
   int rc = build(c, c->K.p);
   if (rc != SNK_OK) return rc;
-  SNK_CK(c, cudaMemcpyAsync(K, c->K.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  if (n) SNK_CK(c, cudaMemcpyAsync(K, c->K.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   SNK_CK(c, cudaStreamSynchronize(c->stream));
   return SNK_OK;
+}
+
+int snk_build_K_batch(snk_ctx* c, double* const* K) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!K) return fail(c, SNK_ERR_INVALID_ARG, "NULL output list");
+  for (int m = 0; m < c->s.n_mol; ++m)
+    if (!K[m]) return fail(c, SNK_ERR_INVALID_ARG, "NULL output for molecule " + std::to_string(m));
+  SNK_CK(c, c->K.ensure(std::max<size_t>((size_t)c->s.packed, 1)));
+  int rc = build(c, c->K.p);
+  if (rc != SNK_OK) return rc;
+  for (int m = 0; m < c->s.n_mol; ++m) {
+    const auto& M = c->s.mols[m];
+    SNK_CK(c, cudaMemcpyAsync(K[m], c->K.p + M.pk_off, sizeof(double) * M.nf * M.nf, cudaMemcpyDeviceToHost,
+                              c->stream));
+  }
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  return SNK_OK;
+}
+
+int snk_autotune(snk_ctx* c, int32_t* runs) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  return autotune(c, runs);
 }
 
 int snk_set_stream(snk_ctx* c, void* stream) {
@@ -691,6 +919,13 @@ int snk_get_stats(const snk_ctx* c, snk_stats* out) {
 
 int64_t snk_n_functions(const snk_ctx* c) { return c ? c->s.nf : -1; }
 
+int32_t snk_n_molecules(const snk_ctx* c) { return c ? c->s.n_mol : -1; }
+
+int64_t snk_molecule_functions(const snk_ctx* c, int32_t m) {
+  if (!c || m < 0 || m >= c->s.n_mol) return -1;
+  return c->s.mols[m].nf;
+}
+
 const char* snk_last_error(const snk_ctx* c) { return c ? c->err.c_str() : "NULL handle"; }
 
 void snk_destroy(snk_ctx* c) { delete c; }
@@ -699,25 +934,11 @@ int snk_debug_boys(int64_t n, const double* T, int nmax, double* out) {
   if (n < 0 || (n > 0 && (!T || !out)) || nmax < 0 || nmax > kBoysLMax) return SNK_ERR_INVALID_ARG;
   if (n == 0) return SNK_OK;
   // the same table the integral kernel uses
-  std::vector<double> tab((size_t)(kBoysLMax + 1) * kBoysRows * kBoysCols);
-  double F[kBoysLMax + kBoysTerms + 1], invfact = 1.0;
-  for (int k = 0; k < kBoysRows; ++k) {
-    double Tk = k * kBoysH;
-    host_boys(kBoysLMax + kBoysTerms, Tk, F);
-    for (int L = 0; L <= kBoysLMax; ++L) {
-      double* row = &tab[((size_t)L * kBoysRows + k) * kBoysCols];
-      invfact = 1.0;
-      for (int m = 0; m < kBoysTerms; ++m) {
-        if (m > 0) invfact /= m;
-        row[m] = F[L + m] * invfact;
-      }
-      row[kBoysTerms] = std::exp(-Tk);
-      row[kBoysTerms + 1] = Tk;
-    }
-  }
+  Setup tab;
+  build_boys_tables(&tab);
   DevBuf<double> dtab, dT, dout;
-  if (dtab.ensure(tab.size()) || dT.ensure(n) || dout.ensure((size_t)n * (nmax + 1))) return SNK_ERR_OOM;
-  if (cudaMemcpy(dtab.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice) ||
+  if (dtab.ensure(tab.boys.size()) || dT.ensure(n) || dout.ensure((size_t)n * (nmax + 1))) return SNK_ERR_OOM;
+  if (cudaMemcpy(dtab.p, tab.boys.data(), sizeof(double) * tab.boys.size(), cudaMemcpyHostToDevice) ||
       cudaMemcpy(dT.p, T, sizeof(double) * n, cudaMemcpyHostToDevice))
     return SNK_ERR_CUDA;
   if (launch_debug_boys(0, dtab.p, n, dT.p, nmax, dout.p) != cudaSuccess) return SNK_ERR_CUDA;
@@ -725,13 +946,31 @@ int snk_debug_boys(int64_t n, const double* T, int nmax, double* out) {
   return SNK_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// pair id of the shells sa, sb (global indices) or -1 (dropped, or different molecules)
+int pair_id(const Setup& s, int sa, int sb) {
+  for (const auto& M : s.mols)
+    if (sa >= M.ms0 && sa < M.ms0 + M.ns) {
+      if (sb < M.ms0 || sb >= M.ms0 + M.ns) return -1;
+      return s.pair_index[(size_t)M.pi_off + (size_t)(sa - M.ms0) * M.ns + (sb - M.ms0)];
+    }
+  return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
 int snk_debug_shell_A(snk_ctx* c, int32_t sa, int32_t sb, int64_t n, const double* xyz, double* out) {
   if (!c) return SNK_ERR_INVALID_ARG;
   Setup& s = c->s;
   if (sa < 0 || sb < 0 || sa >= s.ns || sb >= s.ns || n < 0 || (n > 0 && (!xyz || !out)))
     return fail(c, SNK_ERR_INVALID_ARG, "bad shell index or buffer");
   const int na = ncart(s.l[sa]), nb = ncart(s.l[sb]);
-  const int p = s.pair_index[(size_t)sa * s.ns + sb];
+  const int p = pair_id(s, sa, sb);
   if (n == 0) return SNK_OK;
   if (p < 0) {
     std::fill(out, out + (size_t)n * na * nb, 0.0);
@@ -842,8 +1081,8 @@ extern "C" int snk_shell_A_noalloc(snk_ctx* c, int32_t sa, int32_t sb, int64_t n
   SNK_CK(c, scratch_for_current_device(&scratch));
   if (n == 0) return SNK_OK;
   const int na = ncart(s.l[sa]), nb = ncart(s.l[sb]);
-  const int p = s.pair_index[(size_t)sa * s.ns + sb];
-  if (p < 0) {  // pair dropped at setup: its block is zero to below 1e-40
+  const int p = pair_id(s, sa, sb);
+  if (p < 0) {  // pair dropped at setup: its block is zero to below 1e-20
     SNK_CK(c, cudaMemsetAsync(out, 0, sizeof(double) * n * na * nb, c->stream));
     return SNK_OK;
   }

@@ -77,6 +77,21 @@ struct BatchDesc {
   int32_t nBshell;
   int64_t foff32;    // mixed form: offsets (floats) of the FP32 copies of F and G
   int64_t goff32;
+  int32_t mol;       // molecule of the batch, its first shell and function, N_b,m
+  int32_t ms0;
+  int32_t mf0;
+  int32_t nfm;
+  int64_t pk_off;    // the molecule's P / K block
+  int64_t cm_off;    // the batch's row of shell-local arrays (F-tilde, column maps)
+  int64_t phf_off;   // the batch's row of function-local arrays (Phi-tilde)
+};
+
+// Per molecule, on the device.
+struct MolDesc {
+  int64_t pk_off;
+  int32_t nf, ns, ms0, mf0, mb0, nb;
+  int32_t cr[kNumClasses + 1];
+  int32_t pad;
 };
 
 // Integral-kernel tile: batch, pair-list range, first point.
@@ -87,6 +102,20 @@ struct Tile {
 // ---------------------------------------------------------------- host setup
 
 struct Setup {
+  // molecules: shells [ms0, ms0+ns), functions [mf0, mf0+nf), batches
+  // [mb0, mb0+nb), pairs of class c in [cr[c], cr[c+1]); P / K block at
+  // pk_off (nf x nf, row-major); dense pair index block at pi_off (ns x ns)
+  struct Mol {
+    int ms0 = 0, ns = 0, mf0 = 0, nf = 0, mb0 = 0, nb = 0;
+    int64_t pk_off = 0, pi_off = 0, p0 = 0, npts = 0;
+    int cr[kNumClasses + 1] = {0};
+  };
+  int n_mol = 1;
+  std::vector<Mol> mols;
+  std::vector<int> bmol;                 // molecule of each batch
+  std::vector<int64_t> cm_off, phf_off;  // per batch: offsets of its shell-local and function-local rows
+  int64_t cm_total = 0, phf_total = 0, packed = 0;
+
   int ns = 0, nf = 0, nprim_total = 0;
   std::vector<int> l, nprim, poff, foff, atom;
   std::vector<double> center, exps, d, fcomp, rcut;
@@ -116,9 +145,11 @@ struct Setup {
   std::vector<float> boys_f;          // (kBoysLMax+1) x kBoysRowsF x kBoysColsF
 };
 
-// Validates and normalises the basis and grid; returns an snk_status and fills msg.
-int build_setup(const snk_basis* basis, const snk_grid* grid, const snk_options* opt, Setup* s,
+// Validates and normalises the molecules' bases and grids; returns an
+// snk_status and fills msg.
+int build_setup(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_options* opt, Setup* s,
                 std::string* msg);
+void build_boys_tables(Setup* s);
 double pair_bound(const Setup& s, int sa, int sb);
 void prim_pair_bounds(const Setup& s, int sa, int sb, int k, int m, double* abound, double* qbound);
 void host_boys(int nmax, double T, double* F);
@@ -139,43 +170,47 @@ struct DeviceBasis {
 cudaError_t launch_collocation(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq,
                                int max_nBshell, const int* bshell, const int* bshell_col, const double* xyz,
                                DeviceBasis basis, double* ws);
+// Phi-tilde rows at BatchDesc::phf_off of phit_f, phi-tilde at the batch index
+// relative to dbatch of phit_b.
 cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nB,
-                               const double* ws, const double* w, const int* xfunc, int nf,
-                               double* phit_f, double* phit_b);
-cudaError_t launch_ftilde(cudaStream_t st, const double* P, const double* phit_f, int nf,
-                          int nbatch, const int* fshell, int ns, double* ft_shell);
-struct ClassRanges {
-  int b[kNumClasses + 1];
-};
-
+                               const double* ws, const double* w, const int* xfunc, double* phit_f,
+                               double* phit_b);
+// F-tilde of every molecule's batches (one GEMM per molecule in one launch).
+cudaError_t launch_ftilde(cudaStream_t st, const MolDesc* mols, int n_mol, int max_nf, int max_nb,
+                          const BatchDesc* batches, const double* P, const double* phit_f, const int* fshell,
+                          double* ft_shell);
 // Inputs of the sn-LinK pair screen (Eqs. sp_set, exx_fmat_approx).
 struct ScreenArgs {
+  const MolDesc* mols;
+  const BatchDesc* batches;
   const PairHdr* pairs;
   const double* bound;      // global A-tilde per pair
   const double* qbound;     // total-charge bound per pair
   const double* shell_xyz;  // shell centres
   const double* bcenter;    // batch bounding spheres
   const double* bradius;
-  const double* ft_shell;   // F-tilde per (batch, shell)
+  const double* ft_shell;   // F-tilde per (batch, molecule-local shell), rows at BatchDesc::cm_off
   const double* phit_b;     // phi-tilde per batch
-  int ns;
   int screen;               // snk_screen_mode
   int distance;             // 1: refine A-tilde by charge / distance per batch
   int mixed;                // 1: route low-estimate pairs to the FP32 lists
   double eps_E, eps_K, fp32_bound;
-  ClassRanges cr;
 };
 
 cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, int* counts, long long* ppcounts,
                               unsigned char* sflag);
 cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list);
+// P, Khat and K below are the packed molecule blocks (BatchDesc::pk_off,
+// MolDesc::pk_off); xfunc / sfunc hold molecule-local function indices.
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
-                         const double* P, int nf, const int* xfunc, const int* sfunc,
-                         const double* fcomp, const double* w, double* ws, float* ws32);
+                         const double* P, const int* xfunc, const int* sfunc, const double* fcomp,
+                         const double* w, double* ws, float* ws32, bool tensor);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, int nf, const double* ws, double* Khat);
-cudaError_t launch_finish(cudaStream_t st, const double* Khat, const double* fcomp, int nf, double* K);
-cudaError_t launch_symcheck(cudaStream_t st, const double* P, int nf, double* out2);
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, bool tensor);
+cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* Khat,
+                          const double* fcomp, double* K);
+cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* P,
+                            double* out2);
 
 struct IntegralArgs {
   const Tile* tiles;
@@ -185,8 +220,7 @@ struct IntegralArgs {
   const int* pairlist;
   const PairHdr* pairs;
   const PrimPair* prims;
-  const int* colmap;  // nbatch x ns, local F/G column of each shell or -1
-  int ns;
+  const int* colmap;  // per batch (rows at BatchDesc::cm_off): F/G column of each molecule shell or -1
   const double* xyz;  // batch order
   const double* boys; // device table, all L
   double* ws;

@@ -195,7 +195,15 @@ def test_mixed_precision_form(snk):
     assert np.max(np.abs(Km - K64)) <= 1e-7
     assert np.max(np.abs(Km - Kref)) <= 1e-7
     assert np.max(np.abs(Km - Km.T)) == 0.0
+    # a looser split (1e-3) stays within the 1e-8 target of the mixed form
+    Kl, sl = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e-3)
+    assert sl["pairs_kept_fp32"] > sm["pairs_kept_fp32"]
+    assert np.max(np.abs(Kl - Kref)) <= 1e-8
     # everything in FP32: still a sane exchange matrix, error well above FP64's
     Kf, sf = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e300)
     assert sf["pairs_kept_fp32"] == sf["pairs_kept"]
     assert 1e-12 < np.max(np.abs(Kf - Kref)) <= 1e-5
+    # split-TF32 tensor-core products (FP32 accumulation): FP32-level K
+    Kt, st = _gpu_K(snk, p, batch_max=300, precision="mixed", tensor_gemms=3)
+    assert np.max(np.abs(Kt - Kref)) <= 1e-4
+    assert np.max(np.abs(Kt - Kt.T)) == 0.0
