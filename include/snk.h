@@ -104,7 +104,9 @@ typedef struct {
   int32_t graph;           /* 1: snk_build_K* capture the whole build in a CUDA graph
                               on first use (per density and output buffer) and
                               replay it; phase times are then not reported      */
-  double reserved[7];
+  double learned_skip;     /* learned screen: skip a block whose predicted log10
+                              contribution to K is below this (default -11)     */
+  double reserved[6];
 } snk_options;
 
 /* Per-build counters and phase times (CUDA events on the library stream). */
@@ -128,7 +130,8 @@ typedef struct {
   double integrals_fp32;       /* their integrals                                    */
   double flops_fp32;           /* their algorithmic FP32 flops                       */
   double ms_integrals_fp32;    /* their kernel time                                  */
-  double reserved_stats[8];
+  int64_t pairs_learned_skipped; /* learned screen: kept by sn-LinK, skipped by the MLP */
+  double reserved_stats[7];
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,
@@ -188,6 +191,54 @@ int64_t snk_n_functions(const snk_ctx *ctx);
 const char *snk_last_error(const snk_ctx *ctx);
 const char *snk_status_string(int status);
 void snk_destroy(snk_ctx *ctx);
+
+/* ---- learned block screen ------------------------------------------------ */
+
+/* A small MLP (16 features -> 64 -> 64 -> 64 -> 1, ReLU) predicts log10/10 of
+ * the contribution of a (grid batch, shell pair) block to K.  Features (all
+ * computed on the device): l_a, l_b, smallest and largest exponents of both
+ * shells, distance from the batch to the pair, |AB|, F-tilde of both shells
+ * (the F block norms of Eq. exx_fmat_approx), phi-tilde of the batch, the
+ * rigorous batch bound A-tilde, the sn-LinK estimate epsilon^K, batch radius
+ * and size.  With options.screen = SNK_SCREEN_LEARNED and weights loaded, a
+ * block kept by the rigorous sn-LinK screen is skipped when the prediction is
+ * below options.learned_skip (FP16 tensor-core inference, FP32 accumulation);
+ * without weights the rigorous screen alone applies (the fallback).
+ * Weights: SNK_MLP_WEIGHTS floats, W1[16][64] b1[64] W2[64][64] b2[64]
+ * W3[64][64] b3[64] W4[64] b4. */
+enum { SNK_MLP_FEATURES = 16, SNK_MLP_WEIGHTS = 9473 };
+
+/* Copies the weights (host) into the handle; later snk_set_density calls use
+ * them when options.screen is SNK_SCREEN_LEARNED. */
+int snk_screen_load(snk_ctx *ctx, const float *weights);
+
+/* Training data from the plain FP64 method itself, for the loaded density of a
+ * handle with the rigorous screen: for the batches j with j % stride == 0
+ * (until cap blocks), every kept block's features and label
+ * log10(max_u sum_i |dG_u(i)| max_nu |Phi_{nu i}|) / 10, dG_u(i) the block's
+ * contribution to G row u at point i: an upper bound of the block's
+ * contribution to any K entry, from the block's actual integrals.  n receives
+ * the number of blocks written (features: n x 16, labels: n). */
+int snk_learn_collect(snk_ctx *ctx, int32_t stride, int64_t cap, float *features, float *labels, int64_t *n);
+
+/* Trains the MLP on the GPU with the library's own kernels (FP32 forward,
+ * backward, Adam): mini-batches of `batch` samples, `epochs` passes in a
+ * seeded order, loss = mean c r^2 with r = prediction - label and c = 1 for
+ * over- and under_weight for under-prediction.  init != 0 draws He-normal
+ * weights from seed first; otherwise training continues from *weights.
+ * loss_history (optional, epochs entries) receives the mean loss per epoch.
+ * Host arrays throughout. */
+int snk_mlp_train(const float *features, const float *labels, int64_t n, int32_t epochs, int32_t batch, float lr,
+                  float under_weight, uint64_t seed, int32_t init, float *weights, float *loss_history);
+
+/* Forward pass for n feature rows (host arrays): FP32 (f16 = 0) or the FP16
+ * tensor-core inference path (f16 = 1). */
+int snk_mlp_eval(const float *weights, const float *features, int64_t n, int32_t f16, float *out);
+
+/* Loss and its gradient with respect to every weight (FP32 kernels), for
+ * checks against an independent implementation. */
+int snk_mlp_grad(const float *weights, const float *features, const float *labels, int64_t n, float under_weight,
+                 float *grad, float *loss);
 
 /* ---- test exports: expose intermediate steps for unit parity ------------- */
 

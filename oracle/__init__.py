@@ -62,8 +62,10 @@ def lib():
             L.oracle_snk_K.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, _D, ctypes.c_int]
             L.oracle_snk_K_entries.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int,
                                                             _I, _I, _D, ctypes.c_int]
+            L.oracle_mlp_forward.argtypes = [_D, _D, ctypes.c_long, _D]
+            L.oracle_mlp_loss_grad.argtypes = [_D, _D, _D, ctypes.c_long, ctypes.c_double, _D, _D]
             for name in ("oracle_normalise", "oracle_collocation", "oracle_shell_A", "oracle_eri_K",
-                         "oracle_snk_K", "oracle_snk_K_entries"):
+                         "oracle_snk_K", "oracle_snk_K_entries", "oracle_mlp_forward", "oracle_mlp_loss_grad"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -182,3 +184,24 @@ def snk_K_entries(basis, grid, P, mu, nu, nthreads: int = 0) -> np.ndarray:
                                       int(mu.shape[0]), _ip(mu), _ip(nu), _dp(out), int(nthreads)),
            "snk_K_entries")
     return out
+
+
+MLP_WEIGHTS = 16 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1
+
+
+def mlp_forward(w, X) -> np.ndarray:
+    """Learned-screen MLP output for each row of X (n x 16), FP64."""
+    w, X = _f64(w), _f64(X).reshape(-1, 16)
+    out = np.zeros(X.shape[0])
+    _check(lib().oracle_mlp_forward(_dp(w), _dp(X), ctypes.c_long(X.shape[0]), _dp(out)), "mlp_forward")
+    return out
+
+
+def mlp_loss_grad(w, X, Y, under_weight=4.0):
+    """Asymmetric squared-error loss and its gradient by backpropagation, FP64."""
+    w, X, Y = _f64(w), _f64(X).reshape(-1, 16), _f64(Y).reshape(-1)
+    g = np.zeros(MLP_WEIGHTS)
+    loss = np.zeros(1)
+    _check(lib().oracle_mlp_loss_grad(_dp(w), _dp(X), _dp(Y), ctypes.c_long(X.shape[0]), float(under_weight),
+                                      _dp(g), _dp(loss)), "mlp_loss_grad")
+    return float(loss[0]), g

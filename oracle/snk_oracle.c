@@ -723,3 +723,102 @@ int oracle_snk_K_entries(int n_shells, const int *l, const int *nprim, const dou
   obasis_free(&b);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* MLP of the learned block screen: plain FP64 forward, loss and gradient   */
+/* by backpropagation, for checks of the GPU training kernels.              */
+/* Weights: W1[16][64] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4; */
+/* ReLU hidden layers; loss = (1/n) sum c r^2, r = y - label, c = 1 if      */
+/* r >= 0 else under_weight.                                                */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_NIN 16
+#define ORC_NH 64
+
+static void mlp_offsets(int off[8]) {
+  off[0] = 0;                          /* W1 */
+  off[1] = off[0] + ORC_NIN * ORC_NH;  /* b1 */
+  off[2] = off[1] + ORC_NH;            /* W2 */
+  off[3] = off[2] + ORC_NH * ORC_NH;   /* b2 */
+  off[4] = off[3] + ORC_NH;            /* W3 */
+  off[5] = off[4] + ORC_NH * ORC_NH;   /* b3 */
+  off[6] = off[5] + ORC_NH;            /* W4 */
+  off[7] = off[6] + ORC_NH;            /* b4 */
+}
+
+/* one layer: out[m] = b[m] + sum_k in[k] W[k][m] */
+static void mlp_dense(const double *w, int W, int B, int nin, int nout, const double *in, double *out) {
+  for (int m = 0; m < nout; ++m) {
+    double s = w[B + m];
+    for (int k = 0; k < nin; ++k) s += in[k] * w[W + k * nout + m];
+    out[m] = s;
+  }
+}
+
+static double mlp_forward_store(const double *w, const double *x, double z[3][ORC_NH], double a[3][ORC_NH]) {
+  int off[8];
+  mlp_offsets(off);
+  mlp_dense(w, off[0], off[1], ORC_NIN, ORC_NH, x, z[0]);
+  for (int m = 0; m < ORC_NH; ++m) a[0][m] = z[0][m] > 0.0 ? z[0][m] : 0.0;
+  mlp_dense(w, off[2], off[3], ORC_NH, ORC_NH, a[0], z[1]);
+  for (int m = 0; m < ORC_NH; ++m) a[1][m] = z[1][m] > 0.0 ? z[1][m] : 0.0;
+  mlp_dense(w, off[4], off[5], ORC_NH, ORC_NH, a[1], z[2]);
+  for (int m = 0; m < ORC_NH; ++m) a[2][m] = z[2][m] > 0.0 ? z[2][m] : 0.0;
+  double y;
+  mlp_dense(w, off[6], off[7], ORC_NH, 1, a[2], &y);
+  return y;
+}
+
+int oracle_mlp_forward(const double *w, const double *X, long n, double *out) {
+  double z[3][ORC_NH], a[3][ORC_NH];
+  for (long s = 0; s < n; ++s) out[s] = mlp_forward_store(w, X + s * ORC_NIN, z, a);
+  return 0;
+}
+
+int oracle_mlp_loss_grad(const double *w, const double *X, const double *Y, long n, double under_weight,
+                         double *grad, double *loss) {
+  int off[8];
+  mlp_offsets(off);
+  const int nw = off[7] + 1;
+  for (int e = 0; e < nw; ++e) grad[e] = 0.0;
+  *loss = 0.0;
+  double z[3][ORC_NH], a[3][ORC_NH], d[3][ORC_NH];
+  for (long s = 0; s < n; ++s) {
+    const double *x = X + s * ORC_NIN;
+    const double y = mlp_forward_store(w, x, z, a);
+    const double r = y - Y[s];
+    const double c = r < 0.0 ? under_weight : 1.0;
+    *loss += c * r * r / n;
+    const double dy = 2.0 * c * r / n;
+    /* output layer */
+    grad[off[7]] += dy;
+    for (int k = 0; k < ORC_NH; ++k) grad[off[6] + k] += a[2][k] * dy;
+    for (int k = 0; k < ORC_NH; ++k) d[2][k] = z[2][k] > 0.0 ? w[off[6] + k] * dy : 0.0;
+    /* hidden layer 3 */
+    for (int m = 0; m < ORC_NH; ++m) {
+      grad[off[5] + m] += d[2][m];
+      for (int k = 0; k < ORC_NH; ++k) grad[off[4] + k * ORC_NH + m] += a[1][k] * d[2][m];
+    }
+    for (int k = 0; k < ORC_NH; ++k) {
+      double t = 0.0;
+      for (int m = 0; m < ORC_NH; ++m) t += w[off[4] + k * ORC_NH + m] * d[2][m];
+      d[1][k] = z[1][k] > 0.0 ? t : 0.0;
+    }
+    /* hidden layer 2 */
+    for (int m = 0; m < ORC_NH; ++m) {
+      grad[off[3] + m] += d[1][m];
+      for (int k = 0; k < ORC_NH; ++k) grad[off[2] + k * ORC_NH + m] += a[0][k] * d[1][m];
+    }
+    for (int k = 0; k < ORC_NH; ++k) {
+      double t = 0.0;
+      for (int m = 0; m < ORC_NH; ++m) t += w[off[2] + k * ORC_NH + m] * d[1][m];
+      d[0][k] = z[0][k] > 0.0 ? t : 0.0;
+    }
+    /* hidden layer 1 */
+    for (int m = 0; m < ORC_NH; ++m) {
+      grad[off[1] + m] += d[0][m];
+      for (int k = 0; k < ORC_NIN; ++k) grad[off[0] + k * ORC_NH + m] += x[k] * d[0][m];
+    }
+  }
+  return 0;
+}

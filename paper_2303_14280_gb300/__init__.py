@@ -43,7 +43,9 @@ SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molec
            "snk_set_density", "snk_set_density_device", "snk_set_density_batch", "snk_build_K",
            "snk_build_K_device", "snk_build_K_batch", "snk_autotune", "snk_set_stream", "snk_get_stats",
            "snk_n_functions", "snk_last_error", "snk_status_string", "snk_destroy", "snk_debug_boys",
-           "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc"]
+           "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc",
+           "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad"]
+MLP_FEATURES, MLP_WEIGHTS = 16, 9473
 
 
 class SnkError(RuntimeError):
@@ -69,7 +71,7 @@ class SnkOptions(ctypes.Structure):
                 ("batch_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("distance_bound", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("tensor_gemms", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("reserved", ctypes.c_double * 7)]
+                ("learned_skip", ctypes.c_double), ("reserved", ctypes.c_double * 6)]
 
 
 class SnkStats(ctypes.Structure):
@@ -82,7 +84,8 @@ class SnkStats(ctypes.Structure):
                [("ms_integrals_class", ctypes.c_double * 6), ("integrals_class", ctypes.c_double * 6),
                 ("flops_class", ctypes.c_double * 6), ("pairs_kept_fp32", ctypes.c_int64),
                 ("integrals_fp32", ctypes.c_double), ("flops_fp32", ctypes.c_double),
-                ("ms_integrals_fp32", ctypes.c_double), ("reserved_stats", ctypes.c_double * 8)]
+                ("ms_integrals_fp32", ctypes.c_double), ("pairs_learned_skipped", ctypes.c_int64),
+                ("reserved_stats", ctypes.c_double * 7)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -133,6 +136,13 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
             L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), _I32, ctypes.c_int64,
                                             ctypes.POINTER(ctypes.c_int64)]
             L.snk_shell_A_noalloc.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P]
+            _F = ctypes.POINTER(ctypes.c_float)
+            L.snk_screen_load.argtypes = [_P, _F]
+            L.snk_learn_collect.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, _F, _F, ctypes.POINTER(ctypes.c_int64)]
+            L.snk_mlp_train.argtypes = [_F, _F, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_uint64, ctypes.c_int32, _F, _F]
+            L.snk_mlp_eval.argtypes = [_F, _F, ctypes.c_int64, ctypes.c_int32, _F]
+            L.snk_mlp_grad.argtypes = [_F, _F, _F, ctypes.c_int64, ctypes.c_float, _F, _F]
             _lib = L
     return _lib
 
@@ -168,6 +178,48 @@ def debug_boys(T, nmax: int) -> np.ndarray:
 
 def _is_cuda_tensor(x) -> bool:
     return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a if shape is None else a.reshape(shape)
+
+
+def mlp_train(features, labels, epochs=20, batch=4096, lr=1e-3, under_weight=4.0, seed=0, weights=None):
+    """Train the screen MLP on the GPU (snk_mlp_train); returns (weights, loss per epoch)."""
+    X, Y = _f32(features, (-1, MLP_FEATURES)), _f32(labels, (-1,))
+    w = np.zeros(MLP_WEIGHTS, dtype=np.float32) if weights is None else _f32(weights).copy()
+    hist = np.zeros(max(epochs, 1), dtype=np.float32)
+    rc = lib().snk_mlp_train(_fptr(X), _fptr(Y), X.shape[0], int(epochs), int(batch), float(lr), float(under_weight),
+                             int(seed), 1 if weights is None else 0, _fptr(w), _fptr(hist))
+    if rc != SNK_OK:
+        raise SnkError(rc, "snk_mlp_train")
+    return w, hist[:epochs]
+
+
+def mlp_eval(weights, features, f16=False):
+    """MLP predictions (snk_mlp_eval): FP32, or the FP16 tensor-core path."""
+    w, X = _f32(weights), _f32(features, (-1, MLP_FEATURES))
+    out = np.zeros(X.shape[0], dtype=np.float32)
+    rc = lib().snk_mlp_eval(_fptr(w), _fptr(X), X.shape[0], 1 if f16 else 0, _fptr(out))
+    if rc != SNK_OK:
+        raise SnkError(rc, "snk_mlp_eval")
+    return out
+
+
+def mlp_grad(weights, features, labels, under_weight=4.0):
+    """Loss and gradient of the screen MLP by the GPU training kernels (snk_mlp_grad)."""
+    w, X, Y = _f32(weights), _f32(features, (-1, MLP_FEATURES)), _f32(labels, (-1,))
+    g = np.zeros(MLP_WEIGHTS, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    rc = lib().snk_mlp_grad(_fptr(w), _fptr(X), _fptr(Y), X.shape[0], float(under_weight), _fptr(g), _fptr(loss))
+    if rc != SNK_OK:
+        raise SnkError(rc, "snk_mlp_grad")
+    return float(loss[0]), g
 
 
 def _basis_struct(basis, keep):
@@ -278,6 +330,21 @@ class Engine:
         assert K.dtype == np.float64 and K.flags.c_contiguous and K.size == self.packed
         self._check(lib().snk_build_K(self._h, _P(K.ctypes.data)), "snk_build_K")
         return K
+
+    def screen_load(self, weights):
+        """Load trained MLP weights for options screen='learned' (snk_screen_load)."""
+        w = _f32(weights)
+        assert w.size == MLP_WEIGHTS
+        self._check(lib().snk_screen_load(self._h, _fptr(w)), "snk_screen_load")
+
+    def learn_collect(self, stride=1, cap=1 << 22):
+        """Training blocks of the loaded density (snk_learn_collect): (features, labels)."""
+        feat = np.zeros((cap, MLP_FEATURES), dtype=np.float32)
+        lab = np.zeros(cap, dtype=np.float32)
+        n = ctypes.c_int64()
+        self._check(lib().snk_learn_collect(self._h, int(stride), int(cap), _fptr(feat), _fptr(lab), ctypes.byref(n)),
+                    "snk_learn_collect")
+        return feat[:n.value].copy(), lab[:n.value].copy()
 
     def autotune(self) -> dict:
         """snk_autotune: pairs per tile chosen for each integral list."""

@@ -318,6 +318,20 @@ __global__ void phit_b_kernel(const BatchDesc* __restrict__ batches, const doubl
   }
 }
 
+// max_nu |Phi_{nu i}| at every point i of a batch (weight of a point in the
+// bound sum_i |dG_u(i)| max_nu |Phi_{nu i}| >= |dKt_{u nu}| of the learned
+// screen's labels); xm is indexed by the point's position in batch order.
+__global__ void xmax_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ ws,
+                            double* __restrict__ xm) {
+  const BatchDesc bd = batches[blockIdx.x];
+  const double* X = ws + bd.xoff;
+  for (int i = threadIdx.x; i < bd.q; i += blockDim.x) {
+    double m = 0.0;
+    for (int c = 0; c < bd.nB; ++c) m = fmax(m, fabs(X[(int64_t)c * bd.ldq + i]));
+    xm[bd.p0 + i] = m;
+  }
+}
+
 // ---------------------------------------------------------------- F-tilde
 
 // For molecule blockIdx.z: F-tilde_a^(j) = max_{mu in a} sum_nu |P_{mu nu}|
@@ -588,6 +602,12 @@ cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nba
     phit_f_kernel<<<grid, 128, 0, st>>>(dbatch, ws, w, xfunc, phit_f);
   }
   phit_b_kernel<<<nbatch, 256, 0, st>>>(dbatch, ws, w, phit_b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xmax(cudaStream_t st, const BatchDesc* dbatch, int nbatch, const double* ws, double* xmax) {
+  if (nbatch == 0) return cudaSuccess;
+  xmax_kernel<<<nbatch, 256, 0, st>>>(dbatch, ws, xmax);
   return cudaGetLastError();
 }
 

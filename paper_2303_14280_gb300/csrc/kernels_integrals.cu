@@ -323,6 +323,81 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   }
 }
 
+// Training labels of the learned screen, from the plain FP64 integrals: for
+// every list entry (batch j, pair ab) of the sampled batches, the sums over
+// the batch's points of |dG_u(i)| max_nu |Phi_{nu i}|, dG_u the block's
+// contribution to G row u of shell a (slots 0..5) or b (slots 6..11): an
+// upper bound of the block's contribution to K-tilde row u.  Same tiles as
+// integral_kernel.
+template <int LA, int LB>
+__global__ void __launch_bounds__(kIntThreads) label_kernel(IntegralArgs a, const int64_t* __restrict__ slot_base,
+                                                            const int64_t* __restrict__ list_off,
+                                                            const double* __restrict__ xm,
+                                                            float* __restrict__ lab) {
+  using C = OsClass<LA, LB>;
+  constexpr int NA = C::NA, NB = C::NB;
+  extern __shared__ double s_tab[];
+  const double* gtab = a.boys + (size_t)C::L * kBoysRows * kBoysCols;
+  for (int e = threadIdx.x; e < kBoysRows * kBoysCols; e += blockDim.x) s_tab[e] = gtab[e];
+  __shared__ int s_tile;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= a.n_tiles) break;
+    const Tile tile = a.tiles[t];
+    const BatchDesc bd = a.batches[tile.batch];
+    const int i = tile.i0 + threadIdx.x;
+    const bool active = i < bd.q;
+    const int64_t ldq = bd.ldq;
+    const double cx = active ? a.xyz[3 * (bd.p0 + i)] : 0.0, cy = active ? a.xyz[3 * (bd.p0 + i) + 1] : 0.0,
+                 cz = active ? a.xyz[3 * (bd.p0 + i) + 2] : 0.0;
+    const double* F = a.ws + bd.foff + (active ? i : 0);
+    const int* cmap = a.colmap + bd.cm_off - bd.ms0;
+    const int64_t s0 = slot_base[tile.batch] - list_off[(int64_t)tile.batch * kNumLists];
+    for (int k = tile.k0; k < tile.k1; ++k) {
+      const PairHdr h = a.pairs[a.pairlist[k]];
+      const int cola = cmap[h.sa], colb = cmap[h.sb];
+      float part[NA + NB];
+#pragma unroll
+      for (int u = 0; u < NA + NB; ++u) part[u] = 0.f;
+      if (active && cola >= 0 && colb >= 0) {
+        double xi[NA * NB], fa[NA], fb[NB];
+#pragma unroll
+        for (int u = 0; u < NA; ++u) fa[u] = F[(cola + u) * ldq];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) fb[v] = F[(colb + v) * ldq];
+        pair_xi<LA, LB>(h, a.prims, s_tab, cx, cy, cz, xi);
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          double g = 0.0;
+#pragma unroll
+          for (int v = 0; v < NB; ++v) g = fma(xi[u * NB + v], fb[v], g);
+          part[u] = (float)(fabs(g) * xm[bd.p0 + i]);
+        }
+        if (h.sa != h.sb) {
+#pragma unroll
+          for (int v = 0; v < NB; ++v) {
+            double g = 0.0;
+#pragma unroll
+            for (int u = 0; u < NA; ++u) g = fma(xi[u * NB + v], fa[u], g);
+            part[NA + v] = (float)(fabs(g) * xm[bd.p0 + i]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NA + NB; ++u) {
+        float s = part[u];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && s > 0.f) atomicAdd(&lab[(s0 + k) * 12 + (u < NA ? u : 6 + (u - NA))], s);
+      }
+    }
+  }
+}
+
 template <int LA, int LB>
 __global__ void debug_xi_kernel(const PairHdr* pair, const PrimPair* prims, const double* boys, int64_t n,
                                 const double* xyz, double* out) {
@@ -418,6 +493,30 @@ int integral_max_ctas(int list, int num_sms) {
     case 5: return max_ctas<2, 2>(f32, num_sms);
   }
   return num_sms;
+}
+
+cudaError_t launch_labels(cudaStream_t st, int cls, const IntegralArgs& a, int grid, const int64_t* slot_base,
+                          const int64_t* list_off, const double* xm, float* lab) {
+  if (a.n_tiles == 0) return cudaSuccess;
+#define SNK_LAB(A, B)                                                                                       \
+  {                                                                                                         \
+    cudaError_t e =                                                                                         \
+        cudaFuncSetAttribute(label_kernel<A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64); \
+    if (e != cudaSuccess) return e;                                                                         \
+    label_kernel<A, B><<<grid, kIntThreads, kSmem64, st>>>(a, slot_base, list_off, xm, lab);              \
+    break;                                                                                                  \
+  }
+  switch (cls) {
+    case 0: SNK_LAB(0, 0)
+    case 1: SNK_LAB(1, 0)
+    case 2: SNK_LAB(1, 1)
+    case 3: SNK_LAB(2, 0)
+    case 4: SNK_LAB(2, 1)
+    case 5: SNK_LAB(2, 2)
+    default: return cudaErrorInvalidValue;
+  }
+#undef SNK_LAB
+  return cudaGetLastError();
 }
 
 cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const PrimPair* prims, const double* boys,

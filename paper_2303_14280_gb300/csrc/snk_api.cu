@@ -69,6 +69,12 @@ struct snk_ctx {
   DevBuf<MolDesc> mols;
   int max_nf = 0, max_nb = 0;
 
+  // learned screen
+  DevBuf<float> mlp_w, shell_feat;
+  DevBuf<unsigned char> keep;
+  bool mlp_loaded = false;
+  ScreenArgs sargs{};
+
   // density-dependent state
   bool have_density = false;
   DevBuf<double> P, ft, sym, Khat, K;
@@ -345,6 +351,26 @@ int screen_and_plan(snk_ctx* c) {
   SNK_CK(c, upload(c->list_off, c->hlist_off, st));
   SNK_CK(c, launch_pair_write(st, sa, nb, c->list_off.p, c->list.p));
   ++c->launches_density;
+  c->sargs = sa;
+
+  // learned screen on top of the rigorous lists: the MLP skips blocks whose
+  // predicted contribution is below learned_skip; lists are compacted in place
+  int64_t learned_skipped = 0;
+  if (c->opt.screen == SNK_SCREEN_LEARNED && c->mlp_loaded && tot > 0) {
+    SNK_CK(c, c->keep.ensure((size_t)tot));
+    SNK_CK(c, cudaMemsetAsync(c->keep.p, 1, (size_t)tot, st));
+    SNK_CK(c, launch_learned_filter(st, sa, nb, c->mlp_w.p, c->list.p, c->list_off.p, c->counts.p, c->ppcounts.p,
+                                    c->shell_feat.p, (float)c->opt.learned_skip, c->keep.p));
+    c->launches_density += 2;
+    SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumLists, cudaMemcpyDeviceToHost,
+                              st));
+    SNK_CK(c, cudaMemcpyAsync(c->hpp.data(), c->ppcounts.p, sizeof(long long) * nbx * kNumLists,
+                              cudaMemcpyDeviceToHost, st));
+    SNK_CK(c, cudaStreamSynchronize(st));
+    int64_t after = 0;
+    for (int64_t x = 0; x < (int64_t)nb * kNumLists; ++x) after += c->hcounts[x];
+    learned_skipped = tot - after;
+  }
 
   // shells of V_j -> F / G columns (molecule-local function indices)
   std::vector<int> hcolmap(cmn, -1), hsfunc;
@@ -443,6 +469,7 @@ int screen_and_plan(snk_ctx* c) {
 
   snk_stats& S = c->st;
   S.n_batches = nb;
+  S.pairs_learned_skipped = learned_skipped;
   S.pairs_kept = kept[0] + kept[1];
   S.pairs_kept_fp32 = kept[1];
   S.pair_points = pair_points;
@@ -742,9 +769,23 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
     c->max_nf = std::max(c->max_nf, M.nf);
     c->max_nb = std::max(c->max_nb, M.nb);
   }
+  // per shell features of the learned screen: l/2, log10 of the smallest and
+  // largest exponent / 3
+  std::vector<float> sfeat(4 * (size_t)std::max(s.ns, 1), 0.f);
+  for (int a = 0; a < s.ns; ++a) {
+    double mn = 1e300, mx = 0.0;
+    for (int k = s.poff[a]; k < s.poff[a + 1]; ++k) {
+      mn = std::min(mn, s.exps[k]);
+      mx = std::max(mx, s.exps[k]);
+    }
+    sfeat[4 * a] = 0.5f * s.l[a];
+    sfeat[4 * a + 1] = (float)(std::log10(mn) / 3.0);
+    sfeat[4 * a + 2] = (float)(std::log10(mx) / 3.0);
+  }
   snk_ctx* cp = c.get();
   const cudaStream_t st = cp->stream;
   if ((rc = [&]() -> int {
+         SNK_CK(cp, upload(cp->shell_feat, sfeat, st));
          SNK_CK(cp, upload(cp->l, s.l, st));
          SNK_CK(cp, upload(cp->poff, s.poff, st));
          SNK_CK(cp, upload(cp->nprim, s.nprim, st));
@@ -802,6 +843,7 @@ void snk_options_default(snk_options* o) {
   o->distance_bound = 1;
   o->tensor_gemms = 0;
   o->graph = 0;
+  o->learned_skip = -11.0;
 }
 
 const char* snk_status_string(int status) {
@@ -1095,3 +1137,226 @@ extern "C" int snk_shell_A_noalloc(snk_ctx* c, int32_t sa, int32_t sb, int64_t n
   SNK_CK(c, cudaGetLastError());
   return SNK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned block screen: training data from the plain method, training and
+// evaluation of the MLP with the library's kernels, loading into a handle.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// splitmix64: seeded, platform-independent random numbers for the MLP set-up
+struct SplitMix {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  double normal() { return std::sqrt(-2.0 * std::log(uniform())) * std::cos(6.283185307179586 * uniform()); }
+};
+
+int learn_collect(snk_ctx* c, int stride, int64_t cap, float* feat, float* lab, int64_t* n_out) {
+  if (!n_out || stride < 1 || cap < 0 || (cap > 0 && (!feat || !lab)))
+    return fail(c, SNK_ERR_INVALID_ARG, "snk_learn_collect: bad arguments");
+  *n_out = 0;
+  if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_learn_collect called before snk_set_density");
+  if (c->opt.screen == SNK_SCREEN_LEARNED && c->mlp_loaded)
+    return fail(c, SNK_ERR_BAD_STATE, "snk_learn_collect needs the rigorous screen's lists (screen != learned)");
+  const int nb = c->nbatch, nbx = std::max(nb, 1);
+  const cudaStream_t st = c->stream;
+  std::vector<int> sb;
+  std::vector<int64_t> slot(nbx, -1), soff, entries(nbx, 0);
+  int64_t tot = 0;
+  for (int j = 0; j < nb; j += stride) {
+    for (int L = 0; L < kNumLists; ++L) entries[j] += c->hcounts[(size_t)j * kNumLists + L];
+    if (tot + entries[j] > cap) break;
+    slot[j] = tot;
+    sb.push_back(j);
+    soff.push_back(tot);
+    tot += entries[j];
+  }
+  if (tot == 0) return SNK_OK;
+  DevBuf<float> dlab, dfeat;
+  DevBuf<double> dxmax;
+  DevBuf<int64_t> dslot, dsoff;
+  DevBuf<int> dsb;
+  DevBuf<Tile> dtile;
+  SNK_CK(c, dlab.ensure((size_t)tot * 12));
+  SNK_CK(c, dfeat.ensure((size_t)tot * kMlpIn));
+  SNK_CK(c, dxmax.ensure((size_t)std::max<int64_t>(c->s.npts, 1)));
+  SNK_CK(c, cudaMemsetAsync(dlab.p, 0, sizeof(float) * tot * 12, st));
+  SNK_CK(c, cudaMemsetAsync(dxmax.p, 0, sizeof(double) * std::max<int64_t>(c->s.npts, 1), st));
+  SNK_CK(c, upload(dslot, slot, st));
+  SNK_CK(c, upload(dsoff, soff, st));
+  SNK_CK(c, upload(dsb, sb, st));
+  SNK_CK(c, launch_features(st, c->sargs, c->list.p, c->list_off.p, c->counts.p, dsb.p, dsoff.p, (int)sb.size(),
+                            c->shell_feat.p, dfeat.p));
+  for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
+    const auto& ch = c->chunks[ci];
+    bool any = false;
+    for (int j = ch.b0; j < ch.b1; ++j) any = any || slot[j] >= 0;
+    if (!any) continue;
+    const int nbc = ch.b1 - ch.b0;
+    const BatchDesc* db = c->batch.p + ch.b0;
+    SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
+                                 dev_basis(c), c->ws.p));
+    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
+                           c->ws.p, nullptr, false));
+    SNK_CK(c, launch_xmax(st, db, nbc, c->ws.p, dxmax.p));
+    for (int k = 0; k < kNumLists; ++k) {
+      std::vector<Tile> ht;
+      for (int j = ch.b0; j < ch.b1; ++j) {
+        if (slot[j] < 0) continue;
+        const int64_t n = c->hcounts[(size_t)j * kNumLists + k], base = c->hlist_off[(size_t)j * kNumLists + k];
+        for (int64_t k0 = 0; k0 < n; k0 += c->run[k])
+          for (int i0 = 0; i0 < c->hbatch[j].q; i0 += kPointTile)
+            ht.push_back(Tile{j, (int)(base + k0), (int)(base + std::min<int64_t>(n, k0 + c->run[k])), i0});
+      }
+      if (ht.empty()) continue;
+      SNK_CK(c, upload(dtile, ht, st));
+      SNK_CK(c, cudaMemsetAsync(c->tickets.p, 0, sizeof(int), st));
+      IntegralArgs a = integral_args(c, ci, k);
+      a.tiles = dtile.p;
+      a.n_tiles = (int)ht.size();
+      a.ticket = c->tickets.p;
+      SNK_CK(c, launch_labels(st, k % kNumClasses, a, (int)std::min<int64_t>(c->max_ctas[k % kNumClasses], a.n_tiles),
+                              dslot.p, c->list_off.p, dxmax.p, dlab.p));
+      // the tile buffer is reused by the next list: wait for this launch
+      SNK_CK(c, cudaStreamSynchronize(st));
+    }
+  }
+  std::vector<float> hl((size_t)tot * 12);
+  SNK_CK(c, cudaMemcpyAsync(hl.data(), dlab.p, sizeof(float) * hl.size(), cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(feat, dfeat.p, sizeof(float) * tot * kMlpIn, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaStreamSynchronize(st));
+  for (int j : sb)
+    for (int64_t e = 0; e < entries[j]; ++e) {
+      const int64_t q = slot[j] + e;
+      float m = 0.f;
+      for (int u = 0; u < 12; ++u) m = std::max(m, hl[(size_t)q * 12 + u]);
+      lab[q] = (float)(std::log10(std::max((double)m, 1e-40)) / 10.0);
+    }
+  *n_out = tot;
+  return SNK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snk_screen_load(snk_ctx* c, const float* weights) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!weights) return fail(c, SNK_ERR_INVALID_ARG, "NULL weights");
+  for (int e = 0; e < kMlpWeights; ++e)
+    if (!std::isfinite(weights[e])) return fail(c, SNK_ERR_UNSUPPORTED, "non-finite MLP weight");
+  std::vector<float> w(weights, weights + kMlpWeights);
+  SNK_CK(c, upload(c->mlp_w, w, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  c->mlp_loaded = true;
+  return SNK_OK;
+}
+
+int snk_learn_collect(snk_ctx* c, int32_t stride, int64_t cap, float* features, float* labels, int64_t* n) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  return learn_collect(c, stride, cap, features, labels, n);
+}
+
+int snk_mlp_eval(const float* weights, const float* features, int64_t n, int32_t f16, float* out) {
+  if (!weights || n < 0 || (n > 0 && (!features || !out))) return SNK_ERR_INVALID_ARG;
+  if (n == 0) return SNK_OK;
+  DevBuf<float> dw, dx, dy;
+  if (dw.ensure(kMlpWeights) || dx.ensure((size_t)n * kMlpIn) || dy.ensure(n)) return SNK_ERR_OOM;
+  if (cudaMemcpy(dw.p, weights, sizeof(float) * kMlpWeights, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(dx.p, features, sizeof(float) * n * kMlpIn, cudaMemcpyHostToDevice))
+    return SNK_ERR_CUDA;
+  if (launch_mlp_forward(0, dw.p, dx.p, n, dy.p, f16 != 0) != cudaSuccess) return SNK_ERR_CUDA;
+  if (cudaMemcpy(out, dy.p, sizeof(float) * n, cudaMemcpyDeviceToHost)) return SNK_ERR_CUDA;
+  return SNK_OK;
+}
+
+int snk_mlp_grad(const float* weights, const float* features, const float* labels, int64_t n, float under_weight,
+                 float* grad, float* loss) {
+  if (!weights || !grad || !loss || n <= 0 || !features || !labels) return SNK_ERR_INVALID_ARG;
+  DevBuf<float> dw, dx, dy, dz, dd, dg, dl;
+  if (dw.ensure(kMlpWeights) || dx.ensure((size_t)n * kMlpIn) || dy.ensure(n) ||
+      dz.ensure((size_t)n * 3 * kMlpHidden) || dd.ensure((size_t)n * (3 * kMlpHidden + 1)) ||
+      dg.ensure(kMlpWeights) || dl.ensure(1))
+    return SNK_ERR_OOM;
+  if (cudaMemcpy(dw.p, weights, sizeof(float) * kMlpWeights, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(dx.p, features, sizeof(float) * n * kMlpIn, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(dy.p, labels, sizeof(float) * n, cudaMemcpyHostToDevice))
+    return SNK_ERR_CUDA;
+  if (launch_mlp_grad(0, dw.p, dx.p, dy.p, nullptr, n, under_weight, dz.p, dd.p, dg.p, dl.p) != cudaSuccess)
+    return SNK_ERR_CUDA;
+  if (cudaMemcpy(grad, dg.p, sizeof(float) * kMlpWeights, cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(loss, dl.p, sizeof(float), cudaMemcpyDeviceToHost))
+    return SNK_ERR_CUDA;
+  return SNK_OK;
+}
+
+int snk_mlp_train(const float* features, const float* labels, int64_t n, int32_t epochs, int32_t batch, float lr,
+                  float under_weight, uint64_t seed, int32_t init, float* weights, float* loss_history) {
+  if (!features || !labels || !weights || n <= 0 || epochs < 0 || batch < 1) return SNK_ERR_INVALID_ARG;
+  SplitMix rng{seed};
+  std::vector<float> w(weights, weights + kMlpWeights);
+  if (init) {
+    // He-normal weights, zero biases; the output bias starts at the mean label
+    const int nin[4] = {kMlpIn, kMlpHidden, kMlpHidden, kMlpHidden};
+    const int wo[4] = {0, kMlpIn * kMlpHidden + kMlpHidden,
+                       kMlpIn * kMlpHidden + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden,
+                       kMlpIn * kMlpHidden + kMlpHidden + 2 * (kMlpHidden * kMlpHidden + kMlpHidden)};
+    const int nout[4] = {kMlpHidden, kMlpHidden, kMlpHidden, 1};
+    std::fill(w.begin(), w.end(), 0.f);
+    for (int l = 0; l < 4; ++l) {
+      const double sd = std::sqrt((l == 3 ? 1.0 : 2.0) / nin[l]);
+      for (int e = 0; e < nin[l] * nout[l]; ++e) w[wo[l] + e] = (float)(sd * rng.normal());
+    }
+    double mean = 0.0;
+    for (int64_t s = 0; s < n; ++s) mean += labels[s];
+    w[kMlpWeights - 1] = (float)(mean / n);
+  }
+  const int64_t B = std::min<int64_t>(batch, n);
+  DevBuf<float> dw, dx, dy, dz, dd, dg, dm1, dm2, dl;
+  DevBuf<int64_t> didx;
+  const int64_t nsteps = (n + B - 1) / B;
+  if (dw.ensure(kMlpWeights) || dx.ensure((size_t)n * kMlpIn) || dy.ensure(n) ||
+      dz.ensure((size_t)B * 3 * kMlpHidden) || dd.ensure((size_t)B * (3 * kMlpHidden + 1)) ||
+      dg.ensure(kMlpWeights) || dm1.ensure(kMlpWeights) || dm2.ensure(kMlpWeights) || dl.ensure(nsteps) ||
+      didx.ensure(n))
+    return SNK_ERR_OOM;
+  if (cudaMemcpy(dw.p, w.data(), sizeof(float) * kMlpWeights, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(dx.p, features, sizeof(float) * n * kMlpIn, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(dy.p, labels, sizeof(float) * n, cudaMemcpyHostToDevice) ||
+      cudaMemset(dm1.p, 0, sizeof(float) * kMlpWeights) || cudaMemset(dm2.p, 0, sizeof(float) * kMlpWeights))
+    return SNK_ERR_CUDA;
+  std::vector<int64_t> idx(n);
+  for (int64_t s = 0; s < n; ++s) idx[s] = s;
+  std::vector<float> hl(nsteps);
+  int t = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int64_t s = n - 1; s > 0; --s) std::swap(idx[s], idx[rng.next() % (uint64_t)(s + 1)]);
+    if (cudaMemcpy(didx.p, idx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice)) return SNK_ERR_CUDA;
+    for (int64_t st = 0; st < nsteps; ++st) {
+      const int64_t b0 = st * B, nb = std::min<int64_t>(B, n - b0);
+      if (launch_mlp_grad(0, dw.p, dx.p, dy.p, didx.p + b0, nb, under_weight, dz.p, dd.p, dg.p, dl.p + st) !=
+              cudaSuccess ||
+          launch_adam(0, dw.p, dg.p, dm1.p, dm2.p, ++t, lr) != cudaSuccess)
+        return SNK_ERR_CUDA;
+    }
+    if (cudaMemcpy(hl.data(), dl.p, sizeof(float) * nsteps, cudaMemcpyDeviceToHost)) return SNK_ERR_CUDA;
+    double sum = 0.0, wsum = 0.0;
+    for (int64_t st = 0; st < nsteps; ++st) {
+      const double nb = (double)std::min<int64_t>(B, n - st * B);
+      sum += hl[st] * nb;
+      wsum += nb;
+    }
+    if (loss_history) loss_history[ep] = (float)(sum / wsum);
+  }
+  if (cudaMemcpy(weights, dw.p, sizeof(float) * kMlpWeights, cudaMemcpyDeviceToHost)) return SNK_ERR_CUDA;
+  return SNK_OK;
+}
+
+}  // extern "C"

@@ -34,6 +34,12 @@ constexpr int kBoysRowsF = 302;
 constexpr int kBoysTermsF = 6;
 constexpr int kBoysColsF = kBoysTermsF + 2;
 
+// Learned block screen: MLP 16 -> 64 -> 64 -> 64 -> 1 (ReLU).
+constexpr int kMlpIn = 16;
+constexpr int kMlpHidden = 64;
+constexpr int kMlpWeights = kMlpIn * kMlpHidden + kMlpHidden + 2 * (kMlpHidden * kMlpHidden + kMlpHidden) +
+                            kMlpHidden + 1;
+
 // Primitive pairs whose 3c-CP potential is below this everywhere are left out
 // of a shell pair (their total effect on K is below ~1e-14 for any basis here).
 constexpr double kPrimPairTol = 1e-20;
@@ -242,5 +248,20 @@ cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, co
 void class_flops(int cls, double* per_prim, double* per_pair);
 
 cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64);
+
+// learned screen
+cudaError_t launch_labels(cudaStream_t st, int cls, const IntegralArgs& a, int grid, const int64_t* slot_base,
+                          const int64_t* list_off, const double* xm, float* lab);
+cudaError_t launch_mlp_forward(cudaStream_t st, const float* w, const float* X, int64_t n, float* out, bool f16);
+cudaError_t launch_mlp_grad(cudaStream_t st, const float* w, const float* X, const float* Y, const int64_t* idx,
+                            int64_t n, float under_weight, float* Z, float* D, float* grad, float* loss);
+cudaError_t launch_adam(cudaStream_t st, float* w, const float* g, float* m1, float* m2, int t, float lr);
+cudaError_t launch_features(cudaStream_t st, const ScreenArgs& a, const int* pairlist, const int64_t* list_off,
+                            const int* counts, const int* sample_batches, const int64_t* sample_off, int n_sample,
+                            const float* shell_feat, float* feat);
+cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbatch, const float* w, int* pairlist,
+                                  const int64_t* list_off, int* counts, long long* ppcounts,
+                                  const float* shell_feat, float skip_log10, unsigned char* keep);
+cudaError_t launch_xmax(cudaStream_t st, const BatchDesc* dbatch, int nbatch, const double* ws, double* xm);
 
 }  // namespace snk
