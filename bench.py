@@ -1,26 +1,37 @@
 #!/usr/bin/env python3
-"""sn-K K-build throughput on GB300.
+"""sn-K K-build throughput on GB300: the chosen form against plain FP64.
 
-One step = one full K build of the 96-atom workload (992 Cartesian functions up
-to d, 768,000 grid points, 200 occupied orbitals, FP64): snk_set_density (P
-upload, symmetry check, F-tilde and sn-LinK pair screen, task lists) followed
-by snk_build_K (collocation, F = X P, 3c-CP integrals contracted into G,
-K-tilde = G^T X, symmetrisation).  Inputs are resident in HBM when the timed
-region starts (`value`); `e2e` repeats the measurement through the C ABI with
-host buffers, the P upload and the K download inside the timed region.
+One step = one full K build: snk_set_density (P upload, symmetry check,
+F-tilde, sn-LinK screen, learned screen, task lists) followed by snk_build_K
+(collocation, F = X P, 3c-CP integrals contracted into G, K-tilde = G^T X,
+symmetrisation).  Inputs are resident in HBM when the timed region starts
+(`value`); `e2e` repeats the chosen form through the C ABI with host buffers,
+the P upload and the K download inside the timed region.
+
+Forms:
+  plain   FP64 everywhere, rigorous sn-LinK screen at 1e-12 (eps_B = eps_E = eps_K)
+  chosen  rigorous screen at 1e-10, then the learned block screen (shipped
+          weights and calibrated threshold); pairs whose sn-LinK estimate is
+          below 3e-4 run their integrals in FP32, the rest in double-FP32 (hi +
+          lo float pairs, ~1e-14 relative); F = X P and Kt = G^T X in
+          double-FP32 arithmetic; G and K accumulated in FP64
+  (batch64: the 64 molecules in one handle, FP64, CUDA graph, autotuned tiles,
+   against 64 separate plain builds)
+
+Default workload: the 96-atom cluster (992 functions, 768,000 points).  Other
+workloads: --workload cluster256 | cluster512 | batch64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs under torchrun as independent replicas (the build does not shard);
 the value is the total builds of all ranks over the slowest rank's time.
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
-sample of grid points of the same workload and extrapolates to builds/s.
+sample of grid points of the same workload and scales to builds/s.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -33,23 +44,45 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sn-K K-builds/s at stated max|ΔK|: chosen form vs plain FP64, same GB300"
 WORKLOAD = "cluster96"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (2 DFMA/clk/SM x 152 SMs x ~2.06 GHz)
+# ALU peaks of GB300 (152 SMs at the 2070 MHz maximum SM clock): FP64 as the
+# recipe's nominal 1.25 TFLOP/s; FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz.
+# A DFMA / FFMA microbenchmark on this pool measured 1.19 and 73.2 TFLOP/s.
+FP64_PEAK = 1.25
+FP32_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12
+DF32_OPS_PER_MAC = 12      # FP32 instructions per double-FP32 multiply-add
+PLAIN = dict()
+CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="df32", ds_integrals=1)
+GOLDEN = {"cluster96": os.path.join(ROOT, "tests", "golden", "cluster96_K_entries.txt"),
+          "cluster256": os.path.join(ROOT, "tests", "golden", "cluster256_K_entries.txt")}
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def workload_config(p, name=WORKLOAD):
-    n_heavy = int((p.mol.Z == 8).sum())
-    return {"workload": f"{name}: {p.mol.Z.shape[0]} atoms ({n_heavy} O-like, {p.mol.Z.shape[0] - n_heavy} H-like), "
-                        f"{p.basis.n_functions} Cartesian functions up to d, {p.grid.n_points} grid points "
-                        f"(50 MK radial x 8 GL theta x 20 phi per atom, Becke), {p.meta['n_occ']} occupied orbitals",
-            "precision": "fp64", "screen": "sn-LinK eps_E = eps_K = eps_B = 1e-12", "batch_max": 4096,
-            "l2": "no flush: each step rewrites a >10 GB workspace (X, F, G), far above the 126 MB L2"}
+def make_problems(name, device=None):
+    import synth
+    if name == "batch64":
+        return [synth.multi_molecule(m, device=device) for m in range(64)]
+    return [getattr(synth, name)(device=device)]
+
+
+def workload_config(name, probs):
+    nat = sum(p.mol.Z.shape[0] for p in probs)
+    nh = sum(int((p.mol.Z == 8).sum()) for p in probs)
+    nf = sum(p.basis.n_functions for p in probs)
+    npts = sum(p.grid.n_points for p in probs)
+    if name == "batch64":
+        desc = (f"batch64: 64 molecules of 6-60 atoms ({nat} atoms, {nf} Cartesian functions up to d, {npts} grid "
+                f"points, 40-50 MK radial x 75-160 angular points per atom, Becke), 20% occupied columns")
+    else:
+        p = probs[0]
+        desc = (f"{name}: {nat} atoms ({nh} O-like, {nat - nh} H-like), {nf} Cartesian functions up to d, "
+                f"{npts} grid points (50 MK radial x 8 GL theta x 20 phi per atom, Becke), "
+                f"{p.meta.get('n_occ')} occupied orbitals")
+    return {"workload": desc, "batch_max": 4096,
+            "l2": "no flush: each step rewrites a workspace of several GB (X, F, G), far above the 126 MB L2"}
 
 
 class ClockSampler:
@@ -107,26 +140,22 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-GOLDEN = os.path.join(ROOT, "tests", "golden", "cluster96_K_entries.txt")
-
-
-def sampled_parity(K):
-    """max |K - K_oracle| over the stored oracle entries of the 96-atom workload."""
-    if not os.path.exists(GOLDEN):
-        return {"value": None, "note": "oracle entries file missing"}
-    d = np.loadtxt(GOLDEN)
+def golden_err(name, K):
+    """max |K - K_oracle| over the stored oracle entries of the workload, if any."""
+    path = GOLDEN.get(name)
+    if path is None or not os.path.exists(path):
+        return None
+    d = np.loadtxt(path)
     mu, nu, ref = d[:, 0].astype(int), d[:, 1].astype(int), d[:, 2]
-    err = float(np.max(np.abs(K[mu, nu] - ref)))
-    return {"value": err, "vs": f"{len(ref)} entries of the unscreened FP64 CPU oracle (tests/golden)",
-            "tolerance": 1e-10}
+    return float(np.max(np.abs(K[mu, nu] - ref)))
 
 
-def cpu_oracle_rate(p, target_s: float = 12.0):
+def cpu_oracle_rate(p, target_s: float = 12.0, seed: int = 0):
     """The oracle on a bounded random sample of grid points; returns
-    (builds/s extrapolated, threads, sample description)."""
+    (builds/s scaled to the full grid, threads, sample description)."""
     import oracle
     import synth
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(seed)
     n_total = p.grid.n_points
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
@@ -142,40 +171,131 @@ def cpu_oracle_rate(p, target_s: float = 12.0):
     n = int(min(n_total, max(n0, n0 * target_s / max(t0, 1e-3))))
     t = run(n)
     rate = (n / n_total) / t
-    return rate, cores, f"{n} of {n_total} grid points drawn at random (seed 0), {t:.1f} s; builds/s = (n/N_g)/t"
+    return rate, cores, f"{n} of {n_total} grid points drawn at random (seed {seed}), {t:.1f} s; " \
+                        f"builds/s = (n / N_g) / t"
 
 
 def run_reference(args, rank, world):
-    import synth
     if rank != 0:
         return 0
-    p = synth.cluster96()
     import oracle
+    import synth
     oracle.build()
+    probs = make_problems(args.workload)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     rng = np.random.default_rng(1)
+    n_total = sum(p.grid.n_points for p in probs)
     per_step = max(cores * 8, 64)
-    times = []
+    times, done = [], 0.0
     for step in range(args.warmup + args.steps):
-        idx = np.sort(rng.choice(p.grid.n_points, size=per_step, replace=False))
-        g = synth.Grid(xyz=p.grid.xyz[idx], w=p.grid.w[idx], atom=p.grid.atom[idx])
+        # a bounded sample of the workload's grid points (all molecules of a batch share the sample)
         t = time.perf_counter()
-        oracle.snk_K(p.basis, g, p.P, nthreads=cores)
+        frac = 0.0
+        for p in probs:
+            n = max(1, int(round(per_step * p.grid.n_points / n_total)))
+            idx = np.sort(rng.choice(p.grid.n_points, size=min(n, p.grid.n_points), replace=False))
+            g = synth.Grid(xyz=p.grid.xyz[idx], w=p.grid.w[idx], atom=p.grid.atom[idx])
+            oracle.snk_K(p.basis, g, p.P, nthreads=cores)
+            frac += idx.shape[0] / p.grid.n_points / len(probs)
         if step >= args.warmup:
             times.append(time.perf_counter() - t)
+            done += frac
     t = float(np.sum(times))
-    builds = args.steps * per_step / p.grid.n_points
-    value = builds / t
-    sample = (f"each step: the FP64 CPU oracle (plain C, OpenMP) on {per_step} of {p.grid.n_points} grid points; "
-              f"builds/s = steps * sample / N_g / time")
+    value = done / t
+    sample = (f"each step: the FP64 CPU oracle (plain C, OpenMP) on ~{per_step} of the workload's {n_total} grid "
+              f"points; builds/s = (sampled fraction of the grid, summed over steps) / time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "K-builds/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(p),
+            "data": "synthetic", "config": workload_config(args.workload, probs),
             "cpu_baseline": {"value": value, "unit": "K-builds/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "K-builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+class Runner:
+    """One form on one workload: engine(s), a device step and a host (C ABI) step."""
+
+    def __init__(self, snk, probs, opts, batched, dev, stream, learned=None):
+        import torch
+        self.snk, self.probs, self.batched, self.dev = snk, probs, batched, dev
+        t = time.perf_counter()
+        if batched:
+            self.engs = [snk.Engine([p.basis for p in probs], [p.grid for p in probs], **opts)]
+        elif len(probs) == 1:
+            self.engs = [snk.Engine(probs[0].basis, probs[0].grid, **opts)]
+        else:                                 # one plain engine per molecule
+            self.engs = [snk.Engine(p.basis, p.grid, **opts) for p in probs]
+        self.create_s = time.perf_counter() - t
+        for e in self.engs:
+            e.set_stream(stream)
+            if learned is not None:
+                e.screen_load(learned)
+        if batched:
+            Pd = np.concatenate([p.P.reshape(-1) for p in probs])
+            self.P = [torch.from_numpy(Pd).to(dev)]
+        else:
+            self.P = [torch.from_numpy(p.P).to(dev) for p in probs] if len(self.engs) > 1 else \
+                [torch.from_numpy(probs[0].P).to(dev)]
+        self.K = [torch.empty_like(x) for x in self.P]
+        self.runs = self.engs[0].autotune() if batched else None
+
+    def step(self):
+        for e, P, K in zip(self.engs, self.P, self.K):
+            e.set_density(P)
+            e.build_K(out=K)
+
+    def host_step(self, Ph, Kh):
+        for e, P, K in zip(self.engs, Ph, Kh):
+            e.set_density(P)
+            e.build_K(out=K)
+
+    def host_buffers(self):
+        if self.batched:
+            return [[np.ascontiguousarray(p.P) for p in self.probs]], [None]
+        return [np.ascontiguousarray(p.P) for p in self.probs], [np.empty_like(p.P) for p in self.probs]
+
+    def Ks(self):
+        """Per-molecule host copies of the last device K."""
+        if self.batched:
+            flat = self.K[0].cpu().numpy()
+            out, off = [], 0
+            for p in self.probs:
+                n = p.basis.n_functions
+                out.append(flat[off:off + n * n].reshape(n, n))
+                off += n * n
+            return out
+        return [k.cpu().numpy() for k in self.K]
+
+    def stats(self):
+        return [e.stats() for e in self.engs]
+
+    def close(self):
+        for e in self.engs:
+            e.close()
+
+
+def timed(runner, steps, warmup, stream, barrier):
+    import torch
+    for _ in range(warmup):
+        runner.step()
+    torch.cuda.synchronize()
+    acc = {}
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        runner.step()
+        for s in runner.stats():        # per-phase times from the library's events on the same stream
+            for k in ("ms_integrals", "ms_integrals_fp32", "ms_fgemm", "ms_kgemm", "ms_screen", "ms_collocation",
+                      "ms_finish", "integral_flops", "flops_fp32", "gemm_flops", "kernel_launches", "integrals"):
+                acc[k] = acc.get(k, 0.0) + float(s[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1), acc
 
 
 def main():
@@ -183,16 +303,18 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--plain-steps", type=int, default=None)
+    ap.add_argument("--plain-warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["cluster96", "cluster256", "cluster512", "batch64"])
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
     import torch
-    import synth
     import paper_2303_14280_gb300 as snk
 
     torch.cuda.set_device(local)
@@ -205,97 +327,148 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(x):
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     snk.lib()
     dev = torch.device("cuda", local)
-    p = synth.cluster96(device=dev) if args.workload == WORKLOAD else getattr(synth, args.workload)(device=dev)
-    t_create = time.perf_counter()
-    eng = snk.Engine(p.basis, p.grid)
-    t_create = time.perf_counter() - t_create
     stream = torch.cuda.current_stream()
-    eng.set_stream(stream)
-    nf = eng.nf
-    Pd = torch.from_numpy(p.P).to(dev)
-    Kd = torch.empty_like(Pd)
+    batch = args.workload == "batch64"
+    probs = make_problems(args.workload, device=dev)
+    n_mol = len(probs)
 
-    def step():
-        eng.set_density(Pd)
-        eng.build_K(out=Kd)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    st = eng.stats()
-
-    # device-resident timing: K steps between events on the engine's stream
-    k_ms_int, flops_int = 0.0, 0.0
+    # ---- chosen form
+    learned = None
+    if batch:
+        chosen_opts = dict(graph=1)
+        form = "batched FP64: 64 molecules in one handle, one launch per phase, CUDA graph replay, autotuned tiles"
+    else:
+        chosen_opts = dict(CHOSEN)
+        form = ("mixed: rigorous sn-LinK at 1e-10, FP32 integrals for pairs with estimate < 3e-4, double-FP32 "
+                "integrals otherwise, double-FP32 GEMMs, FP64 G and K accumulation")
+        if not args.no_learned and os.path.exists(snk.SCREEN_WEIGHTS):
+            learned, thr, _ = snk.trained_screen()
+            chosen_opts.update(screen="learned", learned_skip=thr)
+            form += f", learned block screen (skip below 10^{thr:g})"
+    ch = Runner(snk, probs, chosen_opts, batch, dev, stream, learned)
     with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-            s = eng.stats()       # integral-kernel time from the library's events on the same stream
-            k_ms_int += s["ms_integrals"]
-            flops_int += s["integral_flops"]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    ms = e0.elapsed_time(e1)
+        ms, acc = timed(ch, args.steps, args.warmup, stream, barrier)
     clocks = clk.summary()
-    st = eng.stats()
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = world * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms)
+    value = world * args.steps * (n_mol if batch else 1) / (ms * 1e-3)
+    unit = "molecule K-builds/s" if batch else "K-builds/s"
+    st_ch = ch.stats()
+    K_ch = ch.Ks()
 
-    # end to end through the C ABI with host buffers
-    Ph = np.ascontiguousarray(p.P)
-    Kh = np.empty_like(Ph)
+    # e2e through the C ABI with host buffers (P upload and K download inside)
+    Ph, Kh = ch.host_buffers()
     barrier()
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(args.steps):
-        eng.set_density(Ph)
-        eng.build_K(out=Kh)
+        if batch:
+            ch.engs[0].set_density(Ph[0])
+            Kh = [ch.engs[0].build_K()]
+        else:
+            ch.host_step(Ph, Kh)
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / float(e2e_t.item())
-    kdiff = float(np.max(np.abs(Kh - Kd.cpu().numpy())))
+    e2e_s = max_over_ranks(time.perf_counter() - t)
+    e2e_value = world * args.steps * (n_mol if batch else 1) / e2e_s
+    nbytes = sum(p.P.nbytes for p in probs)
+    ch_create = ch.create_s
+    ch.close()
 
-    achieved = flops_int / (k_ms_int * 1e-3) / 1e12 if k_ms_int > 0 else None
-    dK = sampled_parity(Kh) if args.workload == WORKLOAD else None
+    # ---- plain FP64 beside it
+    pl = Runner(snk, probs, dict(PLAIN), False, dev, stream)
+    ps = args.plain_steps if args.plain_steps is not None else args.steps
+    pw = args.plain_warmup if args.plain_warmup is not None else args.warmup
+    ms_pl, acc_pl = timed(pl, ps, pw, stream, barrier)
+    ms_pl = max_over_ranks(ms_pl)
+    value_pl = world * ps * n_mol / (ms_pl * 1e-3)
+    K_pl = pl.Ks()
+    st_pl = pl.stats()
+    pl.close()
+
+    dK_ch_pl = max(float(np.max(np.abs(a - b))) for a, b in zip(K_ch, K_pl))
+    err_ch = golden_err(args.workload, K_ch[0]) if not batch else None
+    err_pl = golden_err(args.workload, K_pl[0]) if not batch else None
+
+    # ---- rooflines of the chosen step's kernels (library events, same stream)
+    n = args.steps
+    kern = {}
+    if acc.get("ms_integrals_fp32", 0) > 0:
+        a = acc["flops_fp32"] / (acc["ms_integrals_fp32"] * 1e-3) / 1e12
+        kern["integral_kernel_f32"] = {"ms_per_step": acc["ms_integrals_fp32"] / n, "bound": "alu", "achieved": a,
+                                       "peak": FP32_PEAK, "unit": "TFLOP/s", "frac": a / FP32_PEAK}
+    ms64 = acc["ms_integrals"]          # the FP64 (or ds) lists; the FP32 lists are counted apart
+    if ms64 > 0:
+        a = acc["integral_flops"] / (ms64 * 1e-3) / 1e12
+        if chosen_opts.get("ds_integrals"):
+            # ds arithmetic runs on the FP32 pipe: frac above 1 is the gain over the FP64 pipe's ceiling
+            kern["integral_kernel_ds"] = {"ms_per_step": ms64 / n, "bound": "alu", "achieved": a,
+                                          "peak": FP64_PEAK, "unit": "TFLOP/s (FP64-equivalent flops)",
+                                          "frac": a / FP64_PEAK}
+        else:
+            kern["integral_kernel"] = {"ms_per_step": ms64 / n, "bound": "alu", "achieved": a, "peak": FP64_PEAK,
+                                       "unit": "TFLOP/s", "frac": a / FP64_PEAK}
+    gms = acc["ms_fgemm"] + acc["ms_kgemm"]
+    if gms > 0:
+        a = acc["gemm_flops"] / (gms * 1e-3) / 1e12
+        if not batch:     # double-FP32: 12 FP32 instructions per multiply-add
+            peak = FP32_PEAK / DF32_OPS_PER_MAC
+            kern["fgemm_kgemm_df32"] = {"ms_per_step": gms / n, "bound": "alu", "achieved": a, "peak": peak,
+                                        "unit": "TFLOP/s (FP64-equivalent 2 flop per multiply-add)",
+                                        "frac": a / peak}
+        else:
+            kern["fgemm_kgemm_fp64"] = {"ms_per_step": gms / n, "bound": "alu", "achieved": a, "peak": FP64_PEAK,
+                                        "unit": "TFLOP/s", "frac": a / FP64_PEAK}
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"]) if kern else None
+    roof = None
+    if dom:
+        d = kern[dom]
+        roof = {"bound": d["bound"], "kernel": dom, "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": None,
+                "peak_source": "nominal ALU peak at 2070 MHz (FP64: the recipe's 1.25 TFLOP/s; FP32: 152 SMs x 128 "
+                               "lanes x 2 flop); ALU peaks are not in MEASURED_PEAKS.json"}
+
     line = {
-        "metric": METRIC, "value": value, "unit": "K-builds/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(p, args.workload),
-        "form": "plain FP64", "max_abs_dK": dK,
-        "integrals_per_s": st["integrals"] / (ms / args.steps * 1e-3),
-        "phases_ms": {k: st[k] for k in ("ms_screen", "ms_collocation", "ms_fgemm", "ms_integrals", "ms_kgemm",
-                                         "ms_finish", "ms_build")},
-        "integral_ms_by_class": dict(zip(["ss", "ps", "pp", "ds", "dp", "dd"], st["ms_integrals_class"])),
-        "pairs_kept": st["pairs_kept"], "n_batches": st["n_batches"], "integrals_per_build": st["integrals"],
-        "create_s": t_create,
-        "roofline": {"bound": "alu", "kernel": "integral_kernel<la,lb> (FP64 VRR/HRR + contraction)",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-                     "peak_source": "nominal FP64 of the recipe (not in MEASURED_PEAKS.json); a DFMA microbenchmark "
-                                    "measured 1.19 TFLOP/s"},
+        "vs_baseline": None, "dtype": "f64" if batch else "f64+f32", "data": "synthetic",
+        "config": workload_config(args.workload, probs),
+        "form": form,
+        "max_abs_dK": {"chosen_vs_oracle_entries": err_ch, "plain_vs_oracle_entries": err_pl,
+                       "chosen_vs_plain_full": dK_ch_pl,
+                       "stated_tolerance": 1e-10 if batch else 1e-8},
+        "plain_fp64": {"value": value_pl, "unit": unit, "ms_per_step": ms_pl / ps, "steps": ps, "warmup": pw,
+                       "pairs_kept": sum(s["pairs_kept"] for s in st_pl)},
+        "speedup_vs_plain_fp64": value / value_pl,
+        "integrals_per_s": acc["integrals"] / (ms * 1e-3),
+        "phases_ms_per_step": {k: acc[k] / n for k in ("ms_screen", "ms_collocation", "ms_fgemm", "ms_integrals",
+                                                         "ms_integrals_fp32", "ms_kgemm", "ms_finish")},
+        "kernels": kern,
+        "pairs_kept": sum(s["pairs_kept"] for s in st_ch),
+        "pairs_kept_fp32": sum(s["pairs_kept_fp32"] for s in st_ch),
+        "pairs_learned_skipped": sum(s["pairs_learned_skipped"] for s in st_ch),
+        "create_s": ch_create,
+        "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": int(st["kernel_launches"]) * args.steps,
-        "e2e": {"value": e2e_value, "unit": "K-builds/s", "h2d_bytes_per_step": nf * nf * 8,
-                "d2h_bytes_per_step": nf * nf * 8, "host_vs_device_K_max_abs_diff": kdiff},
+        "gpu_launches": int(acc["kernel_launches"]),
+        "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
     }
+    if batch:
+        line["autotuned_pairs_per_tile"] = ch.runs
+        line["phases_ms_per_step"] = None   # graph replay: no per-phase events
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(p)
-        line["cpu_baseline"] = {"value": rate, "unit": "K-builds/s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
-    eng.close()
+        rate, cores, sample = cpu_oracle_rate(probs[0] if not batch else probs[int(np.argmax(
+            [p.grid.n_points for p in probs]))])
+        if batch:
+            sample += " (largest molecule of the batch; molecule builds/s)"
+        line["cpu_baseline"] = {"value": rate, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -83,6 +83,7 @@ typedef struct {
 
 typedef enum { SNK_PREC_FP64 = 0, SNK_PREC_MIXED = 1 } snk_precision;
 typedef enum { SNK_SCREEN_NONE = 0, SNK_SCREEN_LINK = 1, SNK_SCREEN_LEARNED = 2 } snk_screen_mode;
+typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1 } snk_gemm_mode;
 
 typedef struct {
   double eps_basis;        /* epsilon_B of Eq. (basis_screen); <= 0 keeps all   */
@@ -106,7 +107,16 @@ typedef struct {
                               replay it; phase times are then not reported      */
   double learned_skip;     /* learned screen: skip a block whose predicted log10
                               contribution to K is below this (default -11)     */
-  double reserved[6];
+  int32_t gemm;            /* mixed form: SNK_GEMM_FP64 (default) or SNK_GEMM_DF32,
+                              F = X P and Kt = G^T X in double-FP32 arithmetic on the
+                              FP32 pipe (operands as hi + lo float pairs, error-free
+                              TwoSum accumulation, ~2^-46 relative); not combined
+                              with tensor_gemms (SNK_ERR_INVALID_ARG)            */
+  int32_t ds_integrals;    /* mixed form: 1 runs the integrals of the pairs above
+                              fp32_bound in double-FP32 arithmetic (hi + lo float
+                              pairs on the FP32 pipe, ~1e-14 relative) instead of
+                              FP64; default 0                                   */
+  double reserved[5];
 } snk_options;
 
 /* Per-build counters and phase times (CUDA events on the library stream). */

@@ -36,6 +36,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported input", -3: "density
           -4: "bad call order", -5: "out of memory", -6: "CUDA error", -7: "device wait timed out"}
 SCREEN = {"none": 0, "link": 1, "learned": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
+GEMM = {"fp64": 0, "df32": 1}
 LISTS = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
 # every entry point declared in include/snk.h
@@ -71,7 +72,8 @@ class SnkOptions(ctypes.Structure):
                 ("batch_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("distance_bound", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("tensor_gemms", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("learned_skip", ctypes.c_double), ("reserved", ctypes.c_double * 6)]
+                ("learned_skip", ctypes.c_double), ("gemm", ctypes.c_int32), ("ds_integrals", ctypes.c_int32),
+                ("reserved", ctypes.c_double * 5)]
 
 
 class SnkStats(ctypes.Structure):
@@ -155,6 +157,8 @@ def options(**kw) -> SnkOptions:
             v = SCREEN[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        if k == "gemm" and isinstance(v, str):
+            v = GEMM[v]
         if k == "eps":
             o.eps_basis = o.eps_E = o.eps_K = float(v)
             continue
@@ -220,6 +224,22 @@ def mlp_grad(weights, features, labels, under_weight=4.0):
     if rc != SNK_OK:
         raise SnkError(rc, "snk_mlp_grad")
     return float(loss[0]), g
+
+
+SCREEN_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "screen_mlp.npz")
+
+
+def trained_screen(path=SCREEN_WEIGHTS):
+    """The shipped learned-screen weights and calibrated skip threshold
+    (written by train_screen.py): (weights float32[MLP_WEIGHTS], threshold, meta dict)."""
+    import json
+    with np.load(path) as z:
+        w = np.ascontiguousarray(z["weights"], dtype=np.float32)
+        t = float(z["threshold"])
+        meta = json.loads(str(z["meta"]))
+    if w.size != MLP_WEIGHTS:
+        raise ValueError(f"{path}: {w.size} weights, expected {MLP_WEIGHTS}")
+    return w, t, meta
 
 
 def _basis_struct(basis, keep):

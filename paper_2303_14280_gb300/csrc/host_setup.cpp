@@ -455,6 +455,29 @@ void build_boys_tables(Setup* s) {
       row[kBoysTerms + 1] = T;
     }
   }
+  // ds table of the mixed form: nodes T_k rounded to (hi, lo) float pairs and
+  // the values at those nodes split the same way, so that T_k - T is exact in
+  // ds arithmetic
+  s->boys_ds.assign((size_t)(kBoysLMax + 1) * kBoysRows * kBoysCols * 2, 0.0f);
+  for (int k = 0; k < kBoysRows; ++k) {
+    const double T0 = k * kBoysH;
+    const float th = (float)T0;
+    const float tl = (float)(T0 - (double)th);
+    const double T = (double)th + (double)tl;
+    host_boys(kBoysLMax + kBoysTerms, T, F);
+    for (int L = 0; L <= kBoysLMax; ++L) {
+      float* row = &s->boys_ds[(((size_t)L * kBoysRows + k) * kBoysCols) * 2];
+      double v[kBoysCols];
+      for (int m = 0; m < kBoysTerms; ++m) v[m] = F[L + m] * invfact[m];
+      v[kBoysTerms] = std::exp(-T);
+      for (int m = 0; m < kBoysTerms + 1; ++m) {
+        row[2 * m] = (float)v[m];
+        row[2 * m + 1] = (float)(v[m] - (double)row[2 * m]);
+      }
+      row[2 * (kBoysTerms + 1)] = th;
+      row[2 * (kBoysTerms + 1) + 1] = tl;
+    }
+  }
   // FP32 table of the mixed form (rounded from the same FP64 values)
   s->boys_f.assign((size_t)(kBoysLMax + 1) * kBoysRowsF * kBoysColsF, 0.0f);
   for (int k = 0; k < kBoysRowsF; ++k)

@@ -227,6 +227,111 @@ __device__ __forceinline__ void tf32x3_tile(int m0, int n0, int mdim, int ndim, 
       }
 }
 
+// ---------------------------------------------------------------- double-FP32 tile (mixed form)
+
+// Operands as unevaluated sums hi + lo of two floats (hi = fl32(v), lo =
+// fl32(v - hi): 48 significant bits).  a b = ah bh + (ah bl + al bh) + al bl:
+// ah bh is split exactly into p + e (e by an FMA), the al bl term (~2^-48
+// relative) is dropped, and the running sum (s, c) adds p with Knuth's
+// error-free TwoSum and everything else into the compensation c.  Twelve FP32
+// operations per multiply-add on the FP32 pipe (64x the FP64 issue rate on
+// GB300), relative error ~k 2^-46 for a length-k sum of same-sign terms.
+__device__ __forceinline__ float2 df32_split(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+__device__ __forceinline__ void df32_mac(float2 a, float2 b, float& s, float& c) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// C[m][n] = sum_k A(m,k) B(k,n) for the 64 x 64 tile at (m0, n0) with float2
+// (hi, lo) operands; la(m, k), lb(k, n) return (0, 0) outside the operands.
+template <class LA, class LB, class ST>
+__device__ __forceinline__ void df32_tile(int m0, int n0, int mdim, int ndim, int kdim, LA la, LB lb, ST st,
+                                          bool a_k_fast, bool b_k_fast) {
+  __shared__ float2 As[TK][TM + 1];
+  __shared__ float2 Bs[TK][TN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.f;
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < kdim; k0 += TK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + r * GEMM_THREADS;
+      int kk, mm;
+      if (a_k_fast) {
+        kk = e % TK;
+        mm = e / TK;
+      } else {
+        mm = e % TM;
+        kk = e / TM;
+      }
+      int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < mdim && k < kdim) ? la(m, k) : zero;
+      int nn;
+      if (b_k_fast) {
+        kk = e % TK;
+        nn = e / TK;
+      } else {
+        nn = e % TN;
+        kk = e / TN;
+      }
+      const int n = n0 + nn;
+      k = k0 + kk;
+      Bs[kk][nn] = (n < ndim && k < kdim) ? lb(k, n) : zero;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty + 16 * q];
+        b[q] = Bs[kk][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df32_mac(a[p], b[q], s[p][q], c[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + ty + 16 * p, n = n0 + tx + 16 * q;
+      if (m < mdim && n < ndim) st(m, n, (double)s[p][q] + (double)c[p][q]);
+    }
+}
+
+// In place: every double of buf[0, n) becomes its (hi, lo) float pair.
+__global__ void split_df32_kernel(double* __restrict__ buf, int64_t n) {
+  float2* out = reinterpret_cast<float2*>(buf);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = df32_split(buf[e]);
+}
+
+// dst[e] = (hi, lo) of src[e].
+__global__ void split_df32_copy_kernel(const double* __restrict__ src, int64_t n, float2* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = df32_split(src[e]);
+}
+
 // ---------------------------------------------------------------- collocation
 
 constexpr int COL_THREADS = 128, COL_SHELLS = 8;
@@ -482,56 +587,72 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, c
 // F-hat_{s i} = w_i f_s sum_{nu in B_j} X_{nu i} P_{nu s}: the quadrature weight
 // and the Cartesian component factor of the column are folded into F.  In the
 // mixed form an FP32 copy is written for the FP32 pairs.
-template <bool TENSOR>
-__global__ void __launch_bounds__(TENSOR ? TC_THREADS : GEMM_THREADS)
-    fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P, const int* __restrict__ xfunc,
-                 const int* __restrict__ sfunc, const double* __restrict__ fcomp, const double* __restrict__ w,
-                 double* __restrict__ ws, float* __restrict__ ws32) {
+template <int MODE>  // MODE: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32
+__global__ void __launch_bounds__(MODE == 1 ? TC_THREADS : GEMM_THREADS, MODE == 2 ? 2 : 3)
+    fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P, const float2* __restrict__ P2,
+                 const int* __restrict__ xfunc, const int* __restrict__ sfunc, const double* __restrict__ fcomp,
+                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32) {
   const BatchDesc bd = batches[blockIdx.z];
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   if (m0 >= bd.ldq || n0 >= bd.nS) return;
-  const double* X = ws + bd.xoff;
   double* F = ws + bd.foff;
   float* F32 = ws32 ? ws32 + bd.foff32 : nullptr;
-  const double* Pm = P + bd.pk_off;
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   const double* fc = fcomp + bd.mf0;
-  auto la = [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; };
-  auto lb = [&](int k, int n) { return Pm[(int64_t)xf[k] * bd.nfm + sf[n]]; };
   auto st = [&](int m, int n, double c) {
     const double wi = m < bd.q ? w[bd.p0 + m] : 0.0;
     const double v = wi * fc[sf[n]] * c;
     F[(int64_t)n * bd.ldq + m] = v;
     if (F32) F32[(int64_t)n * bd.ldq + m] = (float)v;
   };
-  if (TENSOR)
-    tf32x3_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
-  else
-    gemm_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+  if (MODE == 2) {
+    const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
+    const float2* Pm2 = P2 + bd.pk_off;
+    auto la = [&](int m, int k) { return X2[(int64_t)k * bd.ldq + m]; };
+    auto lb = [&](int k, int n) { return Pm2[(int64_t)xf[k] * bd.nfm + sf[n]]; };
+    df32_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+  } else {
+    const double* X = ws + bd.xoff;
+    const double* Pm = P + bd.pk_off;
+    auto la = [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; };
+    auto lb = [&](int k, int n) { return Pm[(int64_t)xf[k] * bd.nfm + sf[n]]; };
+    if (MODE == 1)
+      tf32x3_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+    else
+      gemm_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+  }
 }
 
 // Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the molecule's block
 // of the packed accumulator (several batches add to the same entries).
-template <bool TENSOR>
-__global__ void __launch_bounds__(TENSOR ? TC_THREADS : GEMM_THREADS)
+template <int MODE>
+__global__ void __launch_bounds__(MODE == 1 ? TC_THREADS : GEMM_THREADS, MODE == 2 ? 2 : 3)
     kgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc, const int* __restrict__ sfunc,
                  const double* __restrict__ ws, double* __restrict__ Khat) {
   const BatchDesc bd = batches[blockIdx.z];
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   if (m0 >= bd.nS || n0 >= bd.nB) return;
-  const double* X = ws + bd.xoff;
-  const double* G = ws + bd.goff;
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   double* Km = Khat + bd.pk_off;
-  auto la = [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; };
-  auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
   auto st = [&](int m, int n, double c) { atomicAdd(&Km[(int64_t)sf[m] * bd.nfm + xf[n]], c); };
-  if (TENSOR)
-    tf32x3_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
-  else
-    gemm_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+  if (MODE == 2) {
+    const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
+    const float2* G2 = reinterpret_cast<const float2*>(ws + bd.goff);
+    auto la = [&](int m, int k) { return G2[(int64_t)m * bd.ldq + k]; };
+    auto lb = [&](int k, int n) { return X2[(int64_t)n * bd.ldq + k]; };
+    df32_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+  } else {
+    const double* X = ws + bd.xoff;
+    const double* G = ws + bd.goff;
+    auto la = [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; };
+    auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
+    if (MODE == 1)
+      tf32x3_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+    else
+      gemm_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+  }
 }
 
 // G += G32 over a chunk's contiguous G region (mixed form).
@@ -634,25 +755,43 @@ cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 }
 
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
-                         const double* P, const int* xfunc, const int* sfunc, const double* fcomp, const double* w,
-                         double* ws, float* ws32, bool tensor) {
+                         const double* P, const float2* P2, const int* xfunc, const int* sfunc, const double* fcomp,
+                         const double* w, double* ws, float* ws32, int mode) {
   if (nbatch == 0 || max_ldq == 0 || max_nS == 0) return cudaSuccess;
   dim3 grid((max_ldq + TM - 1) / TM, (max_nS + TN - 1) / TN, nbatch);
-  if (tensor)
-    fgemm_kernel<true><<<grid, TC_THREADS, 0, st>>>(dbatch, P, xfunc, sfunc, fcomp, w, ws, ws32);
+  if (mode == 1)
+    fgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32);
+  else if (mode == 2)
+    fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32);
   else
-    fgemm_kernel<false><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, xfunc, sfunc, fcomp, w, ws, ws32);
+    fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, bool tensor) {
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode) {
   if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
   dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
-  if (tensor)
-    kgemm_kernel<true><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
+  if (mode == 1)
+    kgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
+  else if (mode == 2)
+    kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
   else
-    kgemm_kernel<false><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
+    kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_df32(cudaStream_t st, double* buf, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  split_df32_kernel<<<grid, 256, 0, st>>>(buf, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n, float2* dst) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  split_df32_copy_kernel<<<grid, 256, 0, st>>>(src, n, dst);
   return cudaGetLastError();
 }
 

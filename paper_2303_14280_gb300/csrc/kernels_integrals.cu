@@ -22,6 +22,7 @@
 
 #include <cstdint>
 
+#include "ds_arith.cuh"
 #include "os_generated.cuh"
 #include "snk_internal.h"
 
@@ -323,6 +324,158 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   }
 }
 
+// ---------------------------------------------------------------- double-FP32 pairs (mixed form)
+
+// Constants of the ds Boys evaluation as (hi, lo) float pairs, rounded at
+// compile time: 1/m! for the e^x Taylor series, then 1/(2n+1).
+struct DsConst {
+  float hi, lo;
+};
+#define SNK_DS_C(v) {(float)(v), (float)((v) - (double)(float)(v))}
+__constant__ DsConst c_ds_invfact[8] = {SNK_DS_C(1.0),         SNK_DS_C(1.0),         SNK_DS_C(1.0 / 2.0),
+                                        SNK_DS_C(1.0 / 6.0),   SNK_DS_C(1.0 / 24.0),  SNK_DS_C(1.0 / 120.0),
+                                        SNK_DS_C(1.0 / 720.0), SNK_DS_C(1.0 / 5040.0)};
+__constant__ DsConst c_ds_inv_odd[kBoysLMax + 1] = {SNK_DS_C(1.0), SNK_DS_C(1.0 / 3.0), SNK_DS_C(1.0 / 5.0),
+                                                    SNK_DS_C(1.0 / 7.0), SNK_DS_C(1.0 / 9.0)};
+#undef SNK_DS_C
+
+__device__ __forceinline__ ds ds_ld(const float2* p) {
+  const float2 v = *p;
+  return ds_make(v.x, v.y);
+}
+
+__device__ __forceinline__ ds ds_c(const DsConst& c) { return ds_make(c.hi, c.lo); }
+
+// S_n = pref F_n(T), n = 0..L, in ds arithmetic: the FP64 method's 8-term
+// Taylor expansion about the nearest node of the 0.1-spaced table (nodes
+// rounded to ds-representable values, so T_k - T is exact to ds precision),
+// the downward recursion with e^{-T} = e^{-T_k} e^{x}, and the asymptotic
+// form above T = 50 with a ds reciprocal square root.
+template <int L>
+__device__ __forceinline__ void boys_seeds_ds(ds T, ds pref, ds pref_far, const float2* tab, ds* S) {
+  if (T.hi < (float)kBoysTMax) {
+    const int k = __float2int_rn(T.hi * (float)(1.0 / kBoysH));
+    const float2* row = tab + k * kBoysCols;
+    const ds x = ds_ld(row + kBoysCols - 1) - T;  // T_k - T, |x| <= 0.05
+    ds f = ds_ld(row + 7);
+#pragma unroll
+    for (int m = 6; m >= 0; --m) f = fma(f, x, ds_ld(row + m));
+    S[L] = pref * f;
+    if (L > 0) {
+      ds e = ds_c(c_ds_invfact[7]);
+#pragma unroll
+      for (int m = 6; m >= 0; --m) e = fma(e, x, ds_c(c_ds_invfact[m]));
+      const ds pe = (pref * ds_ld(row + kBoysTerms)) * e;
+      const ds T2 = ds_make(2.0f * T.hi, 2.0f * T.lo);
+#pragma unroll
+      for (int n = L - 1; n >= 0; --n) S[n] = fma(T2, S[n + 1], pe) * ds_c(c_ds_inv_odd[n]);
+    }
+  } else {
+    const ds r = ds_rsqrt(T);
+    S[0] = pref_far * r;
+    if (L > 0) {
+      const ds o = (r * r) * 0.5f;
+#pragma unroll
+      for (int n = 0; n < L; ++n) S[n + 1] = S[n] * (o * (float)(2 * n + 1));
+    }
+  }
+}
+
+// Contracted Xi_ab of one pair at the point c in ds arithmetic; the primitive
+// pair data are the host-split (hi, lo) copies of PrimPair (12 pairs each).
+template <int LA, int LB>
+__device__ __forceinline__ void pair_xi_ds(const PairHdr& h, const float2* __restrict__ prims, const float2* tab,
+                                           ds cx, ds cy, ds cz, ds* xi) {
+  using C = OsClass<LA, LB>;
+  ds acc[C::NACC];
+#pragma unroll
+  for (int k = 0; k < C::NACC; ++k) acc[k] = ds_make(0.f, 0.f);
+  for (int q = 0; q < h.pp_n; ++q) {
+    const float2* pp = prims + (size_t)(h.pp_off + q) * 12;
+    const ds zeta = ds_ld(pp);
+    const ds PCx = ds_ld(pp + 1) - cx, PCy = ds_ld(pp + 2) - cy, PCz = ds_ld(pp + 3) - cz;
+    const ds T = zeta * fma(PCx, PCx, fma(PCy, PCy, PCz * PCz));
+    ds S[C::L + 1];
+    boys_seeds_ds<C::L>(T, ds_ld(pp + 7), ds_ld(pp + 8), tab, S);
+    C::vrr(S, ds_ld(pp + 4), ds_ld(pp + 5), ds_ld(pp + 6), PCx, PCy, PCz, ds_ld(pp + 9), ds_ld(pp + 10),
+           ds_ld(pp + 11), acc);
+  }
+  C::hrr(acc, ds_from(h.ABx), ds_from(h.ABy), ds_from(h.ABz), xi);
+}
+
+// The FP64 lists of the mixed form in ds arithmetic: same tiles, tickets,
+// contraction and FP64 G atomics as integral_kernel; F is read in FP64 and
+// split, each G update is rounded to FP64 once.
+template <int LA, int LB>
+__global__ void __launch_bounds__(kIntThreads) integral_kernel_ds(IntegralArgs a) {
+  using C = OsClass<LA, LB>;
+  constexpr int NA = C::NA, NB = C::NB;
+  extern __shared__ float2 s_tab2[];
+  const float2* gtab = a.boys_ds + (size_t)C::L * kBoysRows * kBoysCols;
+  for (int e = threadIdx.x; e < kBoysRows * kBoysCols; e += blockDim.x) s_tab2[e] = gtab[e];
+  __shared__ int s_tile;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= a.n_tiles) break;
+    const Tile tile = a.tiles[t];
+    const BatchDesc bd = a.batches[tile.batch];
+    const int i = tile.i0 + threadIdx.x;
+    if (i >= bd.q) continue;
+    const int64_t ldq = bd.ldq;
+    const ds cx = ds_from(a.xyz[3 * (bd.p0 + i)]), cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]),
+             cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
+    const double* F = a.ws + bd.foff + i;
+    double* G = a.ws + bd.goff + i;
+    const int* cmap = a.colmap + bd.cm_off - bd.ms0;
+    ds ga[NA], fa[NA];
+    int cur = -1, cola = 0;
+    for (int k = tile.k0; k < tile.k1; ++k) {
+      const PairHdr h = a.pairs[a.pairlist[k]];
+      if (h.sa != cur) {
+        if (cur >= 0) {
+#pragma unroll
+          for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ds_to(ga[u]));
+        }
+        cur = h.sa;
+        cola = cmap[cur];
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          ga[u] = ds_make(0.f, 0.f);
+          fa[u] = ds_from(F[(cola + u) * ldq]);
+        }
+      }
+      const int colb = cmap[h.sb];
+      if (cola < 0 || colb < 0) continue;  // cannot happen: the screen marks both shells of a kept pair
+      ds fb[NB];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) fb[v] = ds_from(F[(colb + v) * ldq]);
+      ds xi[NA * NB];
+      pair_xi_ds<LA, LB>(h, a.prims_ds, s_tab2, cx, cy, cz, xi);
+#pragma unroll
+      for (int u = 0; u < NA; ++u)
+#pragma unroll
+        for (int v = 0; v < NB; ++v) ga[u] = fma(xi[u * NB + v], fb[v], ga[u]);
+      if (h.sa != h.sb) {
+#pragma unroll
+        for (int v = 0; v < NB; ++v) {
+          ds g = ds_make(0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < NA; ++u) g = fma(xi[u * NB + v], fa[u], g);
+          atomicAdd(G + (colb + v) * ldq, ds_to(g));
+        }
+      }
+    }
+    if (cur >= 0) {
+#pragma unroll
+      for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ds_to(ga[u]));
+    }
+  }
+}
+
 // Training labels of the learned screen, from the plain FP64 integrals: for
 // every list entry (batch j, pair ab) of the sampled batches, the sums over
 // the batch's points of |dG_u(i)| max_nu |Phi_{nu i}|, dG_u the block's
@@ -442,6 +595,11 @@ cudaError_t launch_class(cudaStream_t st, bool f32, const IntegralArgs& a, int g
         cudaFuncSetAttribute(integral_kernel_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
     if (e != cudaSuccess) return e;
     integral_kernel_f32<LA, LB><<<grid, kIntThreads, kSmem32, st>>>(a);
+  } else if (a.prims_ds) {
+    cudaError_t e =
+        cudaFuncSetAttribute(integral_kernel_ds<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
+    if (e != cudaSuccess) return e;
+    integral_kernel_ds<LA, LB><<<grid, kIntThreads, kSmem64, st>>>(a);
   } else {
     cudaError_t e =
         cudaFuncSetAttribute(integral_kernel<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
@@ -461,9 +619,10 @@ int ctas_for(K kernel, size_t smem, int num_sms) {
 }
 
 template <int LA, int LB>
-int max_ctas(bool f32, int num_sms) {
-  return f32 ? ctas_for(integral_kernel_f32<LA, LB>, kSmem32, num_sms)
-             : ctas_for(integral_kernel<LA, LB>, kSmem64, num_sms);
+int max_ctas(bool f32, bool ds, int num_sms) {
+  return f32  ? ctas_for(integral_kernel_f32<LA, LB>, kSmem32, num_sms)
+         : ds ? ctas_for(integral_kernel_ds<LA, LB>, kSmem64, num_sms)
+              : ctas_for(integral_kernel<LA, LB>, kSmem64, num_sms);
 }
 
 }  // namespace
@@ -482,15 +641,15 @@ cudaError_t launch_integrals(cudaStream_t st, int list, const IntegralArgs& a, i
   return cudaErrorInvalidValue;
 }
 
-int integral_max_ctas(int list, int num_sms) {
+int integral_max_ctas(int list, int num_sms, bool ds) {
   const bool f32 = list >= kNumClasses;
   switch (list % kNumClasses) {
-    case 0: return max_ctas<0, 0>(f32, num_sms);
-    case 1: return max_ctas<1, 0>(f32, num_sms);
-    case 2: return max_ctas<1, 1>(f32, num_sms);
-    case 3: return max_ctas<2, 0>(f32, num_sms);
-    case 4: return max_ctas<2, 1>(f32, num_sms);
-    case 5: return max_ctas<2, 2>(f32, num_sms);
+    case 0: return max_ctas<0, 0>(f32, ds, num_sms);
+    case 1: return max_ctas<1, 0>(f32, ds, num_sms);
+    case 2: return max_ctas<1, 1>(f32, ds, num_sms);
+    case 3: return max_ctas<2, 0>(f32, ds, num_sms);
+    case 4: return max_ctas<2, 1>(f32, ds, num_sms);
+    case 5: return max_ctas<2, 2>(f32, ds, num_sms);
   }
   return num_sms;
 }

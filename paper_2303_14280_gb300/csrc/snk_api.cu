@@ -63,7 +63,7 @@ struct snk_ctx {
   // geometry (device)
   DevBuf<int> l, poff, nprim, foff, fshell, bshell, bshell_col, xfunc;
   DevBuf<double> center, exps, d, fcomp, xyz, w, boys, bound, qbound, bcenter, bradius, phit_f, phit_b;
-  DevBuf<float> boys_f;
+  DevBuf<float> boys_f, boys_ds, prims_ds;  // ds: (hi, lo) float pairs
   DevBuf<PairHdr> pairs;
   DevBuf<PrimPair> prims;
   DevBuf<MolDesc> mols;
@@ -78,6 +78,7 @@ struct snk_ctx {
   // density-dependent state
   bool have_density = false;
   DevBuf<double> P, ft, sym, Khat, K;
+  DevBuf<float2> P2;  // (hi, lo) pairs of P for the double-FP32 GEMM
   DevBuf<int> counts, list, sfunc, colmap, tickets;
   DevBuf<long long> ppcounts;
   DevBuf<unsigned char> sflag;
@@ -93,7 +94,7 @@ struct snk_ctx {
 
   struct Chunk {
     int b0 = 0, b1 = 0;
-    int64_t bytes = 0, goff = 0, gbytes = 0, g32off = 0, g32n = 0;
+    int64_t bytes = 0, xn = 0, goff = 0, gbytes = 0, g32off = 0, g32n = 0;
     int max_ldq = 0, max_nS = 0, max_nB = 0, max_nBshell = 0;
     int64_t tile_off[kNumLists] = {0}, tile_n[kNumLists] = {0};
   };
@@ -429,6 +430,7 @@ int screen_and_plan(snk_ctx* c) {
     }
     ch.b1 = j;
     int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0, g32cur = fo;
+    ch.xn = xo;
     ch.goff = gcur;
     ch.gbytes = fo * 8;
     ch.g32off = g32cur;
@@ -464,6 +466,7 @@ int screen_and_plan(snk_ctx* c) {
   SNK_CK(c, upload(c->tiles, htiles, st));
   SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
   SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(s.packed, 1)));
+  if (mixed && c->opt.gemm == SNK_GEMM_DF32) SNK_CK(c, c->P2.ensure((size_t)std::max<int64_t>(s.packed, 1)));
   SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
@@ -510,6 +513,10 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.boys_f = c->boys_f.p;
   a.ws32 = c->ws32.p;
   a.bcenter = c->bcenter.p;
+  a.boys_ds = reinterpret_cast<const float2*>(c->boys_ds.p);
+  a.prims_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals)
+                   ? reinterpret_cast<const float2*>(c->prims_ds.p)
+                   : nullptr;
   return a;
 }
 
@@ -518,10 +525,17 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
 int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   Setup& s = c->s;
   const bool mixed = c->opt.precision == SNK_PREC_MIXED;
+  const bool df32 = mixed && c->opt.gemm == SNK_GEMM_DF32;
+  const int fmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 1)) ? 1 : 0;
+  const int kmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 2)) ? 1 : 0;
   int ev = 0;
   c->launches_build = 0;
   if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
   SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)std::max<int64_t>(s.packed, 1), st));
+  if (df32) {  // P2 is allocated with the density (no allocation inside a graph capture)
+    SNK_CK(c, launch_split_df32_copy(st, c->P.p, s.packed, c->P2.p));
+    ++c->launches_build;
+  }
   SNK_CK(c, cudaMemsetAsync(c->tickets.p, 0, sizeof(int) * c->tickets.n, st));
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const auto& ch = c->chunks[ci];
@@ -531,10 +545,14 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
     ++c->launches_build;
+    if (df32) {  // X_j becomes (hi, lo) float pairs; both GEMMs read it so
+      SNK_CK(c, launch_split_df32(st, c->ws.p, ch.xn));
+      ++c->launches_build;
+    }
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     // F_j = X_j P (w and component factors folded in), Eq. (batch_local_exx)
-    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
-                           c->ws.p, mixed ? c->ws32.p : nullptr, mixed && (c->opt.tensor_gemms & 1)));
+    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->P2.p, c->xfunc.p, c->sfunc.p, c->fcomp.p,
+                           c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode));
     ++c->launches_build;
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
     if (mixed) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
@@ -554,8 +572,11 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
       ++c->launches_build;
     }
-    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p,
-                           mixed && (c->opt.tensor_gemms & 2)));
+    if (df32) {
+      SNK_CK(c, launch_split_df32(st, c->ws.p + ch.goff, ch.gbytes / 8));
+      ++c->launches_build;
+    }
+    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p, kmode));
     ++c->launches_build;
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
   }
@@ -731,6 +752,10 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   else
     snk_options_default(&c->opt);
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
+  if (c->opt.gemm < 0 || c->opt.gemm > 1 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
+      (c->opt.gemm == SNK_GEMM_DF32 && c->opt.tensor_gemms != 0) || c->opt.ds_integrals < 0 ||
+      c->opt.ds_integrals > 1)
+    return SNK_ERR_INVALID_ARG;
   for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
   int rc = build_setup(n_mol, bases, grids, &c->opt, &c->s, &c->err);
   if (rc != SNK_OK) return rc;
@@ -802,6 +827,19 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
          SNK_CK(cp, upload(cp->bcenter, s.bcenter, st));
          SNK_CK(cp, upload(cp->bradius, s.bradius, st));
          SNK_CK(cp, upload(cp->boys_f, s.boys_f, st));
+         if (cp->opt.precision == SNK_PREC_MIXED && cp->opt.ds_integrals) {
+           std::vector<float> pds(s.prims.size() * 24);
+           for (size_t q = 0; q < s.prims.size(); ++q) {
+             const double* v = reinterpret_cast<const double*>(&s.prims[q]);
+             for (int m = 0; m < 12; ++m) {
+               const float h = (float)v[m];
+               pds[q * 24 + 2 * m] = h;
+               pds[q * 24 + 2 * m + 1] = (float)(v[m] - (double)h);
+             }
+           }
+           SNK_CK(cp, upload(cp->prims_ds, pds, st));
+           SNK_CK(cp, upload(cp->boys_ds, s.boys_ds, st));
+         }
          SNK_CK(cp, upload(cp->xyz, s.xyz, st));
          SNK_CK(cp, upload(cp->w, s.w, st));
          SNK_CK(cp, upload(cp->bshell, s.bshell, st));
@@ -814,7 +852,8 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
        }()) != SNK_OK)
     return rc;
   if ((rc = geometry_screen(cp)) != SNK_OK) return rc;
-  for (int k = 0; k < kNumLists; ++k) cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms);
+  const bool ds = cp->opt.precision == SNK_PREC_MIXED && cp->opt.ds_integrals;
+  for (int k = 0; k < kNumLists; ++k) cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms, ds);
   std::memset(&cp->st, 0, sizeof(cp->st));
   cp->st.n_points = s.npts;
   cp->st.n_batches = cp->nbatch;
@@ -842,6 +881,8 @@ void snk_options_default(snk_options* o) {
   o->workspace_bytes = 0;
   o->distance_bound = 1;
   o->tensor_gemms = 0;
+  o->gemm = SNK_GEMM_FP64;
+  o->ds_integrals = 0;
   o->graph = 0;
   o->learned_skip = -11.0;
 }
@@ -1203,8 +1244,8 @@ int learn_collect(snk_ctx* c, int stride, int64_t cap, float* feat, float* lab, 
     const BatchDesc* db = c->batch.p + ch.b0;
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
-    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->xfunc.p, c->sfunc.p, c->fcomp.p, c->w.p,
-                           c->ws.p, nullptr, false));
+    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nullptr, c->xfunc.p, c->sfunc.p, c->fcomp.p,
+                           c->w.p, c->ws.p, nullptr, 0));
     SNK_CK(c, launch_xmax(st, db, nbc, c->ws.p, dxmax.p));
     for (int k = 0; k < kNumLists; ++k) {
       std::vector<Tile> ht;

@@ -149,6 +149,7 @@ struct Setup {
 
   std::vector<double> boys;           // (kBoysLMax+1) x kBoysRows x kBoysCols
   std::vector<float> boys_f;          // (kBoysLMax+1) x kBoysRowsF x kBoysColsF
+  std::vector<float> boys_ds;         // (hi, lo) pairs: (kBoysLMax+1) x kBoysRows x kBoysCols x 2
 };
 
 // Validates and normalises the molecules' bases and grids; returns an
@@ -208,11 +209,16 @@ cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list);
 // P, Khat and K below are the packed molecule blocks (BatchDesc::pk_off,
 // MolDesc::pk_off); xfunc / sfunc hold molecule-local function indices.
+// mode: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32 (X, G and P2 then
+// hold (hi, lo) float pairs in place of the doubles, see launch_split_df32).
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
-                         const double* P, const int* xfunc, const int* sfunc, const double* fcomp,
-                         const double* w, double* ws, float* ws32, bool tensor);
+                         const double* P, const float2* P2, const int* xfunc, const int* sfunc,
+                         const double* fcomp, const double* w, double* ws, float* ws32, int mode);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, bool tensor);
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode);
+// In place, each double of buf[0, n) becomes the float pair (fl32(v), fl32(v - fl32(v))).
+cudaError_t launch_split_df32(cudaStream_t st, double* buf, int64_t n);
+cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n, float2* dst);
 cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* Khat,
                           const double* fcomp, double* K);
 cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* P,
@@ -234,10 +240,14 @@ struct IntegralArgs {
   const float* boys_f;
   float* ws32;
   const double* bcenter;
+  // mixed form with double-FP32 high lists: non-null prims_ds selects
+  // integral_kernel_ds for the FP64 lists
+  const float2* boys_ds;   // (hi, lo) Boys table, nodes rounded to ds values
+  const float2* prims_ds;  // 12 (hi, lo) pairs per primitive pair, PrimPair order
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
-int integral_max_ctas(int cls, int num_sms);
+int integral_max_ctas(int cls, int num_sms, bool ds);
 cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const PrimPair* prims,
                            const double* boys, int64_t n, const double* xyz, double* xi);
 cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, const double* T,

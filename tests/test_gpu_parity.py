@@ -207,3 +207,68 @@ def test_mixed_precision_form(snk):
     Kt, st = _gpu_K(snk, p, batch_max=300, precision="mixed", tensor_gemms=3)
     assert np.max(np.abs(Kt - Kref)) <= 1e-4
     assert np.max(np.abs(Kt - Kt.T)) == 0.0
+
+
+def test_double_fp32_gemms(snk):
+    """The double-FP32 GEMMs (hi + lo float pairs, TwoSum accumulation) keep
+    the FP64 build's parity: with every pair in FP64 the only change from the
+    plain build is the arithmetic of F = X P and Kt = G^T X (~2^-46 relative)."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    K64, _ = _gpu_K(snk, p, batch_max=300)
+    Kd, sd = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=0.0, gemm="df32")
+    assert sd["pairs_kept_fp32"] == 0
+    assert np.max(np.abs(Kd - Kref)) <= TOL_K
+    assert np.max(np.abs(Kd - K64)) <= 1e-12
+    assert np.max(np.abs(Kd - Kd.T)) == 0.0
+    # ragged chunks: the in-place split covers each chunk's X and G exactly
+    Kc, sc = _gpu_K(snk, p, batch_max=97, precision="mixed", fp32_bound=0.0, gemm="df32", workspace_bytes=1 << 20)
+    assert sc["n_chunks"] > 1
+    assert np.max(np.abs(Kc - Kref)) <= TOL_K
+    # with the FP32 pairs of the mixed form
+    Km, sm = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e-3, gemm="df32")
+    assert sm["pairs_kept_fp32"] > 0
+    assert np.max(np.abs(Km - Kref)) <= 1e-8
+    # plain precision ignores the GEMM mode; combining it with tensor_gemms is rejected
+    Kp, _ = _gpu_K(snk, p, batch_max=300, gemm="df32")
+    assert np.max(np.abs(Kp - K64)) <= 1e-15       # FP64 atomics: summation order only
+    with pytest.raises(snk.SnkError) as e:
+        snk.Engine(p.basis, p.grid, precision="mixed", gemm="df32", tensor_gemms=1)
+    assert e.value.status == -1
+    # captured in a CUDA graph and replayed
+    eng = snk.Engine(p.basis, p.grid, batch_max=300, precision="mixed", fp32_bound=1e-3, gemm="df32", graph=1)
+    eng.set_density(p.P)
+    Kg1 = eng.build_K()
+    Kg2 = eng.build_K()
+    eng.close()
+    # FP32 atomics into G32 make the FP32 pairs' sums order-dependent: ~1e-11 run to run
+    assert np.max(np.abs(Kg1 - Km)) <= 1e-10 and np.max(np.abs(Kg2 - Km)) <= 1e-10
+
+
+def test_double_fp32_integrals(snk, chain4):
+    """The high lists of the mixed form in double-FP32 arithmetic (Boys seeds,
+    VRR, HRR and contraction on hi + lo float pairs): with every pair in that
+    tier K keeps the FP64 build's parity with the oracle."""
+    Kref = oracle.snk_K(chain4.basis, chain4.grid, chain4.P)
+    K, st = _gpu_K(snk, chain4, screen="none", precision="mixed", fp32_bound=0.0, ds_integrals=1)
+    assert st["pairs_kept_fp32"] == 0
+    assert np.max(np.abs(K - Kref)) <= TOL_K
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    K64, _ = _gpu_K(snk, p, batch_max=300)
+    Kd, _ = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=0.0, ds_integrals=1)
+    assert np.max(np.abs(Kd - Kref)) <= TOL_K
+    assert np.max(np.abs(Kd - K64)) <= 1e-11
+    # the mixed form's three tiers: FP32 below 1e-3, ds above, ds GEMMs; graph replay
+    Km, sm = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="df32")
+    assert sm["pairs_kept_fp32"] > 0
+    assert np.max(np.abs(Km - Kref)) <= 1e-8
+    eng = snk.Engine(p.basis, p.grid, batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1,
+                     gemm="df32", graph=1)
+    eng.set_density(p.P)
+    eng.build_K()
+    Kg = eng.build_K()
+    eng.close()
+    assert np.max(np.abs(Kg - Km)) <= 1e-10         # FP32 atomics: order-dependent at ~1e-11
+    with pytest.raises(snk.SnkError):
+        snk.Engine(p.basis, p.grid, precision="mixed", ds_integrals=2)
