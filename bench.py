@@ -14,7 +14,9 @@ Forms:
           weights and calibrated threshold); pairs whose sn-LinK estimate is
           below 3e-4 run their integrals in FP32, the rest in double-FP32 (hi +
           lo float pairs, ~1e-14 relative); F = X P and Kt = G^T X in
-          double-FP32 arithmetic; G and K accumulated in FP64
+          double-FP32 arithmetic for the columns of shells in double-FP32
+          pairs and as split-TF32 tensor-core products for the rest; G and K
+          accumulated in FP64
   (batch64: the 64 molecules in one handle, FP64, CUDA graph, autotuned tiles,
    against 64 separate plain builds)
 
@@ -51,7 +53,7 @@ FP64_PEAK = 1.25
 FP32_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12
 DF32_OPS_PER_MAC = 12      # FP32 instructions per double-FP32 multiply-add
 PLAIN = dict()
-CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="df32", ds_integrals=1)
+CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1)
 GOLDEN = {"cluster96": os.path.join(ROOT, "tests", "golden", "cluster96_K_entries.txt"),
           "cluster256": os.path.join(ROOT, "tests", "golden", "cluster256_K_entries.txt")}
 
@@ -239,7 +241,10 @@ class Runner:
             self.P = [torch.from_numpy(p.P).to(dev) for p in probs] if len(self.engs) > 1 else \
                 [torch.from_numpy(probs[0].P).to(dev)]
         self.K = [torch.empty_like(x) for x in self.P]
-        self.runs = self.engs[0].autotune() if batched else None
+        self.runs = None
+        if batched:                           # the autotuner times builds of the loaded density
+            self.engs[0].set_density(self.P[0])
+            self.runs = self.engs[0].autotune()
 
     def step(self):
         for e, P, K in zip(self.engs, self.P, self.K):
@@ -308,7 +313,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["cluster96", "cluster256", "cluster512", "batch64"])
+    ap.add_argument("--workload", default=WORKLOAD,  # cluster24: a small case of cluster96's shape for profiles
+                    choices=["cluster24", "cluster96", "cluster256", "cluster512", "batch64"])
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -348,7 +354,8 @@ def main():
     else:
         chosen_opts = dict(CHOSEN)
         form = ("mixed: rigorous sn-LinK at 1e-10, FP32 integrals for pairs with estimate < 3e-4, double-FP32 "
-                "integrals otherwise, double-FP32 GEMMs, FP64 G and K accumulation")
+                "integrals otherwise, GEMMs in double-FP32 for those pairs' shells and split-TF32 tensor-core "
+                "products for the rest, FP64 G and K accumulation")
         if not args.no_learned and os.path.exists(snk.SCREEN_WEIGHTS):
             learned, thr, _ = snk.trained_screen()
             chosen_opts.update(screen="learned", learned_skip=thr)
@@ -418,9 +425,9 @@ def main():
     gms = acc["ms_fgemm"] + acc["ms_kgemm"]
     if gms > 0:
         a = acc["gemm_flops"] / (gms * 1e-3) / 1e12
-        if not batch:     # double-FP32: 12 FP32 instructions per multiply-add
+        if not batch:     # double-FP32 (12 FP32 instructions per multiply-add) and split-TF32 columns
             peak = FP32_PEAK / DF32_OPS_PER_MAC
-            kern["fgemm_kgemm_df32"] = {"ms_per_step": gms / n, "bound": "alu", "achieved": a, "peak": peak,
+            kern["fgemm_kgemm_split"] = {"ms_per_step": gms / n, "bound": "alu", "achieved": a, "peak": peak,
                                         "unit": "TFLOP/s (FP64-equivalent 2 flop per multiply-add)",
                                         "frac": a / peak}
         else:
@@ -451,6 +458,10 @@ def main():
         "phases_ms_per_step": {k: acc[k] / n for k in ("ms_screen", "ms_collocation", "ms_fgemm", "ms_integrals",
                                                          "ms_integrals_fp32", "ms_kgemm", "ms_finish")},
         "kernels": kern,
+        "integral_ms_by_class": {tier: dict(zip(["ss", "ps", "pp", "ds", "dp", "dd"],
+                                                [round(x, 2) for x in st_ch[0][key]]))
+                                 for tier, key in (("high", "ms_integrals_class"),
+                                                   ("fp32", "ms_integrals_class_fp32"))},
         "pairs_kept": sum(s["pairs_kept"] for s in st_ch),
         "pairs_kept_fp32": sum(s["pairs_kept_fp32"] for s in st_ch),
         "pairs_learned_skipped": sum(s["pairs_learned_skipped"] for s in st_ch),

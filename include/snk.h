@@ -83,7 +83,7 @@ typedef struct {
 
 typedef enum { SNK_PREC_FP64 = 0, SNK_PREC_MIXED = 1 } snk_precision;
 typedef enum { SNK_SCREEN_NONE = 0, SNK_SCREEN_LINK = 1, SNK_SCREEN_LEARNED = 2 } snk_screen_mode;
-typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1 } snk_gemm_mode;
+typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1, SNK_GEMM_SPLIT = 2 } snk_gemm_mode;
 
 typedef struct {
   double eps_basis;        /* epsilon_B of Eq. (basis_screen); <= 0 keeps all   */
@@ -107,11 +107,15 @@ typedef struct {
                               replay it; phase times are then not reported      */
   double learned_skip;     /* learned screen: skip a block whose predicted log10
                               contribution to K is below this (default -11)     */
-  int32_t gemm;            /* mixed form: SNK_GEMM_FP64 (default) or SNK_GEMM_DF32,
+  int32_t gemm;            /* mixed form: SNK_GEMM_FP64 (default); SNK_GEMM_DF32,
                               F = X P and Kt = G^T X in double-FP32 arithmetic on the
                               FP32 pipe (operands as hi + lo float pairs, error-free
-                              TwoSum accumulation, ~2^-46 relative); not combined
-                              with tensor_gemms (SNK_ERR_INVALID_ARG)            */
+                              TwoSum accumulation, ~2^-46 relative); SNK_GEMM_SPLIT,
+                              double-FP32 for the F columns and G rows of shells
+                              in a batch's FP64-tier pairs and split-TF32 tensor-core
+                              products (FP32 partial sums of 64 terms folded into
+                              double-FP32) for the shells only FP32-tier pairs use;
+                              not combined with tensor_gemms (SNK_ERR_INVALID_ARG) */
   int32_t ds_integrals;    /* mixed form: 1 runs the integrals of the pairs above
                               fp32_bound in double-FP32 arithmetic (hi + lo float
                               pairs on the FP32 pipe, ~1e-14 relative) instead of
@@ -141,7 +145,9 @@ typedef struct {
   double flops_fp32;           /* their algorithmic FP32 flops                       */
   double ms_integrals_fp32;    /* their kernel time                                  */
   int64_t pairs_learned_skipped; /* learned screen: kept by sn-LinK, skipped by the MLP */
-  double reserved_stats[7];
+  double gemm_flops_hi;        /* the part of gemm_flops on high-tier columns / rows
+                                  (SNK_GEMM_SPLIT; equal to gemm_flops otherwise)   */
+  double ms_integrals_class_fp32[6]; /* FP32-tier kernel time per class            */
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,

@@ -36,7 +36,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported input", -3: "density
           -4: "bad call order", -5: "out of memory", -6: "CUDA error", -7: "device wait timed out"}
 SCREEN = {"none": 0, "link": 1, "learned": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
-GEMM = {"fp64": 0, "df32": 1}
+GEMM = {"fp64": 0, "df32": 1, "split": 2}
 LISTS = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
 # every entry point declared in include/snk.h
@@ -87,7 +87,7 @@ class SnkStats(ctypes.Structure):
                 ("flops_class", ctypes.c_double * 6), ("pairs_kept_fp32", ctypes.c_int64),
                 ("integrals_fp32", ctypes.c_double), ("flops_fp32", ctypes.c_double),
                 ("ms_integrals_fp32", ctypes.c_double), ("pairs_learned_skipped", ctypes.c_int64),
-                ("reserved_stats", ctypes.c_double * 7)]
+                ("gemm_flops_hi", ctypes.c_double), ("ms_integrals_class_fp32", ctypes.c_double * 6)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)

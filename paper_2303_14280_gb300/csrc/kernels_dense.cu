@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "ds_arith.cuh"
 #include "snk_internal.h"
 
 namespace snk {
@@ -134,7 +135,11 @@ constexpr int TC_THREADS = 128, TC_M = 64, TC_N = 64, TC_K = 16, TC_PAD = 4;
 
 // C[m][n] = sum_k A(m,k) B(k,n) over the 64 x 64 tile at (m0, n0); four warps
 // in 2 x 2, each 32 x 32 = 2 x 4 m16n8k8 tiles; st(m, n, c) stores.
-template <class LA, class LB, class ST>
+// With CHUNKED, the FP32 accumulators are folded into double-FP32 sums every
+// kTcChunk k (and cleared), so FP32 rounding acts on 64-term partial sums only.
+constexpr int kTcChunk = 64;
+
+template <bool CHUNKED = false, class LA, class LB, class ST>
 __device__ __forceinline__ void tf32x3_tile(int m0, int n0, int mdim, int ndim, int kdim, LA la, LB lb, ST st,
                                             bool a_k_fast, bool b_k_fast) {
   __shared__ uint32_t Ah[TC_M][TC_K + TC_PAD], Al[TC_M][TC_K + TC_PAD];
@@ -143,13 +148,28 @@ __device__ __forceinline__ void tf32x3_tile(int m0, int n0, int mdim, int ndim, 
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int g = lane >> 2, t = lane & 3;
   float acc[2][4][4];
+  ds sum[CHUNKED ? 2 : 1][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+      for (int r = 0; r < 4; ++r) {
+        acc[i][j][r] = 0.f;
+        if (CHUNKED) sum[i % (CHUNKED ? 2 : 1)][j][r] = ds_make(0.f, 0.f);
+      }
   for (int k0 = 0; k0 < kdim; k0 += TC_K) {
+    if (CHUNKED && k0 > 0 && k0 % kTcChunk == 0) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            sum[i % (CHUNKED ? 2 : 1)][j][r] += ds_make(acc[i][j][r], 0.f);
+            acc[i][j][r] = 0.f;
+          }
+    }
 #pragma unroll
     for (int r = 0; r < (TC_M * TC_K) / TC_THREADS; ++r) {
       const int e = tid + r * TC_THREADS;
@@ -223,7 +243,9 @@ __device__ __forceinline__ void tf32x3_tile(int m0, int n0, int mdim, int ndim, 
       for (int r = 0; r < 4; ++r) {
         const int m = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
         const int n = n0 + wn + j * 8 + 2 * t + (r & 1);
-        if (m < mdim && n < ndim) st(m, n, (double)acc[i][j][r]);
+        double v = (double)acc[i][j][r];
+        if (CHUNKED) v += ds_to(sum[i % (CHUNKED ? 2 : 1)][j][r]);
+        if (m < mdim && n < ndim) st(m, n, v);
       }
 }
 
@@ -505,11 +527,13 @@ __device__ __forceinline__ int classify_pair(const ScreenArgs& a, const BatchDes
 // pairs of the batch's molecule only.
 __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, int* __restrict__ counts,
                                                                  long long* __restrict__ ppcounts,
-                                                                 unsigned char* __restrict__ sflag) {
+                                                                 unsigned char* __restrict__ sflag,
+                                                                 int64_t hflag_off) {
   const int j = blockIdx.x;
   const BatchDesc bd = a.batches[j];
   const MolDesc md = a.mols[bd.mol];
-  unsigned char* fl = sflag + bd.cm_off;
+  unsigned char* fl = sflag + bd.cm_off;           // shells of V_j
+  unsigned char* hl = sflag + hflag_off + bd.cm_off;  // shells of V_j's FP64 (high-tier) pairs
   __shared__ int s_cnt[kNumLists];
   __shared__ unsigned long long s_pp[kNumLists];
   if (threadIdx.x < kNumLists) {
@@ -527,6 +551,10 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
         fl[h.sa - bd.ms0] = 1;
         fl[h.sb - bd.ms0] = 1;
         const int prec = li >= kNumClasses;
+        if (!prec) {
+          hl[h.sa - bd.ms0] = 1;
+          hl[h.sb - bd.ms0] = 1;
+        }
         n[prec] += 1;
         pp[prec] += (unsigned long long)h.pp_n;
       }
@@ -587,14 +615,25 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, c
 // F-hat_{s i} = w_i f_s sum_{nu in B_j} X_{nu i} P_{nu s}: the quadrature weight
 // and the Cartesian component factor of the column are folded into F.  In the
 // mixed form an FP32 copy is written for the FP32 pairs.
-template <int MODE>  // MODE: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32
-__global__ void __launch_bounds__(MODE == 1 ? TC_THREADS : GEMM_THREADS, MODE == 2 ? 2 : 3)
+// Column ranges of a GEMM part: 0 all of S_j, 1 the high-tier columns
+// [0, nS_hi), 2 the low-tier columns [nS_hi, nS).
+__device__ __forceinline__ void part_range(const BatchDesc& bd, int part, int& lo, int& hi) {
+  lo = part == 2 ? bd.nS_hi : 0;
+  hi = part == 1 ? bd.nS_hi : bd.nS;
+}
+
+// MODE: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32 on (hi, lo) operands,
+// 3 split-TF32 on the hi floats of (hi, lo) operands with chunked ds accumulation
+template <int MODE>
+__global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THREADS, MODE >= 2 ? 2 : 3)
     fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P, const float2* __restrict__ P2,
                  const int* __restrict__ xfunc, const int* __restrict__ sfunc, const double* __restrict__ fcomp,
-                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32) {
+                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32, int part) {
   const BatchDesc bd = batches[blockIdx.z];
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-  if (m0 >= bd.ldq || n0 >= bd.nS) return;
+  int c0, c1;
+  part_range(bd, part, c0, c1);
+  const int m0 = blockIdx.x * TM, n0 = c0 + blockIdx.y * TN;
+  if (m0 >= bd.ldq || n0 >= c1) return;
   double* F = ws + bd.foff;
   float* F32 = ws32 ? ws32 + bd.foff32 : nullptr;
   const int* xf = xfunc + bd.xfunc_off;
@@ -606,52 +645,91 @@ __global__ void __launch_bounds__(MODE == 1 ? TC_THREADS : GEMM_THREADS, MODE ==
     F[(int64_t)n * bd.ldq + m] = v;
     if (F32) F32[(int64_t)n * bd.ldq + m] = (float)v;
   };
-  if (MODE == 2) {
+  if (MODE == 2 || MODE == 3) {
     const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
     const float2* Pm2 = P2 + bd.pk_off;
     auto la = [&](int m, int k) { return X2[(int64_t)k * bd.ldq + m]; };
     auto lb = [&](int k, int n) { return Pm2[(int64_t)xf[k] * bd.nfm + sf[n]]; };
-    df32_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+    if (MODE == 2) {
+      df32_tile(m0, n0, bd.ldq, c1, bd.nB, la, lb, st, false, false);
+    } else {
+      auto la1 = [&](int m, int k) { return la(m, k).x; };
+      auto lb1 = [&](int k, int n) { return lb(k, n).x; };
+      tf32x3_tile<true>(m0, n0, bd.ldq, c1, bd.nB, la1, lb1, st, false, false);
+    }
   } else {
     const double* X = ws + bd.xoff;
     const double* Pm = P + bd.pk_off;
     auto la = [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; };
     auto lb = [&](int k, int n) { return Pm[(int64_t)xf[k] * bd.nfm + sf[n]]; };
     if (MODE == 1)
-      tf32x3_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+      tf32x3_tile(m0, n0, bd.ldq, c1, bd.nB, la, lb, st, false, false);
     else
-      gemm_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
+      gemm_tile(m0, n0, bd.ldq, c1, bd.nB, la, lb, st, false, false);
   }
 }
 
 // Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the molecule's block
 // of the packed accumulator (several batches add to the same entries).
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 1 ? TC_THREADS : GEMM_THREADS, MODE == 2 ? 2 : 3)
+__global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THREADS, MODE >= 2 ? 2 : 3)
     kgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc, const int* __restrict__ sfunc,
-                 const double* __restrict__ ws, double* __restrict__ Khat) {
+                 const double* __restrict__ ws, double* __restrict__ Khat, int part) {
   const BatchDesc bd = batches[blockIdx.z];
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-  if (m0 >= bd.nS || n0 >= bd.nB) return;
+  int r0, r1;
+  part_range(bd, part, r0, r1);
+  const int m0 = r0 + blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= r1 || n0 >= bd.nB) return;
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   double* Km = Khat + bd.pk_off;
   auto st = [&](int m, int n, double c) { atomicAdd(&Km[(int64_t)sf[m] * bd.nfm + xf[n]], c); };
-  if (MODE == 2) {
+  if (MODE == 2 || MODE == 3) {
     const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
     const float2* G2 = reinterpret_cast<const float2*>(ws + bd.goff);
     auto la = [&](int m, int k) { return G2[(int64_t)m * bd.ldq + k]; };
     auto lb = [&](int k, int n) { return X2[(int64_t)n * bd.ldq + k]; };
-    df32_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+    if (MODE == 2) {
+      df32_tile(m0, n0, r1, bd.nB, bd.q, la, lb, st, true, true);
+    } else {
+      auto la1 = [&](int m, int k) { return la(m, k).x; };
+      auto lb1 = [&](int k, int n) { return lb(k, n).x; };
+      tf32x3_tile<true>(m0, n0, r1, bd.nB, bd.q, la1, lb1, st, true, true);
+    }
   } else {
     const double* X = ws + bd.xoff;
     const double* G = ws + bd.goff;
     auto la = [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; };
     auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
     if (MODE == 1)
-      tf32x3_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+      tf32x3_tile(m0, n0, r1, bd.nB, bd.q, la, lb, st, true, true);
     else
-      gemm_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
+      gemm_tile(m0, n0, r1, bd.nB, bd.q, la, lb, st, true, true);
+  }
+}
+
+// Tiles of list k of batch j (one block per (batch, list)).
+__global__ void gen_tiles_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ counts,
+                                 const int64_t* __restrict__ list_off, const int64_t* __restrict__ tstart,
+                                 RunLengths runs, Tile* __restrict__ tiles) {
+  const int j = blockIdx.x, k = blockIdx.y;
+  const int64_t e = (int64_t)j * kNumLists + k;
+  const int n = counts[e];
+  if (n == 0) return;
+  const int run = runs.run[k];
+  const int q = batches[j].q;
+  const int nslab = (q + kPointTile - 1) / kPointTile;
+  const int nrun = (n + run - 1) / run;
+  const int base = (int)list_off[e];
+  Tile* out = tiles + tstart[e];
+  for (int u = threadIdx.x; u < nrun * nslab; u += blockDim.x) {
+    const int r = u / nslab, sl = u - r * nslab;
+    Tile t;
+    t.batch = j;
+    t.k0 = base + r * run;
+    t.k1 = base + min(n, (r + 1) * run);
+    t.i0 = sl * kPointTile;
+    out[u] = t;
   }
 }
 
@@ -742,9 +820,9 @@ cudaError_t launch_ftilde(cudaStream_t st, const MolDesc* mols, int n_mol, int m
 }
 
 cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, int* counts, long long* ppcounts,
-                              unsigned char* sflag) {
+                              unsigned char* sflag, int64_t hflag_off) {
   if (nbatch == 0) return cudaSuccess;
-  pair_count_kernel<<<nbatch, SCR_THREADS, 0, st>>>(a, counts, ppcounts, sflag);
+  pair_count_kernel<<<nbatch, SCR_THREADS, 0, st>>>(a, counts, ppcounts, sflag, hflag_off);
   return cudaGetLastError();
 }
 
@@ -756,28 +834,35 @@ cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc, const double* fcomp,
-                         const double* w, double* ws, float* ws32, int mode) {
+                         const double* w, double* ws, float* ws32, int mode, int part) {
   if (nbatch == 0 || max_ldq == 0 || max_nS == 0) return cudaSuccess;
   dim3 grid((max_ldq + TM - 1) / TM, (max_nS + TN - 1) / TN, nbatch);
-  if (mode == 1)
-    fgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32);
-  else if (mode == 2)
-    fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32);
-  else
-    fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32);
+  switch (mode) {
+    case 1: fgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part); break;
+    case 2: fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part); break;
+    case 3: fgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part); break;
+    default: fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode) {
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part) {
   if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
   dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
-  if (mode == 1)
-    kgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
-  else if (mode == 2)
-    kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
-  else
-    kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat);
+  switch (mode) {
+    case 1: kgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part); break;
+    case 2: kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part); break;
+    case 3: kgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part); break;
+    default: kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batches, const int* counts,
+                             const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles) {
+  if (nbatch == 0) return cudaSuccess;
+  gen_tiles_kernel<<<dim3(nbatch, kNumLists), 256, 0, st>>>(batches, counts, list_off, tstart, runs, tiles);
   return cudaGetLastError();
 }
 

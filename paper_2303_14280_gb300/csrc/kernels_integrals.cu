@@ -201,25 +201,18 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
 }
 
 // Primitive pair in FP32, its product centre relative to the batch centre.
-struct PrimPairF {
-  float zeta, Rx, Ry, Rz, PAx, PAy, PAz, pref, pref_far, k1, k2, k3;
-};
-
-// Same decomposition as integral_kernel, FP32 arithmetic: points and product
-// centres are taken relative to the batch centre (differences formed in FP64
-// once per tile) so that T = zeta |P - r|^2 keeps FP32 relative accuracy; F is
-// read from the FP32 copy and G accumulates into the FP32 buffer, which the
-// driver adds into the FP64 G before the K product.
+// The FP32 lists of the mixed form.  Primitive-pair data come as one 64-byte
+// FP32 record per primitive pair (four broadcast 16-byte loads, no staging and
+// no barrier per pair) with the product centre split into hi + lo floats, and
+// P - r_i is formed as (P_hi - r_hi) + (P_lo - r_lo) so that it is accurate to
+// FP32 relative to |P - r_i| however far the molecule sits from the origin.
 template <int LA, int LB>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
-  extern __shared__ float s_f[];
-  float* s_tab = s_f;
-  PrimPairF* s_pp = reinterpret_cast<PrimPairF*>(s_f + kBoysRowsF * kBoysColsF);
+  extern __shared__ float s_tabf[];
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
-  for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tab[e] = gtab[e];
-  __shared__ float s_ab[3];
+  for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
   __shared__ int s_tile;
   __syncthreads();
   for (;;) {
@@ -231,14 +224,9 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     const Tile tile = a.tiles[t];
     const BatchDesc bd = a.batches[tile.batch];
     const int i = tile.i0 + threadIdx.x;
-    const bool active = i < bd.q;
-    const double ox = a.bcenter[3 * tile.batch], oy = a.bcenter[3 * tile.batch + 1], oz = a.bcenter[3 * tile.batch + 2];
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    if (active) {
-      cx = (float)(a.xyz[3 * (bd.p0 + i)] - ox);
-      cy = (float)(a.xyz[3 * (bd.p0 + i) + 1] - oy);
-      cz = (float)(a.xyz[3 * (bd.p0 + i) + 2] - oz);
-    }
+    if (i >= bd.q) continue;
+    const ds cx = ds_from(a.xyz[3 * (bd.p0 + i)]), cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]),
+             cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
     const int64_t ldq = bd.ldq;
     const float* F = a.ws32 + bd.foff32 + i;
     float* G = a.ws32 + bd.goff32 + i;
@@ -246,32 +234,8 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     float ga[NA], fa[NA];
     int cur = -1, cola = 0;
     for (int k = tile.k0; k < tile.k1; ++k) {
-      const PairHdr h = a.pairs[a.pairlist[k]];
-      __syncthreads();  // the previous pair's staged primitives are consumed
-      for (int q = threadIdx.x; q < h.pp_n; q += blockDim.x) {
-        const PrimPair pp = a.prims[h.pp_off + q];
-        PrimPairF f;
-        f.zeta = (float)pp.zeta;
-        f.Rx = (float)(pp.Px - ox);
-        f.Ry = (float)(pp.Py - oy);
-        f.Rz = (float)(pp.Pz - oz);
-        f.PAx = (float)pp.PAx;
-        f.PAy = (float)pp.PAy;
-        f.PAz = (float)pp.PAz;
-        f.pref = (float)pp.pref;
-        f.pref_far = (float)pp.pref_far;
-        f.k1 = (float)pp.k1;
-        f.k2 = (float)pp.k2;
-        f.k3 = (float)pp.k3;
-        s_pp[q] = f;
-      }
-      if (threadIdx.x == 0) {
-        s_ab[0] = (float)h.ABx;
-        s_ab[1] = (float)h.ABy;
-        s_ab[2] = (float)h.ABz;
-      }
-      __syncthreads();
-      if (!active) continue;
+      const int p = a.pairlist[k];
+      const PairHdr h = a.pairs[p];
       if (h.sa != cur) {
         if (cur >= 0) {
 #pragma unroll
@@ -294,15 +258,19 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
 #pragma unroll
       for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
       for (int q = 0; q < h.pp_n; ++q) {
-        const PrimPairF pp = s_pp[q];
-        const float PCx = pp.Rx - cx, PCy = pp.Ry - cy, PCz = pp.Rz - cz;
-        const float T = pp.zeta * fmaf(PCx, PCx, fmaf(PCy, PCy, PCz * PCz));
+        const float4* pp = a.prims_f32 + (size_t)(h.pp_off + q) * 4;
+        const float4 r0 = pp[0], r1 = pp[1], r2 = pp[2], r3 = pp[3];
+        const float PCx = (r0.y - cx.hi) + (r1.x - cx.lo);
+        const float PCy = (r0.z - cy.hi) + (r1.y - cy.lo);
+        const float PCz = (r0.w - cz.hi) + (r1.z - cz.lo);
+        const float T = r0.x * fmaf(PCx, PCx, fmaf(PCy, PCy, PCz * PCz));
         float S[C::L + 1];
-        boys_seeds_f32<C::L>(T, pp.pref, pp.pref_far, s_tab, S);
-        C::vrr(S, pp.PAx, pp.PAy, pp.PAz, PCx, PCy, PCz, pp.k1, pp.k2, pp.k3, acc);
+        boys_seeds_f32<C::L>(T, r1.w, r2.w, s_tabf, S);
+        C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
       }
+      const float2* ab = a.pair_ab + 4 * (size_t)p;
       float xi[NA * NB];
-      C::hrr(acc, s_ab[0], s_ab[1], s_ab[2], xi);
+      C::hrr(acc, ab[0].x, ab[1].x, ab[2].x, xi);
 #pragma unroll
       for (int u = 0; u < NA; ++u)
 #pragma unroll
@@ -317,7 +285,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         }
       }
     }
-    if (active && cur >= 0) {
+    if (cur >= 0) {
 #pragma unroll
       for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
     }
@@ -384,8 +352,9 @@ __device__ __forceinline__ void boys_seeds_ds(ds T, ds pref, ds pref_far, const 
 // Contracted Xi_ab of one pair at the point c in ds arithmetic; the primitive
 // pair data are the host-split (hi, lo) copies of PrimPair (12 pairs each).
 template <int LA, int LB>
-__device__ __forceinline__ void pair_xi_ds(const PairHdr& h, const float2* __restrict__ prims, const float2* tab,
-                                           ds cx, ds cy, ds cz, ds* xi) {
+__device__ __forceinline__ void pair_xi_ds(const PairHdr& h, const float2* __restrict__ prims,
+                                           const float2* __restrict__ ab, const float2* tab, ds cx, ds cy, ds cz,
+                                           ds* xi) {
   using C = OsClass<LA, LB>;
   ds acc[C::NACC];
 #pragma unroll
@@ -400,7 +369,7 @@ __device__ __forceinline__ void pair_xi_ds(const PairHdr& h, const float2* __res
     C::vrr(S, ds_ld(pp + 4), ds_ld(pp + 5), ds_ld(pp + 6), PCx, PCy, PCz, ds_ld(pp + 9), ds_ld(pp + 10),
            ds_ld(pp + 11), acc);
   }
-  C::hrr(acc, ds_from(h.ABx), ds_from(h.ABy), ds_from(h.ABz), xi);
+  C::hrr(acc, ds_ld(ab), ds_ld(ab + 1), ds_ld(ab + 2), xi);
 }
 
 // The FP64 lists of the mixed form in ds arithmetic: same tiles, tickets,
@@ -434,7 +403,8 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_ds(IntegralArgs a
     ds ga[NA], fa[NA];
     int cur = -1, cola = 0;
     for (int k = tile.k0; k < tile.k1; ++k) {
-      const PairHdr h = a.pairs[a.pairlist[k]];
+      const int p = a.pairlist[k];
+      const PairHdr h = a.pairs[p];
       if (h.sa != cur) {
         if (cur >= 0) {
 #pragma unroll
@@ -454,7 +424,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_ds(IntegralArgs a
 #pragma unroll
       for (int v = 0; v < NB; ++v) fb[v] = ds_from(F[(colb + v) * ldq]);
       ds xi[NA * NB];
-      pair_xi_ds<LA, LB>(h, a.prims_ds, s_tab2, cx, cy, cz, xi);
+      pair_xi_ds<LA, LB>(h, a.prims_ds, a.pair_ab + 4 * (size_t)p, s_tab2, cx, cy, cz, xi);
 #pragma unroll
       for (int u = 0; u < NA; ++u)
 #pragma unroll
@@ -584,7 +554,7 @@ __global__ void debug_boys_kernel(const double* boys, int64_t n, const double* T
 }
 
 constexpr size_t kSmem64 = sizeof(double) * kBoysRows * kBoysCols;
-constexpr size_t kSmem32 = sizeof(float) * kBoysRowsF * kBoysColsF + sizeof(PrimPairF) * 256;
+constexpr size_t kSmem32 = sizeof(float) * kBoysRowsF * kBoysColsF;
 
 // list < kNumClasses: FP64 kernel of that class; otherwise the FP32 kernel of
 // class list - kNumClasses.
@@ -595,7 +565,7 @@ cudaError_t launch_class(cudaStream_t st, bool f32, const IntegralArgs& a, int g
         cudaFuncSetAttribute(integral_kernel_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
     if (e != cudaSuccess) return e;
     integral_kernel_f32<LA, LB><<<grid, kIntThreads, kSmem32, st>>>(a);
-  } else if (a.prims_ds) {
+  } else if (a.hi_ds) {
     cudaError_t e =
         cudaFuncSetAttribute(integral_kernel_ds<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
     if (e != cudaSuccess) return e;

@@ -63,7 +63,7 @@ struct snk_ctx {
   // geometry (device)
   DevBuf<int> l, poff, nprim, foff, fshell, bshell, bshell_col, xfunc;
   DevBuf<double> center, exps, d, fcomp, xyz, w, boys, bound, qbound, bcenter, bradius, phit_f, phit_b;
-  DevBuf<float> boys_f, boys_ds, prims_ds;  // ds: (hi, lo) float pairs
+  DevBuf<float> boys_f, boys_ds, prims_ds, pair_ab, prims_f32;  // mixed form: FP32 and (hi, lo) copies
   DevBuf<PairHdr> pairs;
   DevBuf<PrimPair> prims;
   DevBuf<MolDesc> mols;
@@ -82,7 +82,7 @@ struct snk_ctx {
   DevBuf<int> counts, list, sfunc, colmap, tickets;
   DevBuf<long long> ppcounts;
   DevBuf<unsigned char> sflag;
-  DevBuf<int64_t> list_off;
+  DevBuf<int64_t> list_off, tstart;  // per (batch, list): first list entry, first tile
   DevBuf<BatchDesc> batch;
   DevBuf<Tile> tiles;
   DevBuf<double> ws;
@@ -236,37 +236,34 @@ int ensure_events(snk_ctx* c, size_t n) {
   return SNK_OK;
 }
 
-// Integral tiles per (chunk, list): (batch, run of pairs, 128-point slab),
-// larger tiles first so that the persistent CTAs finish together.
-void make_tiles(snk_ctx* c, std::vector<Tile>& htiles) {
-  htiles.clear();
+// Integral tiles (batch, run of pairs, 128-point slab) of every list of every
+// chunk, written on the device: the host only computes where each (batch,
+// list)'s tiles start (from the per-list counts it already holds), and
+// gen_tiles writes them.  Within a (chunk, list) the tiles go batch by batch,
+// a run's slabs consecutively; the persistent CTAs take them from a ticket.
+int make_tiles(snk_ctx* c, cudaStream_t st) {
   const auto& bd = c->hbatch;
+  const int nb = c->nbatch;
+  std::vector<int64_t> tstart((size_t)std::max(nb, 1) * kNumLists, 0);
+  int64_t tot = 0;
   for (auto& ch : c->chunks)
     for (int k = 0; k < kNumLists; ++k) {
-      ch.tile_off[k] = (int64_t)htiles.size();
-      size_t first = htiles.size();
+      ch.tile_off[k] = tot;
       const int run = c->run[k];
       for (int t = ch.b0; t < ch.b1; ++t) {
-        int64_t n = c->hcounts[(size_t)t * kNumLists + k];
-        int64_t base = c->hlist_off[(size_t)t * kNumLists + k];
-        for (int64_t k0 = 0; k0 < n; k0 += run)
-          for (int i0 = 0; i0 < bd[t].q; i0 += kPointTile) {
-            Tile tl;
-            tl.batch = t;
-            tl.k0 = (int)(base + k0);
-            tl.k1 = (int)(base + std::min<int64_t>(n, k0 + run));
-            tl.i0 = i0;
-            htiles.push_back(tl);
-          }
+        const int64_t n = c->hcounts[(size_t)t * kNumLists + k];
+        tstart[(size_t)t * kNumLists + k] = tot;
+        tot += (n + run - 1) / run * ((bd[t].q + kPointTile - 1) / kPointTile);
       }
-      std::stable_sort(htiles.begin() + first, htiles.end(), [&](const Tile& x, const Tile& y) {
-        int64_t cx = (int64_t)(x.k1 - x.k0) * std::min(kPointTile, bd[x.batch].q - x.i0);
-        int64_t cy = (int64_t)(y.k1 - y.k0) * std::min(kPointTile, bd[y.batch].q - y.i0);
-        return cx > cy;
-      });
-      ch.tile_n[k] = (int64_t)htiles.size() - ch.tile_off[k];
+      ch.tile_n[k] = tot - ch.tile_off[k];
     }
-  if (htiles.empty()) htiles.push_back(Tile{0, 0, 0, 0});
+  SNK_CK(c, c->tiles.ensure((size_t)std::max<int64_t>(tot, 1)));
+  SNK_CK(c, upload(c->tstart, tstart, st));
+  RunLengths rl;
+  for (int k = 0; k < kNumLists; ++k) rl.run[k] = c->run[k];
+  SNK_CK(c, launch_gen_tiles(st, nb, c->batch.p, c->counts.p, c->list_off.p, c->tstart.p, rl, c->tiles.p));
+  ++c->launches_density;
+  return SNK_OK;
 }
 
 // Density-dependent part of set_density once P is on the device.
@@ -296,9 +293,9 @@ int screen_and_plan(snk_ctx* c) {
   SNK_CK(c, c->ft.ensure(cmn));
   SNK_CK(c, c->counts.ensure((size_t)nbx * kNumLists));
   SNK_CK(c, c->ppcounts.ensure((size_t)nbx * kNumLists));
-  SNK_CK(c, c->sflag.ensure(cmn));
+  SNK_CK(c, c->sflag.ensure(2 * cmn));  // shells of V_j, then shells of its high-tier pairs
   SNK_CK(c, cudaMemsetAsync(c->ft.p, 0, sizeof(double) * cmn, st));
-  SNK_CK(c, cudaMemsetAsync(c->sflag.p, 0, cmn, st));
+  SNK_CK(c, cudaMemsetAsync(c->sflag.p, 0, 2 * cmn, st));
   const int screen = c->opt.screen == SNK_SCREEN_NONE ? SNK_SCREEN_NONE : SNK_SCREEN_LINK;
   // geometry descriptors for the screen kernels
   c->hbatch.assign(nbx, BatchDesc{});
@@ -326,15 +323,15 @@ int screen_and_plan(snk_ctx* c) {
   sa.eps_E = c->opt.eps_E;
   sa.eps_K = c->opt.eps_K;
   sa.fp32_bound = c->opt.fp32_bound;
-  SNK_CK(c, launch_pair_count(st, sa, nb, c->counts.p, c->ppcounts.p, c->sflag.p));
+  SNK_CK(c, launch_pair_count(st, sa, nb, c->counts.p, c->ppcounts.p, c->sflag.p, (int64_t)cmn));
   ++c->launches_density;
   c->hcounts.assign((size_t)nbx * kNumLists, 0);
   c->hpp.assign((size_t)nbx * kNumLists, 0);
-  std::vector<unsigned char> hflag(cmn);
+  std::vector<unsigned char> hflag(2 * cmn);
   SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumLists, cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaMemcpyAsync(c->hpp.data(), c->ppcounts.p, sizeof(long long) * nbx * kNumLists, cudaMemcpyDeviceToHost,
                             st));
-  SNK_CK(c, cudaMemcpyAsync(hflag.data(), c->sflag.p, cmn, cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(hflag.data(), c->sflag.p, 2 * cmn, cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
   // pair lists: offsets, then the deterministic compaction pass
@@ -373,7 +370,9 @@ int screen_and_plan(snk_ctx* c) {
     learned_skipped = tot - after;
   }
 
-  // shells of V_j -> F / G columns (molecule-local function indices)
+  // shells of V_j -> F / G columns (molecule-local function indices); with
+  // the split GEMMs the shells of high-tier pairs come first, [0, nS_hi)
+  const bool split = mixed && c->opt.gemm == SNK_GEMM_SPLIT;
   std::vector<int> hcolmap(cmn, -1), hsfunc;
   auto& bd = c->hbatch;
   c->chunks.clear();
@@ -382,22 +381,29 @@ int screen_and_plan(snk_ctx* c) {
     const Setup::Mol& m = s.mols[b.mol];
     b.sfunc_off = (int)hsfunc.size();
     int col = 0;
-    for (int a = 0; a < m.ns; ++a)
-      if (hflag[(size_t)b.cm_off + a]) {
+    for (int pass = split ? 0 : 1; pass < 2; ++pass) {
+      for (int a = 0; a < m.ns; ++a) {
+        const bool used = hflag[(size_t)b.cm_off + a] != 0;
+        const bool hi = hflag[cmn + (size_t)b.cm_off + a] != 0;
+        if (!used || (pass == 0 && !hi) || (pass == 1 && split && hi)) continue;
         hcolmap[(size_t)b.cm_off + a] = col;
         const int g = m.ms0 + a;
         for (int u = 0; u < ncart(s.l[g]); ++u) hsfunc.push_back(s.foff[g] - m.mf0 + u);
         col += ncart(s.l[g]);
       }
+      if (pass == 0) b.nS_hi = col;
+    }
     b.nS = col;
+    if (!split) b.nS_hi = col;
   }
   // counts for the statistics: integrals and algorithmic flops per list
   double per_prim[kNumClasses], per_pair[kNumClasses];
   for (int k = 0; k < kNumClasses; ++k) class_flops(k, &per_prim[k], &per_pair[k]);
-  double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0;
+  double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0, gflops_hi = 0.0;
   int64_t kept[2] = {0, 0}, pair_points = 0;
   for (int j = 0; j < nb; ++j) {
     gflops += 4.0 * bd[j].q * (double)bd[j].nB * bd[j].nS;
+    gflops_hi += 4.0 * bd[j].q * (double)bd[j].nB * bd[j].nS_hi;
     for (int k = 0; k < kNumLists; ++k) {
       const int cls = k % kNumClasses;
       const int la = cls >= 3 ? 2 : (cls >= 1 ? 1 : 0), lb = cls - la * (la + 1) / 2;
@@ -461,12 +467,10 @@ int screen_and_plan(snk_ctx* c) {
   if (mixed) SNK_CK(c, c->ws32.ensure((size_t)need32));
   SNK_CK(c, upload(c->batch, bd, st));
 
-  std::vector<Tile> htiles;
-  make_tiles(c, htiles);
-  SNK_CK(c, upload(c->tiles, htiles, st));
+  if (int rc = make_tiles(c, st)) return rc;
   SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
   SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(s.packed, 1)));
-  if (mixed && c->opt.gemm == SNK_GEMM_DF32) SNK_CK(c, c->P2.ensure((size_t)std::max<int64_t>(s.packed, 1)));
+  if (mixed && c->opt.gemm != SNK_GEMM_FP64) SNK_CK(c, c->P2.ensure((size_t)std::max<int64_t>(s.packed, 1)));
   SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
@@ -486,6 +490,7 @@ int screen_and_plan(snk_ctx* c) {
     S.flops_fp32 += lflops[k + kNumClasses];
   }
   S.gemm_flops = gflops;
+  S.gemm_flops_hi = gflops_hi;
   S.n_chunks = (int64_t)c->chunks.size();
   S.workspace_bytes = (int64_t)(c->ws.n * 8 + c->ws32.n * 4);
   float ms = 0.f;
@@ -514,9 +519,10 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.ws32 = c->ws32.p;
   a.bcenter = c->bcenter.p;
   a.boys_ds = reinterpret_cast<const float2*>(c->boys_ds.p);
-  a.prims_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals)
-                   ? reinterpret_cast<const float2*>(c->prims_ds.p)
-                   : nullptr;
+  a.prims_ds = reinterpret_cast<const float2*>(c->prims_ds.p);
+  a.pair_ab = reinterpret_cast<const float2*>(c->pair_ab.p);
+  a.prims_f32 = reinterpret_cast<const float4*>(c->prims_f32.p);
+  a.hi_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals) ? 1 : 0;
   return a;
 }
 
@@ -525,9 +531,11 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
 int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   Setup& s = c->s;
   const bool mixed = c->opt.precision == SNK_PREC_MIXED;
-  const bool df32 = mixed && c->opt.gemm == SNK_GEMM_DF32;
+  const bool split = mixed && c->opt.gemm == SNK_GEMM_SPLIT;
+  const bool df32 = mixed && (c->opt.gemm == SNK_GEMM_DF32 || split);
   const int fmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 1)) ? 1 : 0;
   const int kmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 2)) ? 1 : 0;
+  const int gpart = split ? 1 : 0;  // with split: df32 on the high-tier columns, then mode 3 on the rest
   int ev = 0;
   c->launches_build = 0;
   if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
@@ -552,8 +560,13 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     // F_j = X_j P (w and component factors folded in), Eq. (batch_local_exx)
     SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->P2.p, c->xfunc.p, c->sfunc.p, c->fcomp.p,
-                           c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode));
+                           c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode, gpart));
     ++c->launches_build;
+    if (split) {
+      SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->P2.p, c->xfunc.p, c->sfunc.p,
+                             c->fcomp.p, c->w.p, c->ws.p, c->ws32.p, 3, 2));
+      ++c->launches_build;
+    }
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
     if (mixed) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
@@ -576,8 +589,13 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       SNK_CK(c, launch_split_df32(st, c->ws.p + ch.goff, ch.gbytes / 8));
       ++c->launches_build;
     }
-    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p, kmode));
+    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p, kmode,
+                           gpart));
     ++c->launches_build;
+    if (split) {
+      SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p, 3, 2));
+      ++c->launches_build;
+    }
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
   }
   // K = (Kt + Kt^T) / 2 in every molecule block, Eq. (sn_k)
@@ -653,7 +671,7 @@ void collect_times(snk_ctx* c) {
   const int last = (int)c->chunks.size() * kPhaseEvents + 1;  // the event after the finish kernel
   if (cudaEventSynchronize(c->events[last]) != cudaSuccess) return;
   st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = st.ms_integrals_fp32 = 0.0;
-  for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = 0.0;
+  for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = st.ms_integrals_class_fp32[k] = 0.0;
   int ev = 0;
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const int e0 = ev;  // previous boundary
@@ -665,6 +683,7 @@ void collect_times(snk_ctx* c) {
         st.ms_integrals_class[k] += t;
         st.ms_integrals += t;
       } else {
+        st.ms_integrals_class_fp32[k - kNumClasses] += t;
         st.ms_integrals_fp32 += t;
       }
     }
@@ -697,16 +716,14 @@ int autotune(snk_ctx* c, int32_t* runs_out) {
   cudaEvent_t e0, e1;
   SNK_CK(c, cudaEventCreate(&e0));
   SNK_CK(c, cudaEventCreate(&e1));
-  std::vector<Tile> htiles;
   for (int k = 0; k < kNumLists; ++k) {
     if (c->chunks[ci].tile_n[k] == 0) continue;
     double best = 1e300;
     int best_run = c->run[k];
     for (int r : kRunCandidates) {
       c->run[k] = r;
-      make_tiles(c, htiles);
       if ((rc = [&]() -> int {
-             SNK_CK(c, upload(c->tiles, htiles, c->stream));
+             if (int e = make_tiles(c, c->stream)) return e;
              double t = 1e300;
              for (int rep = 0; rep < 2; ++rep) {
                IntegralArgs a = integral_args(c, ci, k);
@@ -733,8 +750,7 @@ int autotune(snk_ctx* c, int32_t* runs_out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != SNK_OK) return rc;
-  make_tiles(c, htiles);
-  SNK_CK(c, upload(c->tiles, htiles, c->stream));
+  if ((rc = make_tiles(c, c->stream)) != SNK_OK) return rc;
   SNK_CK(c, cudaStreamSynchronize(c->stream));
   c->graph_valid = false;
   if (runs_out)
@@ -752,8 +768,8 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   else
     snk_options_default(&c->opt);
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
-  if (c->opt.gemm < 0 || c->opt.gemm > 1 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
-      (c->opt.gemm == SNK_GEMM_DF32 && c->opt.tensor_gemms != 0) || c->opt.ds_integrals < 0 ||
+  if (c->opt.gemm < 0 || c->opt.gemm > 2 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
+      (c->opt.gemm != SNK_GEMM_FP64 && c->opt.tensor_gemms != 0) || c->opt.ds_integrals < 0 ||
       c->opt.ds_integrals > 1)
     return SNK_ERR_INVALID_ARG;
   for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
@@ -827,7 +843,17 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
          SNK_CK(cp, upload(cp->bcenter, s.bcenter, st));
          SNK_CK(cp, upload(cp->bradius, s.bradius, st));
          SNK_CK(cp, upload(cp->boys_f, s.boys_f, st));
-         if (cp->opt.precision == SNK_PREC_MIXED && cp->opt.ds_integrals) {
+         if (cp->opt.precision == SNK_PREC_MIXED) {
+           std::vector<float> pab(s.pairs.size() * 8, 0.0f);
+           for (size_t q = 0; q < s.pairs.size(); ++q) {
+             const double v[3] = {s.pairs[q].ABx, s.pairs[q].ABy, s.pairs[q].ABz};
+             for (int m = 0; m < 3; ++m) {
+               const float hh = (float)v[m];
+               pab[q * 8 + 2 * m] = hh;
+               pab[q * 8 + 2 * m + 1] = (float)(v[m] - (double)hh);
+             }
+           }
+           SNK_CK(cp, upload(cp->pair_ab, pab, st));
            std::vector<float> pds(s.prims.size() * 24);
            for (size_t q = 0; q < s.prims.size(); ++q) {
              const double* v = reinterpret_cast<const double*>(&s.prims[q]);
@@ -838,6 +864,26 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
              }
            }
            SNK_CK(cp, upload(cp->prims_ds, pds, st));
+           std::vector<float> pf(s.prims.size() * 16, 0.0f);
+           for (size_t q = 0; q < s.prims.size(); ++q) {
+             const PrimPair& P = s.prims[q];
+             float* r = &pf[q * 16];
+             const double c3[3] = {P.Px, P.Py, P.Pz};
+             r[0] = (float)P.zeta;
+             for (int m = 0; m < 3; ++m) {
+               r[1 + m] = (float)c3[m];
+               r[4 + m] = (float)(c3[m] - (double)r[1 + m]);
+             }
+             r[7] = (float)P.pref;
+             r[8] = (float)P.PAx;
+             r[9] = (float)P.PAy;
+             r[10] = (float)P.PAz;
+             r[11] = (float)P.pref_far;
+             r[12] = (float)P.k1;
+             r[13] = (float)P.k2;
+             r[14] = (float)P.k3;
+           }
+           SNK_CK(cp, upload(cp->prims_f32, pf, st));
            SNK_CK(cp, upload(cp->boys_ds, s.boys_ds, st));
          }
          SNK_CK(cp, upload(cp->xyz, s.xyz, st));
@@ -1245,7 +1291,7 @@ int learn_collect(snk_ctx* c, int stride, int64_t cap, float* feat, float* lab, 
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
     SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nullptr, c->xfunc.p, c->sfunc.p, c->fcomp.p,
-                           c->w.p, c->ws.p, nullptr, 0));
+                           c->w.p, c->ws.p, nullptr, 0, 0));
     SNK_CK(c, launch_xmax(st, db, nbc, c->ws.p, dxmax.p));
     for (int k = 0; k < kNumLists; ++k) {
       std::vector<Tile> ht;

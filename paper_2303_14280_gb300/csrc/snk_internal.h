@@ -90,6 +90,8 @@ struct BatchDesc {
   int64_t pk_off;    // the molecule's P / K block
   int64_t cm_off;    // the batch's row of shell-local arrays (F-tilde, column maps)
   int64_t phf_off;   // the batch's row of function-local arrays (Phi-tilde)
+  int32_t nS_hi;     // F / G columns [0, nS_hi) belong to shells of high-tier pairs
+  int32_t pad_;
 };
 
 // Per molecule, on the device.
@@ -103,6 +105,11 @@ struct MolDesc {
 // Integral-kernel tile: batch, pair-list range, first point.
 struct Tile {
   int32_t batch, k0, k1, i0;
+};
+
+// Pairs per tile of each of the kNumLists lists (kernel argument by value).
+struct RunLengths {
+  int32_t run[kNumLists];
 };
 
 // ---------------------------------------------------------------- host setup
@@ -205,17 +212,20 @@ struct ScreenArgs {
 };
 
 cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, int* counts, long long* ppcounts,
-                              unsigned char* sflag);
+                              unsigned char* sflag, int64_t hflag_off);
 cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list);
 // P, Khat and K below are the packed molecule blocks (BatchDesc::pk_off,
 // MolDesc::pk_off); xfunc / sfunc hold molecule-local function indices.
 // mode: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32 (X, G and P2 then
 // hold (hi, lo) float pairs in place of the doubles, see launch_split_df32).
+// mode 3: split-TF32 on the hi floats of (hi, lo) operands, FP32 partial sums
+// of 64 terms folded into double-FP32.  part: 0 all F / G columns, 1 the
+// high-tier columns [0, nS_hi), 2 the rest.
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc,
-                         const double* fcomp, const double* w, double* ws, float* ws32, int mode);
+                         const double* fcomp, const double* w, double* ws, float* ws32, int mode, int part);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode);
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part);
 // In place, each double of buf[0, n) becomes the float pair (fl32(v), fl32(v - fl32(v))).
 cudaError_t launch_split_df32(cudaStream_t st, double* buf, int64_t n);
 cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n, float2* dst);
@@ -240,10 +250,15 @@ struct IntegralArgs {
   const float* boys_f;
   float* ws32;
   const double* bcenter;
-  // mixed form with double-FP32 high lists: non-null prims_ds selects
-  // integral_kernel_ds for the FP64 lists
+  // mixed form: (hi, lo) float splits of the pair data, read by the FP32 and
+  // ds kernels; hi_ds selects integral_kernel_ds for the FP64 lists
   const float2* boys_ds;   // (hi, lo) Boys table, nodes rounded to ds values
   const float2* prims_ds;  // 12 (hi, lo) pairs per primitive pair, PrimPair order
+  const float2* pair_ab;   // 4 per shell pair: R_a - R_b as 3 (hi, lo) pairs, padding
+  // FP32 record per primitive pair: {zeta, Px_hi, Py_hi, Pz_hi}, {Px_lo, Py_lo,
+  // Pz_lo, pref}, {PAx, PAy, PAz, pref_far}, {k1, k2, k3, 0}
+  const float4* prims_f32;
+  int hi_ds;
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
@@ -257,6 +272,10 @@ cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, co
 // primitive pair and per contracted pair (from the generator's counts).
 void class_flops(int cls, double* per_prim, double* per_pair);
 
+// Tiles of every (batch, list): ceil(count / run) runs x ceil(q / 128) slabs,
+// the (batch, list)'s tiles from tiles[tstart[batch * kNumLists + list]] on.
+cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batches, const int* counts,
+                             const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles);
 cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64);
 
 // learned screen

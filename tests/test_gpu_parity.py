@@ -272,3 +272,25 @@ def test_double_fp32_integrals(snk, chain4):
     assert np.max(np.abs(Kg - Km)) <= 1e-10         # FP32 atomics: order-dependent at ~1e-11
     with pytest.raises(snk.SnkError):
         snk.Engine(p.basis, p.grid, precision="mixed", ds_integrals=2)
+
+
+def test_split_gemms(snk):
+    """SNK_GEMM_SPLIT: double-FP32 products for the F columns / G rows of
+    shells in FP64-tier pairs, chunked split-TF32 for the shells only FP32-tier
+    pairs touch; the FP32 tier's own accuracy bounds the result."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    form = dict(batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1)
+    Kd, sd = _gpu_K(snk, p, gemm="df32", **form)
+    Ks, ss = _gpu_K(snk, p, gemm="split", **form)
+    assert 0 < ss["gemm_flops_hi"] < ss["gemm_flops"]
+    assert sd["gemm_flops_hi"] == sd["gemm_flops"]
+    assert np.max(np.abs(Ks - Kref)) <= 1e-8
+    assert np.max(np.abs(Ks - Kd)) <= 1e-8
+    assert np.max(np.abs(Ks - Ks.T)) == 0.0
+    # several chunks; and with no FP32 pairs every column is high-tier
+    Kc, sc = _gpu_K(snk, p, gemm="split", workspace_bytes=1 << 20, **form)
+    assert sc["n_chunks"] > 1 and np.max(np.abs(Kc - Kref)) <= 1e-8
+    K0, s0 = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=0.0, ds_integrals=1, gemm="split")
+    assert s0["gemm_flops_hi"] == s0["gemm_flops"]
+    assert np.max(np.abs(K0 - Kref)) <= TOL_K
