@@ -31,6 +31,7 @@ namespace snk {
 namespace {
 
 constexpr int kIntThreads = kPointTile;
+constexpr int kMaxRun = 128;  // longest pair run of a tile (the autotuner's largest candidate)
 constexpr long long kBoysTMaxBits = 0x4049000000000000LL;  // bit pattern of 50.0
 static_assert(kBoysTMax == 50.0, "kBoysTMaxBits encodes 50.0");
 
@@ -213,52 +214,77 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   extern __shared__ float s_tabf[];
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
   for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
+  // the tile's pairs, staged once per tile: primitive range, shells, F / G
+  // columns and R_a - R_b
+  __shared__ int s_ppo[kMaxRun], s_ppn[kMaxRun], s_sa[kMaxRun], s_sb[kMaxRun], s_ca[kMaxRun], s_cb[kMaxRun];
+  __shared__ float s_ab[kMaxRun][3];
   __shared__ int s_tile;
   __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1);
     __syncthreads();
     const int t = s_tile;
-    __syncthreads();
+    __syncthreads();  // every thread is done with the previous tile's staged pairs
     if (t >= a.n_tiles) break;
     const Tile tile = a.tiles[t];
     const BatchDesc bd = a.batches[tile.batch];
+    const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
+    const int nrun = tile.k1 - tile.k0;                // <= kMaxRun
+    for (int r = threadIdx.x; r < nrun; r += blockDim.x) {
+      const int p = a.pairlist[tile.k0 + r];
+      const PairHdr h = a.pairs[p];
+      s_ppo[r] = h.pp_off;
+      s_ppn[r] = h.pp_n;
+      s_sa[r] = h.sa;
+      s_sb[r] = h.sb;
+      s_ca[r] = cmap[h.sa];
+      s_cb[r] = cmap[h.sb];
+      const float2* ab = a.pair_ab + 4 * (size_t)p;
+      s_ab[r][0] = ab[0].x;
+      s_ab[r][1] = ab[1].x;
+      s_ab[r][2] = ab[2].x;
+    }
+    __syncthreads();
     const int i = tile.i0 + threadIdx.x;
-    if (i >= bd.q) continue;
+    if (i >= bd.q || nrun <= 0) continue;
     const ds cx = ds_from(a.xyz[3 * (bd.p0 + i)]), cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]),
              cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
     const int64_t ldq = bd.ldq;
     const float* F = a.ws32 + bd.foff32 + i;
     float* G = a.ws32 + bd.goff32 + i;
-    const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
-    float ga[NA], fa[NA];
+    float ga[NA], fa[NA], fn[NB];
     int cur = -1, cola = 0;
-    for (int k = tile.k0; k < tile.k1; ++k) {
-      const int p = a.pairlist[k];
-      const PairHdr h = a.pairs[p];
-      if (h.sa != cur) {
+#pragma unroll
+    for (int v = 0; v < NB; ++v) fn[v] = F[(s_cb[0] + v) * ldq];
+    for (int r = 0; r < nrun; ++r) {
+      float fb[NB];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) fb[v] = fn[v];
+      if (r + 1 < nrun) {  // the next pair's F_b is in flight while this pair computes
+        const int cn = s_cb[r + 1];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) fn[v] = F[(cn + v) * ldq];
+      }
+      const int sa = s_sa[r];
+      if (sa != cur) {
         if (cur >= 0) {
 #pragma unroll
           for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
         }
-        cur = h.sa;
-        cola = cmap[cur];
+        cur = sa;
+        cola = s_ca[r];
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
           ga[u] = 0.f;
           fa[u] = F[(cola + u) * ldq];
         }
       }
-      const int colb = cmap[h.sb];
-      if (cola < 0 || colb < 0) continue;  // cannot happen: the screen marks both shells of a kept pair
-      float fb[NB];
-#pragma unroll
-      for (int v = 0; v < NB; ++v) fb[v] = F[(colb + v) * ldq];
       float acc[C::NACC];
 #pragma unroll
       for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
-      for (int q = 0; q < h.pp_n; ++q) {
-        const float4* pp = a.prims_f32 + (size_t)(h.pp_off + q) * 4;
+      const int ppo = s_ppo[r], ppn = s_ppn[r];
+      for (int q = 0; q < ppn; ++q) {
+        const float4* pp = a.prims_f32 + (size_t)(ppo + q) * 4;
         const float4 r0 = pp[0], r1 = pp[1], r2 = pp[2], r3 = pp[3];
         const float PCx = (r0.y - cx.hi) + (r1.x - cx.lo);
         const float PCy = (r0.z - cy.hi) + (r1.y - cy.lo);
@@ -268,14 +294,14 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         boys_seeds_f32<C::L>(T, r1.w, r2.w, s_tabf, S);
         C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
       }
-      const float2* ab = a.pair_ab + 4 * (size_t)p;
       float xi[NA * NB];
-      C::hrr(acc, ab[0].x, ab[1].x, ab[2].x, xi);
+      C::hrr(acc, s_ab[r][0], s_ab[r][1], s_ab[r][2], xi);
 #pragma unroll
       for (int u = 0; u < NA; ++u)
 #pragma unroll
         for (int v = 0; v < NB; ++v) ga[u] = fmaf(xi[u * NB + v], fb[v], ga[u]);
-      if (h.sa != h.sb) {
+      if (sa != s_sb[r]) {
+        const int colb = s_cb[r];
 #pragma unroll
         for (int v = 0; v < NB; ++v) {
           float g = 0.f;
@@ -285,10 +311,8 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         }
       }
     }
-    if (cur >= 0) {
 #pragma unroll
-      for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
-    }
+    for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
   }
 }
 

@@ -250,6 +250,8 @@ int make_tiles(snk_ctx* c, cudaStream_t st) {
     for (int k = 0; k < kNumLists; ++k) {
       ch.tile_off[k] = tot;
       const int run = c->run[k];
+      if (run < 1 || run > 128)  // the FP32 kernel stages at most 128 pairs per tile
+        return fail(c, SNK_ERR_INVALID_ARG, "pairs per tile outside 1..128");
       for (int t = ch.b0; t < ch.b1; ++t) {
         const int64_t n = c->hcounts[(size_t)t * kNumLists + k];
         tstart[(size_t)t * kNumLists + k] = tot;
