@@ -171,8 +171,11 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
 template <int L>
 __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_far, const float* tab, float* S) {
   if (T < kBoysTMaxF) {
+    static_assert(kBoysColsF == 8 && kBoysTermsF == 6, "an FP32 table row is two float4");
     const int k = __float2int_rn(T * (float)(1.0 / kBoysH));
-    const float* row = tab + k * kBoysColsF;
+    const float4 lo = reinterpret_cast<const float4*>(tab)[2 * k];      // F_{L+m}/m!, m = 0..3
+    const float4 hi = reinterpret_cast<const float4*>(tab)[2 * k + 1];  // m = 4, 5; e^{-T_k}; T_k
+    const float row[kBoysColsF] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
     const float x = row[kBoysColsF - 1] - T;
     float f = row[kBoysTermsF - 1];
 #pragma unroll
@@ -211,7 +214,7 @@ template <int LA, int LB>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
-  extern __shared__ float s_tabf[];
+  extern __shared__ __align__(16) float s_tabf[];
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
   for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
   // the tile's pairs, staged once per tile: primitive range, shells, F / G

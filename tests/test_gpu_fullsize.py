@@ -43,3 +43,30 @@ def test_fullsize_properties(built):
     assert np.all(np.isfinite(K))
     assert st["n_points"] == 768000 and st["n_functions"] == 992
     assert 0 < st["pairs_kept"] <= st["n_pairs"] * st["n_batches"]
+
+
+GOLDEN256 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster256_K_entries.txt")
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN256), reason="cluster256 oracle entries not generated")
+def test_cluster256_mixed_form_matches_oracle_entries():
+    """The mixed form on the 256-atom workload (2,640 functions, 2,048,000
+    points) in the configuration bench.py times, against 105 oracle entries;
+    target max|dK| <= 1e-8 (the FP32 tier's ~1e-6 relative error on blocks
+    whose estimate is below 3e-4)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2303_14280_gb300 as snk
+    p = synth.cluster256(device="cuda")
+    w, thr, _ = snk.trained_screen()
+    eng = snk.Engine(p.basis, p.grid, eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1,
+                     screen="learned", learned_skip=thr)
+    eng.screen_load(w)
+    eng.set_density(p.P)
+    K = eng.build_K()
+    eng.close()
+    d = np.loadtxt(GOLDEN256)
+    mu, nu, ref = d[:, 0].astype(int), d[:, 1].astype(int), d[:, 2]
+    assert np.max(np.abs(K[mu, nu] - ref)) <= 1e-8
+    assert np.max(np.abs(K - K.T)) == 0.0
