@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
 #pragma unroll
       for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
       const int ppo = s_ppo[r], ppn = s_ppn[r];
+#pragma unroll 2
       for (int q = 0; q < ppn; ++q) {
         const float4* pp = a.prims_f32 + (size_t)(ppo + q) * 4;
         const float4 r0 = pp[0], r1 = pp[1], r2 = pp[2], r3 = pp[3];

@@ -305,37 +305,48 @@ __global__ void mlp_infer_kernel(const float* __restrict__ wg, const float* __re
 //   distance from the batch sphere to the segment AB (/10 bohr), |AB| (/10),
 //   log10 F-tilde_a, F-tilde_b, phi-tilde_j, the batch bound A-tilde_j and the
 //   sn-LinK estimate epsilon^K (/10), the batch radius (/10), log10 |Q_j| (/4).
+// log10(max(x, 1e-40)) of a double through its binary exponent and an FP32
+// log of the mantissa: no FP64 transcendental.
+__device__ __forceinline__ float log10_clamped(double x) {
+  int e;
+  const float m = (float)frexp(fmax(x, 1e-40), &e);  // x = m 2^e, m in [0.5, 1)
+  return log10f(m) + (float)e * 0.30102999566f;
+}
+
 __device__ void block_features(const ScreenArgs& a, const BatchDesc& bd, int j, int p, const PairHdr& h,
                                const float* __restrict__ shell_feat, float* f) {
+  // geometry in FP32 and logs through log10_clamped: the FP64 pipe is 1/64 of
+  // the FP32 rate on this GPU, and the features feed an FP16 network
   const double* ft = a.ft_shell + bd.cm_off;
   const double fa = ft[h.sa - bd.ms0], fb = ft[h.sb - bd.ms0];
   const double* A = a.shell_xyz + 3 * h.sa;
-  const double vx = -h.ABx, vy = -h.ABy, vz = -h.ABz;
-  const double wx = a.bcenter[3 * j] - A[0], wy = a.bcenter[3 * j + 1] - A[1], wz = a.bcenter[3 * j + 2] - A[2];
-  const double vv = vx * vx + vy * vy + vz * vz;
-  double t = vv > 0.0 ? (wx * vx + wy * vy + wz * vz) / vv : 0.0;
-  t = fmin(fmax(t, 0.0), 1.0);
-  const double dx = wx - t * vx, dy = wy - t * vy, dz = wz - t * vz;
-  const double d = fmax(sqrt(dx * dx + dy * dy + dz * dz) - a.bradius[j], 0.0);
+  const float vx = (float)-h.ABx, vy = (float)-h.ABy, vz = (float)-h.ABz;
+  const float wx = (float)(a.bcenter[3 * j] - A[0]), wy = (float)(a.bcenter[3 * j + 1] - A[1]),
+              wz = (float)(a.bcenter[3 * j + 2] - A[2]);
+  const float vv = vx * vx + vy * vy + vz * vz;
+  float t = vv > 0.f ? __fdividef(wx * vx + wy * vy + wz * vz, vv) : 0.f;
+  t = fminf(fmaxf(t, 0.f), 1.f);
+  const float dx = wx - t * vx, dy = wy - t * vy, dz = wz - t * vz;
+  const float rad = (float)a.bradius[j];
+  const float d = fmaxf(sqrtf(dx * dx + dy * dy + dz * dz) - rad, 0.f);
   double bnd = a.bound[p];
-  if (d > 0.0) bnd = fmin(bnd, a.qbound[p] / d);
+  if (d > 0.f) bnd = fmin(bnd, a.qbound[p] * (double)(1.0f / d));
   const double eK = fmax(fa, fb) * a.phit_b[j] * bnd;
-  auto lg = [](double x) { return (float)log10(fmax(x, 1e-40)); };
   f[0] = shell_feat[4 * h.sa + 0];  // l / 2
   f[1] = shell_feat[4 * h.sb + 0];
   f[2] = shell_feat[4 * h.sa + 1];  // log10 min exponent / 3
   f[3] = shell_feat[4 * h.sb + 1];
   f[4] = shell_feat[4 * h.sa + 2];  // log10 max exponent / 3
   f[5] = shell_feat[4 * h.sb + 2];
-  f[6] = (float)(d / 10.0);
-  f[7] = (float)(sqrt(vv) / 10.0);
-  f[8] = lg(fa) / 10.f;
-  f[9] = lg(fb) / 10.f;
-  f[10] = lg(a.phit_b[j]) / 10.f;
-  f[11] = lg(bnd) / 10.f;
-  f[12] = lg(eK) / 10.f;
-  f[13] = (float)(a.bradius[j] / 10.0);
-  f[14] = lg((double)bd.q) / 4.f;
+  f[6] = d / 10.f;
+  f[7] = sqrtf(vv) / 10.f;
+  f[8] = log10_clamped(fa) / 10.f;
+  f[9] = log10_clamped(fb) / 10.f;
+  f[10] = log10_clamped(a.phit_b[j]) / 10.f;
+  f[11] = log10_clamped(bnd) / 10.f;
+  f[12] = log10_clamped(eK) / 10.f;
+  f[13] = rad / 10.f;
+  f[14] = log10f((float)bd.q) / 4.f;
   f[15] = 1.f;
 }
 
