@@ -66,6 +66,21 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x (the slowest replica sets the job time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms_max, steps, world, units_per_step=1):
+    """Whole-job rate: the units every replica processed over the slowest
+    replica's time (replicas only: each rank runs its own full builds)."""
+    return world * steps * units_per_step / (ms_max * 1e-3)
+
+
 def make_problems(name, device=None):
     import synth
     if name == "batch64":
@@ -336,12 +351,6 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     snk.lib()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -369,8 +378,8 @@ def main():
     with ClockSampler(local) as clk:
         ms, acc = timed(ch, args.steps, args.warmup, stream, barrier)
     clocks = clk.summary()
-    ms = max_over_ranks(ms)
-    value = world * args.steps * (n_mol if batch else 1) / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_throughput(ms, args.steps, world, n_mol if batch else 1)
     unit = "molecule K-builds/s" if batch else "K-builds/s"
     st_ch = ch.stats()
     K_ch = ch.Ks()
@@ -388,8 +397,8 @@ def main():
             ch.host_step(Ph, Kh)
     torch.cuda.synchronize()
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t)
-    e2e_value = world * args.steps * (n_mol if batch else 1) / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
+    e2e_value = job_throughput(e2e_s * 1e3, args.steps, world, n_mol if batch else 1)
     nbytes = sum(p.P.nbytes for p in probs)
     ch_create = ch.create_s
     ch.close()
@@ -399,8 +408,8 @@ def main():
     ps = args.plain_steps if args.plain_steps is not None else args.steps
     pw = args.plain_warmup if args.plain_warmup is not None else args.warmup
     ms_pl, acc_pl = timed(pl, ps, pw, stream, barrier)
-    ms_pl = max_over_ranks(ms_pl)
-    value_pl = world * ps * n_mol / (ms_pl * 1e-3)
+    ms_pl = max_over_ranks(ms_pl, dist, dev)
+    value_pl = job_throughput(ms_pl, ps, world, n_mol)
     K_pl = pl.Ks()
     st_pl = pl.stats()
     pl.close()

@@ -120,7 +120,14 @@ typedef struct {
                               fp32_bound in double-FP32 arithmetic (hi + lo float
                               pairs on the FP32 pipe, ~1e-14 relative) instead of
                               FP64; default 0                                   */
-  double reserved[5];
+  int32_t fp32_g64;        /* mixed form: 1 adds the FP32 pairs' G contributions
+                              to the FP64 G with FP64 atomics (no FP32 partial
+                              sums); default 0, an FP32 copy of G merged once   */
+  int32_t fp32_hrr_ds;     /* mixed form: 1 runs the FP32 pairs' HRR (Eq. hrr, once per
+                              pair and point) in double-FP32 on the FP32 VRR result;
+                              the transfer's cancellation for distant shells is the
+                              FP32 tier's main error source; default 0          */
+  double reserved[4];
 } snk_options;
 
 /* Per-build counters and phase times (CUDA events on the library stream). */

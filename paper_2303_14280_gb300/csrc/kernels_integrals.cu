@@ -210,7 +210,7 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
 // no barrier per pair) with the product centre split into hi + lo floats, and
 // P - r_i is formed as (P_hi - r_hi) + (P_lo - r_lo) so that it is accurate to
 // FP32 relative to |P - r_i| however far the molecule sits from the origin.
-template <int LA, int LB>
+template <int LA, int LB, bool HRR_DS>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   // the tile's pairs, staged once per tile: primitive range, shells, F / G
   // columns and R_a - R_b
   __shared__ int s_ppo[kMaxRun], s_ppn[kMaxRun], s_sa[kMaxRun], s_sb[kMaxRun], s_ca[kMaxRun], s_cb[kMaxRun];
-  __shared__ float s_ab[kMaxRun][3];
+  __shared__ float2 s_ab[kMaxRun][3];  // (hi, lo)
   __shared__ int s_tile;
   __syncthreads();
   for (;;) {
@@ -243,9 +243,9 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       s_ca[r] = cmap[h.sa];
       s_cb[r] = cmap[h.sb];
       const float2* ab = a.pair_ab + 4 * (size_t)p;
-      s_ab[r][0] = ab[0].x;
-      s_ab[r][1] = ab[1].x;
-      s_ab[r][2] = ab[2].x;
+      s_ab[r][0] = ab[0];
+      s_ab[r][1] = ab[1];
+      s_ab[r][2] = ab[2];
     }
     __syncthreads();
     const int i = tile.i0 + threadIdx.x;
@@ -255,6 +255,14 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     const int64_t ldq = bd.ldq;
     const float* F = a.ws32 + bd.foff32 + i;
     float* G = a.ws32 + bd.goff32 + i;
+    double* G64 = a.ws + bd.goff + i;
+    const bool g64 = a.f32_g64 != 0;
+    auto gadd = [&](int col, float v) {
+      if (g64)
+        atomicAdd(G64 + col * ldq, (double)v);
+      else
+        atomicAdd(G + col * ldq, v);
+    };
     float ga[NA], fa[NA], fn[NB];
     int cur = -1, cola = 0;
 #pragma unroll
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       if (sa != cur) {
         if (cur >= 0) {
 #pragma unroll
-          for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
+          for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
         }
         cur = sa;
         cola = s_ca[r];
@@ -299,7 +307,17 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
       }
       float xi[NA * NB];
-      C::hrr(acc, s_ab[r][0], s_ab[r][1], s_ab[r][2], xi);
+      if (HRR_DS && LB > 0) {
+        ds accd[C::NACC], xid[NA * NB];
+#pragma unroll
+        for (int u = 0; u < C::NACC; ++u) accd[u] = ds_make(acc[u], 0.f);
+        C::hrr(accd, ds_make(s_ab[r][0].x, s_ab[r][0].y), ds_make(s_ab[r][1].x, s_ab[r][1].y),
+               ds_make(s_ab[r][2].x, s_ab[r][2].y), xid);
+#pragma unroll
+        for (int u = 0; u < NA * NB; ++u) xi[u] = __fadd_rn(xid[u].hi, xid[u].lo);
+      } else {
+        C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
+      }
 #pragma unroll
       for (int u = 0; u < NA; ++u)
 #pragma unroll
@@ -311,12 +329,12 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
           float g = 0.f;
 #pragma unroll
           for (int u = 0; u < NA; ++u) g = fmaf(xi[u * NB + v], fa[u], g);
-          atomicAdd(G + (colb + v) * ldq, g);
+          gadd(colb + v, g);
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
+    for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
   }
 }
 
@@ -588,11 +606,16 @@ constexpr size_t kSmem32 = sizeof(float) * kBoysRowsF * kBoysColsF;
 // class list - kNumClasses.
 template <int LA, int LB>
 cudaError_t launch_class(cudaStream_t st, bool f32, const IntegralArgs& a, int grid) {
-  if (f32) {
-    cudaError_t e =
-        cudaFuncSetAttribute(integral_kernel_f32<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
+  if (f32 && a.f32_hrr_ds) {
+    cudaError_t e = cudaFuncSetAttribute(integral_kernel_f32<LA, LB, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
     if (e != cudaSuccess) return e;
-    integral_kernel_f32<LA, LB><<<grid, kIntThreads, kSmem32, st>>>(a);
+    integral_kernel_f32<LA, LB, true><<<grid, kIntThreads, kSmem32, st>>>(a);
+  } else if (f32) {
+    cudaError_t e = cudaFuncSetAttribute(integral_kernel_f32<LA, LB, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
+    if (e != cudaSuccess) return e;
+    integral_kernel_f32<LA, LB, false><<<grid, kIntThreads, kSmem32, st>>>(a);
   } else if (a.hi_ds) {
     cudaError_t e =
         cudaFuncSetAttribute(integral_kernel_ds<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
@@ -617,8 +640,9 @@ int ctas_for(K kernel, size_t smem, int num_sms) {
 }
 
 template <int LA, int LB>
-int max_ctas(bool f32, bool ds, int num_sms) {
-  return f32  ? ctas_for(integral_kernel_f32<LA, LB>, kSmem32, num_sms)
+int max_ctas(bool f32, bool ds, bool hrr_ds, int num_sms) {
+  if (f32 && hrr_ds) return ctas_for(integral_kernel_f32<LA, LB, true>, kSmem32, num_sms);
+  return f32  ? ctas_for(integral_kernel_f32<LA, LB, false>, kSmem32, num_sms)
          : ds ? ctas_for(integral_kernel_ds<LA, LB>, kSmem64, num_sms)
               : ctas_for(integral_kernel<LA, LB>, kSmem64, num_sms);
 }
@@ -639,15 +663,15 @@ cudaError_t launch_integrals(cudaStream_t st, int list, const IntegralArgs& a, i
   return cudaErrorInvalidValue;
 }
 
-int integral_max_ctas(int list, int num_sms, bool ds) {
+int integral_max_ctas(int list, int num_sms, bool ds, bool hrr_ds) {
   const bool f32 = list >= kNumClasses;
   switch (list % kNumClasses) {
-    case 0: return max_ctas<0, 0>(f32, ds, num_sms);
-    case 1: return max_ctas<1, 0>(f32, ds, num_sms);
-    case 2: return max_ctas<1, 1>(f32, ds, num_sms);
-    case 3: return max_ctas<2, 0>(f32, ds, num_sms);
-    case 4: return max_ctas<2, 1>(f32, ds, num_sms);
-    case 5: return max_ctas<2, 2>(f32, ds, num_sms);
+    case 0: return max_ctas<0, 0>(f32, ds, hrr_ds, num_sms);
+    case 1: return max_ctas<1, 0>(f32, ds, hrr_ds, num_sms);
+    case 2: return max_ctas<1, 1>(f32, ds, hrr_ds, num_sms);
+    case 3: return max_ctas<2, 0>(f32, ds, hrr_ds, num_sms);
+    case 4: return max_ctas<2, 1>(f32, ds, hrr_ds, num_sms);
+    case 5: return max_ctas<2, 2>(f32, ds, hrr_ds, num_sms);
   }
   return num_sms;
 }

@@ -525,6 +525,8 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.pair_ab = reinterpret_cast<const float2*>(c->pair_ab.p);
   a.prims_f32 = reinterpret_cast<const float4*>(c->prims_f32.p);
   a.hi_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals) ? 1 : 0;
+  a.f32_g64 = c->opt.fp32_g64 ? 1 : 0;
+  a.f32_hrr_ds = c->opt.fp32_hrr_ds ? 1 : 0;
   return a;
 }
 
@@ -570,7 +572,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       ++c->launches_build;
     }
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
-    if (mixed) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
+    if (mixed && !c->opt.fp32_g64) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, list by list
     for (int k = 0; k < kNumLists; ++k) {
@@ -583,7 +585,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     }
     // the FP32 pairs' G into the FP64 G, then Kt += G_j^T X_j, Eq. (usym_k)
-    if (mixed && ch.g32n > 0) {
+    if (mixed && ch.g32n > 0 && !c->opt.fp32_g64) {
       SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
       ++c->launches_build;
     }
@@ -772,7 +774,8 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
   if (c->opt.gemm < 0 || c->opt.gemm > 2 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
       (c->opt.gemm != SNK_GEMM_FP64 && c->opt.tensor_gemms != 0) || c->opt.ds_integrals < 0 ||
-      c->opt.ds_integrals > 1)
+      c->opt.ds_integrals > 1 || c->opt.fp32_g64 < 0 || c->opt.fp32_g64 > 1 ||
+      c->opt.fp32_hrr_ds < 0 || c->opt.fp32_hrr_ds > 1)
     return SNK_ERR_INVALID_ARG;
   for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
   int rc = build_setup(n_mol, bases, grids, &c->opt, &c->s, &c->err);
@@ -901,7 +904,8 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
     return rc;
   if ((rc = geometry_screen(cp)) != SNK_OK) return rc;
   const bool ds = cp->opt.precision == SNK_PREC_MIXED && cp->opt.ds_integrals;
-  for (int k = 0; k < kNumLists; ++k) cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms, ds);
+  for (int k = 0; k < kNumLists; ++k)
+    cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms, ds, cp->opt.fp32_hrr_ds != 0);
   std::memset(&cp->st, 0, sizeof(cp->st));
   cp->st.n_points = s.npts;
   cp->st.n_batches = cp->nbatch;
@@ -931,6 +935,8 @@ void snk_options_default(snk_options* o) {
   o->tensor_gemms = 0;
   o->gemm = SNK_GEMM_FP64;
   o->ds_integrals = 0;
+  o->fp32_g64 = 0;
+  o->fp32_hrr_ds = 0;
   o->graph = 0;
   o->learned_skip = -11.0;
 }

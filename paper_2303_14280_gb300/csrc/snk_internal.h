@@ -259,10 +259,12 @@ struct IntegralArgs {
   // Pz_lo, pref}, {PAx, PAy, PAz, pref_far}, {k1, k2, k3, 0}
   const float4* prims_f32;
   int hi_ds;
+  int f32_g64;  // FP32 lists add into the FP64 G (ws + goff) instead of the FP32 copy
+  int f32_hrr_ds;  // FP32 lists run the HRR in double-FP32
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
-int integral_max_ctas(int cls, int num_sms, bool ds);
+int integral_max_ctas(int cls, int num_sms, bool ds, bool hrr_ds);
 cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const PrimPair* prims,
                            const double* boys, int64_t n, const double* xyz, double* xi);
 cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, const double* T,

@@ -294,3 +294,21 @@ def test_split_gemms(snk):
     K0, s0 = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=0.0, ds_integrals=1, gemm="split")
     assert s0["gemm_flops_hi"] == s0["gemm_flops"]
     assert np.max(np.abs(K0 - Kref)) <= TOL_K
+
+
+def test_fp32_tier_accumulation_and_hrr_variants(snk):
+    """FP32 pairs added straight into the FP64 G (fp32_g64) and their HRR run in
+    double-FP32 (fp32_hrr_ds): both keep the mixed form's parity; neither
+    changes its accuracy measurably (the FP32 tier's error is in the FP32
+    Boys seeds and recursions), so both are off by default."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    form = dict(batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="split")
+    K0, s0 = _gpu_K(snk, p, **form)
+    K1, _ = _gpu_K(snk, p, fp32_g64=1, **form)
+    K2, _ = _gpu_K(snk, p, fp32_hrr_ds=1, **form)
+    assert s0["pairs_kept_fp32"] > 0
+    for K in (K0, K1, K2):
+        assert np.max(np.abs(K - Kref)) <= 1e-8
+        assert np.max(np.abs(K - K.T)) == 0.0
+    assert np.max(np.abs(K1 - K0)) <= 1e-9 and np.max(np.abs(K2 - K0)) <= 1e-9
