@@ -11,7 +11,8 @@ the P upload and the K download inside the timed region.
 Forms:
   plain   FP64 everywhere, rigorous sn-LinK screen at 1e-12 (eps_B = eps_E = eps_K)
   chosen  rigorous screen at 1e-10, then the learned block screen (shipped
-          weights and calibrated threshold); pairs whose sn-LinK estimate is
+          weights and calibrated thresholds: skip, and move high-tier blocks
+          with a small predicted contribution to FP32); pairs whose sn-LinK estimate is
           below 3e-4 run their integrals in FP32, the rest in double-FP32 (hi +
           lo float pairs, ~1e-14 relative); F = X P and Kt = G^T X in
           double-FP32 arithmetic for the columns of shells in double-FP32
@@ -371,9 +372,11 @@ def main():
                 "integrals otherwise, GEMMs in double-FP32 for those pairs' shells and split-TF32 tensor-core "
                 "products for the rest, FP64 G and K accumulation")
         if not args.no_learned and os.path.exists(snk.SCREEN_WEIGHTS):
-            learned, thr, _ = snk.trained_screen()
-            chosen_opts.update(screen="learned", learned_skip=thr)
-            form += f", learned block screen (skip below 10^{thr:g})"
+            learned, thr, meta = snk.trained_screen()
+            thr32 = float(meta.get("fp32_threshold", -99.0))
+            chosen_opts.update(screen="learned", learned_skip=thr, learned_fp32=thr32)
+            form += (f", learned block screen (skip below 10^{thr:g}, double-FP32 blocks predicted below "
+                     f"10^{thr32:g} moved to the FP32 tier)")
     ch = Runner(snk, probs, chosen_opts, batch, dev, stream, learned)
     with ClockSampler(local) as clk:
         ms, acc = timed(ch, args.steps, args.warmup, stream, barrier)

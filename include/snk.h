@@ -125,9 +125,13 @@ typedef struct {
                               sums); default 0, an FP32 copy of G merged once   */
   int32_t fp32_hrr_ds;     /* mixed form: 1 runs the FP32 pairs' HRR (Eq. hrr, once per
                               pair and point) in double-FP32 on the FP32 VRR result;
-                              the transfer's cancellation for distant shells is the
-                              FP32 tier's main error source; default 0          */
-  double reserved[4];
+                              measured to leave the FP32 tier's error unchanged (it
+                              comes from the FP32 seeds and VRR); default 0      */
+  double learned_fp32;     /* learned screen, mixed form: a block of the FP64 (or
+                              double-FP32) tier whose predicted log10 contribution
+                              is below this moves to the FP32 tier; default -99
+                              (off)                                             */
+  double reserved[3];
 } snk_options;
 
 /* Per-build counters and phase times (CUDA events on the library stream). */

@@ -73,7 +73,8 @@ class SnkOptions(ctypes.Structure):
                 ("distance_bound", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64), ("tensor_gemms", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("learned_skip", ctypes.c_double), ("gemm", ctypes.c_int32), ("ds_integrals", ctypes.c_int32),
-                ("fp32_g64", ctypes.c_int32), ("fp32_hrr_ds", ctypes.c_int32), ("reserved", ctypes.c_double * 4)]
+                ("fp32_g64", ctypes.c_int32), ("fp32_hrr_ds", ctypes.c_int32),
+                ("learned_fp32", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
 
 
 class SnkStats(ctypes.Structure):

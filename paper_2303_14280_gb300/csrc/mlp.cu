@@ -375,12 +375,14 @@ __global__ void features_kernel(ScreenArgs a, const int* __restrict__ pairlist, 
 // Learned screen: for every entry of batch j's lists, predict log10 of the
 // block's contribution to K and clear its keep flag if the prediction is below
 // skip_log10.  One warp evaluates 16 entries at a time on the tensor cores.
+// Entries of the FP64 (high-tier) lists predicted below fp32_log10 are
+// marked 2: they move to the FP32 list of their class.
 __global__ void __launch_bounds__(128) learned_filter_kernel(ScreenArgs a, const float* __restrict__ wg,
                                                              const int* __restrict__ pairlist,
                                                              const int64_t* __restrict__ list_off,
                                                              const int* __restrict__ counts,
                                                              const float* __restrict__ shell_feat, float skip_log10,
-                                                             unsigned char* __restrict__ keep) {
+                                                             float fp32_log10, unsigned char* __restrict__ keep) {
   __shared__ MlpSmem sm;
   __shared__ float fbuf[4][16][kMlpIn + 1];
   load_mlp_smem(&sm, wg);
@@ -390,8 +392,9 @@ __global__ void __launch_bounds__(128) learned_filter_kernel(ScreenArgs a, const
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int64_t b0 = list_off[(int64_t)j * kNumLists];
-  int64_t tot = 0;
+  int64_t tot = 0, n64 = 0;
   for (int L = 0; L < kNumLists; ++L) tot += counts[(int64_t)j * kNumLists + L];
+  for (int L = 0; L < kNumClasses; ++L) n64 += counts[(int64_t)j * kNumLists + L];
   for (int64_t base = (int64_t)warp * 16; base < tot; base += 4 * 16) {
     // lanes 0..15 compute one row of features each
     if (lane < 16) {
@@ -414,51 +417,102 @@ __global__ void __launch_bounds__(128) learned_filter_kernel(ScreenArgs a, const
     mlp_infer16(&sm, in, lane, &y0, &y1);
     if (t == 0) {
       // labels are trained as log10(contribution) / 10
-      if (base + g < tot && 10.f * y0 < skip_log10) keep[b0 + base + g] = 0;
-      if (base + g + 8 < tot && 10.f * y1 < skip_log10) keep[b0 + base + g + 8] = 0;
+      const int64_t e0 = base + g, e1 = base + g + 8;
+      if (e0 < tot) keep[b0 + e0] = 10.f * y0 < skip_log10 ? 0 : (e0 < n64 && 10.f * y0 < fp32_log10) ? 2 : 1;
+      if (e1 < tot) keep[b0 + e1] = 10.f * y1 < skip_log10 ? 0 : (e1 < n64 && 10.f * y1 < fp32_log10) ? 2 : 1;
     }
     __syncwarp();
   }
 }
 
-// Compacts every (batch, list) segment of the pair lists in place, keeping
-// the entries whose flag is set (order kept); writes the new counts.
-__global__ void __launch_bounds__(256) compact_lists_kernel(int* __restrict__ pairlist,
-                                                            const int64_t* __restrict__ list_off,
-                                                            int* __restrict__ counts,
-                                                            const unsigned char* __restrict__ keep,
-                                                            const PairHdr* __restrict__ pairs,
-                                                            long long* __restrict__ ppcounts) {
-  __shared__ unsigned long long s_pp;
-  if (threadIdx.x == 0) s_pp = 0ull;
-  const int64_t seg = blockIdx.x;  // batch * kNumLists + list
-  const int64_t b0 = list_off[seg];
-  const int n = counts[seg];
-  __shared__ int warp_tot[8];
+// Block-wide stream compaction of one list segment: appends the entries of
+// src[0, n) whose code equals `want` to dst[out...]; returns the new out.
+__device__ int append_coded(const int* __restrict__ src, const unsigned char* __restrict__ code, int n,
+                            unsigned char want, int* __restrict__ dst, int out, const PairHdr* __restrict__ pairs,
+                            unsigned long long* s_pp, int* warp_tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int out = 0;
   for (int base = 0; base < n; base += 256) {
     const int e = base + threadIdx.x;
-    const bool k = e < n && keep[b0 + e];
-    const int v = k ? pairlist[b0 + e] : 0;
+    const bool k = e < n && code[e] == want;
+    const int v = k ? src[e] : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, k);
     if (lane == 0) warp_tot[warp] = __popc(bal);
-    __syncthreads();  // every read of this chunk is done before any write below
+    __syncthreads();
     int before = 0, total = 0;
     for (int q = 0; q < 8; ++q) {
       before += q < warp ? warp_tot[q] : 0;
       total += warp_tot[q];
     }
     if (k) {
-      pairlist[b0 + out + before + __popc(bal & ((1u << lane) - 1u))] = v;
-      atomicAdd(&s_pp, (unsigned long long)pairs[v].pp_n);
+      dst[out + before + __popc(bal & ((1u << lane) - 1u))] = v;
+      atomicAdd(s_pp, (unsigned long long)pairs[v].pp_n);
     }
     out += total;
+    __syncthreads();  // warp_tot is rewritten by the next chunk
+  }
+  return out;
+}
+
+// One block per batch: rewrites the batch's twelve lists into dst (same
+// batch base, order kept): a high-tier list keeps its code-1 entries, an
+// FP32 list its own code-1 entries followed by the code-2 entries of the
+// high-tier list of its class.  New offsets and counts replace the old ones;
+// the batch's high-tier shell flags are re-marked from the final lists.
+__global__ void __launch_bounds__(256) reorder_lists_kernel(const int* __restrict__ src, int* __restrict__ dst,
+                                                            int64_t* __restrict__ list_off, int* __restrict__ counts,
+                                                            const unsigned char* __restrict__ keep,
+                                                            const PairHdr* __restrict__ pairs,
+                                                            long long* __restrict__ ppcounts,
+                                                            const BatchDesc* __restrict__ batches,
+                                                            const MolDesc* __restrict__ mols,
+                                                            unsigned char* __restrict__ hflag) {
+  __shared__ unsigned long long s_pp;
+  __shared__ int warp_tot[8];
+  __shared__ int64_t s_off[kNumLists];
+  __shared__ int s_n[kNumLists];
+  const int j = blockIdx.x;
+  const int64_t seg0 = (int64_t)j * kNumLists;
+  if (threadIdx.x < kNumLists) {
+    s_off[threadIdx.x] = list_off[seg0 + threadIdx.x];
+    s_n[threadIdx.x] = counts[seg0 + threadIdx.x];
+  }
+  __syncthreads();
+  const int64_t b0 = s_off[0];
+  int out = 0;
+  int64_t new_off[kNumLists];
+  int new_n[kNumLists];
+  unsigned long long new_pp[kNumLists];
+  for (int k = 0; k < kNumLists; ++k) {
+    if (threadIdx.x == 0) s_pp = 0ull;
+    __syncthreads();
+    const int start = out;
+    out = append_coded(src + s_off[k], keep + s_off[k], s_n[k], 1, dst + b0, out, pairs, &s_pp, warp_tot);
+    if (k >= kNumClasses) {
+      const int h = k - kNumClasses;
+      out = append_coded(src + s_off[h], keep + s_off[h], s_n[h], 2, dst + b0, out, pairs, &s_pp, warp_tot);
+    }
+    new_off[k] = b0 + start;
+    new_n[k] = out - start;
+    new_pp[k] = s_pp;
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    counts[seg] = out;
-    ppcounts[seg] = (long long)s_pp;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kNumLists; ++k) {
+      list_off[seg0 + k] = new_off[k];
+      counts[seg0 + k] = new_n[k];
+      ppcounts[seg0 + k] = (long long)new_pp[k];
+    }
+  // high-tier shells of the final lists
+  const BatchDesc bd = batches[j];
+  const MolDesc md = mols[bd.mol];
+  unsigned char* hl = hflag + bd.cm_off;
+  for (int a = threadIdx.x; a < md.ns; a += blockDim.x) hl[a] = 0;
+  __syncthreads();
+  const int nhi = (int)(new_off[kNumClasses] - b0);
+  for (int e = threadIdx.x; e < nhi; e += blockDim.x) {
+    const PairHdr h = pairs[dst[b0 + e]];
+    hl[h.sa - bd.ms0] = 1;
+    hl[h.sb - bd.ms0] = 1;
   }
 }
 
@@ -499,14 +553,17 @@ cudaError_t launch_features(cudaStream_t st, const ScreenArgs& a, const int* pai
   return cudaGetLastError();
 }
 
-cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbatch, const float* w, int* pairlist,
-                                  const int64_t* list_off, int* counts, long long* ppcounts,
-                                  const float* shell_feat, float skip_log10, unsigned char* keep) {
+cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbatch, const float* w,
+                                  const int* pairlist, int* pairlist_out, int64_t* list_off, int* counts,
+                                  long long* ppcounts, const float* shell_feat, float skip_log10, float fp32_log10,
+                                  unsigned char* keep, unsigned char* hflag) {
   if (nbatch == 0) return cudaSuccess;
-  learned_filter_kernel<<<nbatch, 128, 0, st>>>(a, w, pairlist, list_off, counts, shell_feat, skip_log10, keep);
+  learned_filter_kernel<<<nbatch, 128, 0, st>>>(a, w, pairlist, list_off, counts, shell_feat, skip_log10, fp32_log10,
+                                                keep);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  compact_lists_kernel<<<nbatch * kNumLists, 256, 0, st>>>(pairlist, list_off, counts, keep, a.pairs, ppcounts);
+  reorder_lists_kernel<<<nbatch, 256, 0, st>>>(pairlist, pairlist_out, list_off, counts, keep, a.pairs, ppcounts,
+                                               a.batches, a.mols, hflag);
   return cudaGetLastError();
 }
 

@@ -79,7 +79,7 @@ struct snk_ctx {
   bool have_density = false;
   DevBuf<double> P, ft, sym, Khat, K;
   DevBuf<float2> P2;  // (hi, lo) pairs of P for the double-FP32 GEMM
-  DevBuf<int> counts, list, sfunc, colmap, tickets;
+  DevBuf<int> counts, list, list2, sfunc, colmap, tickets;  // list2: rewrite target of the learned screen
   DevBuf<long long> ppcounts;
   DevBuf<unsigned char> sflag;
   DevBuf<int64_t> list_off, tstart;  // per (batch, list): first list entry, first tile
@@ -354,18 +354,28 @@ int screen_and_plan(snk_ctx* c) {
   c->sargs = sa;
 
   // learned screen on top of the rigorous lists: the MLP skips blocks whose
-  // predicted contribution is below learned_skip; lists are compacted in place
+  // predicted contribution is below learned_skip and, in the mixed form,
+  // moves high-tier blocks predicted below learned_fp32 to the FP32 lists;
+  // the lists are rewritten into the second list buffer, which becomes current
   int64_t learned_skipped = 0;
   if (c->opt.screen == SNK_SCREEN_LEARNED && c->mlp_loaded && tot > 0) {
     SNK_CK(c, c->keep.ensure((size_t)tot));
+    SNK_CK(c, c->list2.ensure((size_t)tot));
     SNK_CK(c, cudaMemsetAsync(c->keep.p, 1, (size_t)tot, st));
-    SNK_CK(c, launch_learned_filter(st, sa, nb, c->mlp_w.p, c->list.p, c->list_off.p, c->counts.p, c->ppcounts.p,
-                                    c->shell_feat.p, (float)c->opt.learned_skip, c->keep.p));
+    const float fp32_log10 = mixed ? (float)c->opt.learned_fp32 : -1e30f;
+    SNK_CK(c, launch_learned_filter(st, sa, nb, c->mlp_w.p, c->list.p, c->list2.p, c->list_off.p, c->counts.p,
+                                    c->ppcounts.p, c->shell_feat.p, (float)c->opt.learned_skip, fp32_log10, c->keep.p,
+                                    c->sflag.p + cmn));
     c->launches_density += 2;
+    std::swap(c->list.p, c->list2.p);
+    std::swap(c->list.n, c->list2.n);
     SNK_CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts.p, sizeof(int) * nbx * kNumLists, cudaMemcpyDeviceToHost,
                               st));
     SNK_CK(c, cudaMemcpyAsync(c->hpp.data(), c->ppcounts.p, sizeof(long long) * nbx * kNumLists,
                               cudaMemcpyDeviceToHost, st));
+    SNK_CK(c, cudaMemcpyAsync(c->hlist_off.data(), c->list_off.p, sizeof(int64_t) * nbx * kNumLists,
+                              cudaMemcpyDeviceToHost, st));
+    SNK_CK(c, cudaMemcpyAsync(hflag.data() + cmn, c->sflag.p + cmn, cmn, cudaMemcpyDeviceToHost, st));
     SNK_CK(c, cudaStreamSynchronize(st));
     int64_t after = 0;
     for (int64_t x = 0; x < (int64_t)nb * kNumLists; ++x) after += c->hcounts[x];
@@ -937,6 +947,7 @@ void snk_options_default(snk_options* o) {
   o->ds_integrals = 0;
   o->fp32_g64 = 0;
   o->fp32_hrr_ds = 0;
+  o->learned_fp32 = -99.0;
   o->graph = 0;
   o->learned_skip = -11.0;
 }

@@ -290,9 +290,14 @@ cudaError_t launch_adam(cudaStream_t st, float* w, const float* g, float* m1, fl
 cudaError_t launch_features(cudaStream_t st, const ScreenArgs& a, const int* pairlist, const int64_t* list_off,
                             const int* counts, const int* sample_batches, const int64_t* sample_off, int n_sample,
                             const float* shell_feat, float* feat);
-cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbatch, const float* w, int* pairlist,
-                                  const int64_t* list_off, int* counts, long long* ppcounts,
-                                  const float* shell_feat, float skip_log10, unsigned char* keep);
+// MLP over every list entry, then the lists rewritten into pairlist_out:
+// entries predicted below skip_log10 dropped, high-tier entries predicted
+// below fp32_log10 moved to the FP32 list of their class; list_off, counts,
+// ppcounts and the high-tier shell flags (hflag, rows at cm_off) updated.
+cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbatch, const float* w,
+                                  const int* pairlist, int* pairlist_out, int64_t* list_off, int* counts,
+                                  long long* ppcounts, const float* shell_feat, float skip_log10, float fp32_log10,
+                                  unsigned char* keep, unsigned char* hflag);
 cudaError_t launch_xmax(cudaStream_t st, const BatchDesc* dbatch, int nbatch, const double* ws, double* xm);
 
 }  // namespace snk

@@ -11,10 +11,12 @@ trained by snk_mlp_train (the library's FP32 forward/backward/Adam kernels).
 
 Calibration: on one more fresh instance, K with the learned screen is
 compared with K of the same form without it (rigorous screen at 1e-10, FP32
-integrals below an estimate of 3e-4, double-FP32 integrals above it and
-double-FP32 GEMMs) for a ladder of
-thresholds; the largest threshold whose max|dK| stays within a fifth of the
-1e-8 tolerance is stored with the weights.
+integrals below an estimate of 3e-4, double-FP32 integrals above it,
+split GEMMs) for a ladder of thresholds: first the skip threshold (the
+largest whose max|dK| stays within a fifth of the 1e-8 tolerance), then, with
+that skip threshold, the tier threshold below which a double-FP32 block moves
+to the FP32 tier (the largest keeping skip and moves together within 0.3 of
+the tolerance).  Both are stored with the weights.
 
     python -m paper_2303_14280_gb300.train_screen [--instances 20] [--out PATH]
 """
@@ -34,6 +36,8 @@ TRAIN_SEED0 = 3000
 TOLERANCE = 1e-8
 THRESHOLDS = (-12.0, -11.5, -11.0, -10.75, -10.5, -10.25, -10.0, -9.75, -9.5)
 BUDGET = 0.2  # share of the tolerance the skipped blocks may use
+FP32_THRESHOLDS = (-6.0, -5.5, -5.0, -4.75, -4.5, -4.25, -4.0, -3.75, -3.5)
+FP32_BUDGET = 0.3  # share of the tolerance skipped and moved blocks may use together
 
 
 def instance(seed, device):
@@ -52,12 +56,18 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--under-weight", type=float, default=8.0)
     ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--calibrate-only", action="store_true",
+                    help="keep the weights of --out and redo the calibration")
     args = ap.parse_args(argv)
 
     import torch
     import paper_2303_14280_gb300 as snk
 
     dev = torch.device("cuda", torch.cuda.current_device())
+    if args.calibrate_only:
+        w, _, meta = snk.trained_screen(args.out)
+        calibrate(snk, w, meta, args, dev)
+        return 0
     feats, labs = [], []
     t0 = time.perf_counter()
     for k in range(args.instances):
@@ -78,38 +88,53 @@ def main(argv=None):
     print(f"{F.shape[0]} blocks collected in {t_collect:.1f} s, trained in {t_train:.1f} s, "
           f"loss {hist[0]:.4g} -> {hist[-1]:.4g}", flush=True)
 
-    # calibration on a held-out instance
+    meta = {"train_seeds": [TRAIN_SEED0, TRAIN_SEED0 + args.instances - 1], "blocks": int(F.shape[0]),
+            "stride": args.stride, "cap": args.cap, "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
+            "under_weight": args.under_weight, "loss_history": [float(x) for x in hist]}
+    calibrate(snk, w, meta, args, dev)
+    return 0
+
+
+def calibrate(snk, w, meta, args, dev):
+    """Skip and tier thresholds on a held-out instance (see the module text)."""
     p = instance(TRAIN_SEED0 + args.instances, dev)
-    form = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="df32", ds_integrals=1)
+    form = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1)
     rig = snk.Engine(p.basis, p.grid, **form)
     rig.set_density(p.P)
     K0 = rig.build_K()
-    kept0 = rig.stats()["pairs_kept"]
+    s0 = rig.stats()
     rig.close()
-    table, chosen = [], THRESHOLDS[0]
-    for t in THRESHOLDS:
-        e = snk.Engine(p.basis, p.grid, screen="learned", learned_skip=t, **form)
+
+    def run(skip, fp32):
+        e = snk.Engine(p.basis, p.grid, screen="learned", learned_skip=skip, learned_fp32=fp32, **form)
         e.screen_load(w)
         e.set_density(p.P)
         K1 = e.build_K()
         s = e.stats()
         e.close()
-        err = float(np.max(np.abs(K1 - K0)))
-        table.append({"threshold": t, "max_abs_dK": err, "skipped": int(s["pairs_learned_skipped"]),
-                      "kept_rigorous": int(kept0)})
+        return {"skip": skip, "fp32": fp32, "max_abs_dK": float(np.max(np.abs(K1 - K0))),
+                "skipped": int(s["pairs_learned_skipped"]), "fp32_pairs": int(s["pairs_kept_fp32"]),
+                "kept_rigorous": int(s0["pairs_kept"]), "fp32_pairs_rigorous": int(s0["pairs_kept_fp32"])}
+
+    table, chosen = [], THRESHOLDS[0]
+    for t in THRESHOLDS:
+        table.append(run(t, -99.0))
         print(json.dumps(table[-1]), flush=True)
-        if err <= BUDGET * TOLERANCE:
-            chosen = t
-        else:
+        if table[-1]["max_abs_dK"] > BUDGET * TOLERANCE:
             break
-    meta = {"train_seeds": [TRAIN_SEED0, TRAIN_SEED0 + args.instances - 1],
-            "holdout_seed": TRAIN_SEED0 + args.instances, "blocks": int(F.shape[0]), "stride": args.stride,
-            "cap": args.cap, "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
-            "under_weight": args.under_weight, "loss_history": [float(x) for x in hist],
-            "calibration": table, "tolerance": TOLERANCE, "budget": BUDGET, "form": form}
+        chosen = t
+    table32, chosen32 = [], -99.0
+    for t in FP32_THRESHOLDS:
+        table32.append(run(chosen, t))
+        print(json.dumps(table32[-1]), flush=True)
+        if table32[-1]["max_abs_dK"] > FP32_BUDGET * TOLERANCE:
+            break
+        chosen32 = t
+    meta.update(holdout_seed=TRAIN_SEED0 + args.instances, calibration=table, calibration_fp32=table32,
+                tolerance=TOLERANCE, budget=BUDGET, fp32_budget=FP32_BUDGET, form=form,
+                fp32_threshold=chosen32)
     np.savez(args.out, weights=w, threshold=np.float32(chosen), meta=json.dumps(meta))
-    print(f"threshold {chosen}; wrote {args.out}", flush=True)
-    return 0
+    print(f"skip threshold {chosen}, tier threshold {chosen32}; wrote {args.out}", flush=True)
 
 
 if __name__ == "__main__":

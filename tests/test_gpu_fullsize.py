@@ -59,9 +59,9 @@ def test_cluster256_mixed_form_matches_oracle_entries():
         pytest.skip("no CUDA device")
     import paper_2303_14280_gb300 as snk
     p = synth.cluster256(device="cuda")
-    w, thr, _ = snk.trained_screen()
+    w, thr, meta = snk.trained_screen()
     eng = snk.Engine(p.basis, p.grid, eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1,
-                     screen="learned", learned_skip=thr)
+                     screen="learned", learned_skip=thr, learned_fp32=float(meta.get("fp32_threshold", -99.0)))
     eng.screen_load(w)
     eng.set_density(p.P)
     K = eng.build_K()

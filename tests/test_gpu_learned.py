@@ -98,3 +98,30 @@ def test_learned_screen_beats_rigorous_screen_within_tolerance(snk):
     assert s1["pairs_kept"] == s0["pairs_kept"] - s1["pairs_learned_skipped"]
     assert np.max(np.abs(K0 - Kref)) <= 1e-8
     assert np.max(np.abs(K1 - Kref)) <= 1e-8
+
+
+def test_learned_tier_routing(snk):
+    """With learned_fp32 the trained screen also moves high-tier blocks whose
+    predicted contribution is small to the FP32 tier: fewer double-FP32
+    blocks, the same kept blocks, K within 1e-8 of the oracle.  The molecule is
+    smaller and its grid coarser than the training clusters, so the threshold
+    is a decade below the calibrated one."""
+    w, thr, _ = snk.trained_screen()
+    p = _cluster(3200)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    form = dict(eps=1e-10, batch_max=400, precision="mixed", fp32_bound=3e-4, ds_integrals=1, gemm="split",
+                screen="learned", learned_skip=thr)
+    out = {}
+    for lf in (-99.0, -5.0):
+        e = snk.Engine(p.basis, p.grid, learned_fp32=lf, **form)
+        e.screen_load(w)
+        e.set_density(p.P)
+        out[lf] = (e.build_K(), e.stats())
+        e.close()
+    (K0, s0), (K1, s1) = out[-99.0], out[-5.0]
+    assert s1["pairs_kept"] == s0["pairs_kept"]
+    assert s1["pairs_kept_fp32"] > s0["pairs_kept_fp32"]
+    assert s1["gemm_flops_hi"] <= s0["gemm_flops_hi"]
+    assert np.max(np.abs(K0 - Kref)) <= 1e-8
+    assert np.max(np.abs(K1 - Kref)) <= 1e-8
+    assert np.max(np.abs(K1 - K1.T)) == 0.0
