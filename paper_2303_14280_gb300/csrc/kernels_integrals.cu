@@ -214,6 +214,7 @@ template <int LA, int LB, bool HRR_DS>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
+  constexpr int kStage = 16;  // primitive records per pair staged per warp (64 float4)
   extern __shared__ __align__(16) float s_tabf[];
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
   for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
@@ -221,8 +222,12 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   // columns and R_a - R_b
   __shared__ int s_ppo[kMaxRun], s_ppn[kMaxRun], s_sa[kMaxRun], s_sb[kMaxRun], s_ca[kMaxRun], s_cb[kMaxRun];
   __shared__ float2 s_ab[kMaxRun][3];  // (hi, lo)
+  // per warp, double-buffered: the current pair's primitive records; the next
+  // pair's are loaded (coalesced, one request per 128 B) while this one computes
+  __shared__ float4 s_pr[kIntThreads / 32][2][kStage * 4];
   __shared__ int s_tile;
   __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1);
     __syncthreads();
@@ -249,9 +254,14 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     }
     __syncthreads();
     const int i = tile.i0 + threadIdx.x;
-    if (i >= bd.q || nrun <= 0) continue;
-    const ds cx = ds_from(a.xyz[3 * (bd.p0 + i)]), cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]),
-             cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
+    const bool active = i < bd.q;  // inactive lanes still stage records for their warp
+    if (nrun <= 0 || __all_sync(0xffffffffu, !active)) continue;
+    ds cx = ds_make(0.f, 0.f), cy = cx, cz = cx;
+    if (active) {
+      cx = ds_from(a.xyz[3 * (bd.p0 + i)]);
+      cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]);
+      cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
+    }
     const int64_t ldq = bd.ldq;
     const float* F = a.ws32 + bd.foff32 + i;
     float* G = a.ws32 + bd.goff32 + i;
@@ -263,78 +273,106 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       else
         atomicAdd(G + col * ldq, v);
     };
+    {  // the first pair's records
+      const int n4 = min(s_ppn[0], kStage) * 4;
+      const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 4;
+      for (int e = lane; e < n4; e += 32) s_pr[wid][0][e] = src[e];
+    }
+    __syncwarp();
     float ga[NA], fa[NA], fn[NB];
     int cur = -1, cola = 0;
 #pragma unroll
-    for (int v = 0; v < NB; ++v) fn[v] = F[(s_cb[0] + v) * ldq];
+    for (int v = 0; v < NB; ++v) fn[v] = active ? F[(s_cb[0] + v) * ldq] : 0.f;
     for (int r = 0; r < nrun; ++r) {
+      const float4* rec = s_pr[wid][r & 1];
+      float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
+      int n4n = 0;
+      if (r + 1 < nrun) {  // the next pair's records are in flight while this pair computes
+        n4n = min(s_ppn[r + 1], kStage) * 4;
+        const float4* src = a.prims_f32 + (size_t)s_ppo[r + 1] * 4;
+        if (lane < n4n) pre0 = src[lane];
+        if (lane + 32 < n4n) pre1 = src[lane + 32];
+      }
       float fb[NB];
 #pragma unroll
       for (int v = 0; v < NB; ++v) fb[v] = fn[v];
-      if (r + 1 < nrun) {  // the next pair's F_b is in flight while this pair computes
+      if (active && r + 1 < nrun) {
         const int cn = s_cb[r + 1];
 #pragma unroll
         for (int v = 0; v < NB; ++v) fn[v] = F[(cn + v) * ldq];
       }
       const int sa = s_sa[r];
-      if (sa != cur) {
-        if (cur >= 0) {
+      if (active) {
+        if (sa != cur) {
+          if (cur >= 0) {
 #pragma unroll
-          for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
+            for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
+          }
+          cur = sa;
+          cola = s_ca[r];
+#pragma unroll
+          for (int u = 0; u < NA; ++u) {
+            ga[u] = 0.f;
+            fa[u] = F[(cola + u) * ldq];
+          }
         }
-        cur = sa;
-        cola = s_ca[r];
+        float acc[C::NACC];
 #pragma unroll
-        for (int u = 0; u < NA; ++u) {
-          ga[u] = 0.f;
-          fa[u] = F[(cola + u) * ldq];
+        for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
+        auto prim = [&](float4 r0, float4 r1, float4 r2, float4 r3) {
+          const float PCx = (r0.y - cx.hi) + (r1.x - cx.lo);
+          const float PCy = (r0.z - cy.hi) + (r1.y - cy.lo);
+          const float PCz = (r0.w - cz.hi) + (r1.z - cz.lo);
+          const float T = r0.x * fmaf(PCx, PCx, fmaf(PCy, PCy, PCz * PCz));
+          float S[C::L + 1];
+          boys_seeds_f32<C::L>(T, r1.w, r2.w, s_tabf, S);
+          C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
+        };
+        const int ppn = s_ppn[r];
+        if (ppn <= kStage) {
+          for (int q = 0; q < ppn; ++q) prim(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
+        } else {  // more primitive pairs than staged: read them from global memory
+          const float4* pp = a.prims_f32 + (size_t)s_ppo[r] * 4;
+          for (int q = 0; q < ppn; ++q) prim(pp[4 * q], pp[4 * q + 1], pp[4 * q + 2], pp[4 * q + 3]);
+        }
+        float xi[NA * NB];
+        if (HRR_DS && LB > 0) {
+          ds accd[C::NACC], xid[NA * NB];
+#pragma unroll
+          for (int u = 0; u < C::NACC; ++u) accd[u] = ds_make(acc[u], 0.f);
+          C::hrr(accd, ds_make(s_ab[r][0].x, s_ab[r][0].y), ds_make(s_ab[r][1].x, s_ab[r][1].y),
+                 ds_make(s_ab[r][2].x, s_ab[r][2].y), xid);
+#pragma unroll
+          for (int u = 0; u < NA * NB; ++u) xi[u] = __fadd_rn(xid[u].hi, xid[u].lo);
+        } else {
+          C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
+        }
+#pragma unroll
+        for (int u = 0; u < NA; ++u)
+#pragma unroll
+          for (int v = 0; v < NB; ++v) ga[u] = fmaf(xi[u * NB + v], fb[v], ga[u]);
+        if (sa != s_sb[r]) {
+          const int colb = s_cb[r];
+#pragma unroll
+          for (int v = 0; v < NB; ++v) {
+            float g = 0.f;
+#pragma unroll
+            for (int u = 0; u < NA; ++u) g = fmaf(xi[u * NB + v], fa[u], g);
+            gadd(colb + v, g);
+          }
         }
       }
-      float acc[C::NACC];
-#pragma unroll
-      for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
-      const int ppo = s_ppo[r], ppn = s_ppn[r];
-#pragma unroll 2
-      for (int q = 0; q < ppn; ++q) {
-        const float4* pp = a.prims_f32 + (size_t)(ppo + q) * 4;
-        const float4 r0 = pp[0], r1 = pp[1], r2 = pp[2], r3 = pp[3];
-        const float PCx = (r0.y - cx.hi) + (r1.x - cx.lo);
-        const float PCy = (r0.z - cy.hi) + (r1.y - cy.lo);
-        const float PCz = (r0.w - cz.hi) + (r1.z - cz.lo);
-        const float T = r0.x * fmaf(PCx, PCx, fmaf(PCy, PCy, PCz * PCz));
-        float S[C::L + 1];
-        boys_seeds_f32<C::L>(T, r1.w, r2.w, s_tabf, S);
-        C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
-      }
-      float xi[NA * NB];
-      if (HRR_DS && LB > 0) {
-        ds accd[C::NACC], xid[NA * NB];
-#pragma unroll
-        for (int u = 0; u < C::NACC; ++u) accd[u] = ds_make(acc[u], 0.f);
-        C::hrr(accd, ds_make(s_ab[r][0].x, s_ab[r][0].y), ds_make(s_ab[r][1].x, s_ab[r][1].y),
-               ds_make(s_ab[r][2].x, s_ab[r][2].y), xid);
-#pragma unroll
-        for (int u = 0; u < NA * NB; ++u) xi[u] = __fadd_rn(xid[u].hi, xid[u].lo);
-      } else {
-        C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
-      }
-#pragma unroll
-      for (int u = 0; u < NA; ++u)
-#pragma unroll
-        for (int v = 0; v < NB; ++v) ga[u] = fmaf(xi[u * NB + v], fb[v], ga[u]);
-      if (sa != s_sb[r]) {
-        const int colb = s_cb[r];
-#pragma unroll
-        for (int v = 0; v < NB; ++v) {
-          float g = 0.f;
-#pragma unroll
-          for (int u = 0; u < NA; ++u) g = fmaf(xi[u * NB + v], fa[u], g);
-          gadd(colb + v, g);
-        }
-      }
+      // every lane is past its reads of the other buffer (the previous
+      // iteration's closing __syncwarp), so it can take the next records
+      float4* nxt = s_pr[wid][(r + 1) & 1];
+      if (lane < n4n) nxt[lane] = pre0;
+      if (lane + 32 < n4n) nxt[lane + 32] = pre1;
+      __syncwarp();
     }
+    if (active) {
 #pragma unroll
-    for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
+      for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
+    }
   }
 }
 
