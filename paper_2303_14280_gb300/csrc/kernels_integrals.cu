@@ -215,6 +215,10 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
   constexpr int kStage = 16;  // primitive records per pair staged per warp (64 float4)
+  // staging pays for the light classes, whose few FP32 operations per
+  // primitive cannot cover the record loads; heavier classes read the records
+  // directly (fewer registers, more resident warps)
+  constexpr bool STAGE = C::L <= 1;
   extern __shared__ __align__(16) float s_tabf[];
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
   for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   __shared__ float2 s_ab[kMaxRun][3];  // (hi, lo)
   // per warp, double-buffered: the current pair's primitive records; the next
   // pair's are loaded (coalesced, one request per 128 B) while this one computes
-  __shared__ float4 s_pr[kIntThreads / 32][2][kStage * 4];
+  __shared__ float4 s_pr[STAGE ? kIntThreads / 32 : 1][2][STAGE ? kStage * 4 : 1];
   __shared__ int s_tile;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -273,21 +277,21 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       else
         atomicAdd(G + col * ldq, v);
     };
-    {  // the first pair's records
+    if (STAGE) {  // the first pair's records
       const int n4 = min(s_ppn[0], kStage) * 4;
       const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 4;
       for (int e = lane; e < n4; e += 32) s_pr[wid][0][e] = src[e];
+      __syncwarp();
     }
-    __syncwarp();
     float ga[NA], fa[NA], fn[NB];
     int cur = -1, cola = 0;
 #pragma unroll
     for (int v = 0; v < NB; ++v) fn[v] = active ? F[(s_cb[0] + v) * ldq] : 0.f;
     for (int r = 0; r < nrun; ++r) {
-      const float4* rec = s_pr[wid][r & 1];
+      const float4* rec = s_pr[STAGE ? wid : 0][r & 1];
       float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
       int n4n = 0;
-      if (r + 1 < nrun) {  // the next pair's records are in flight while this pair computes
+      if (STAGE && r + 1 < nrun) {  // the next pair's records are in flight while this pair computes
         n4n = min(s_ppn[r + 1], kStage) * 4;
         const float4* src = a.prims_f32 + (size_t)s_ppo[r + 1] * 4;
         if (lane < n4n) pre0 = src[lane];
@@ -329,9 +333,9 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
           C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
         };
         const int ppn = s_ppn[r];
-        if (ppn <= kStage) {
+        if (STAGE && ppn <= kStage) {
           for (int q = 0; q < ppn; ++q) prim(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
-        } else {  // more primitive pairs than staged: read them from global memory
+        } else {  // heavier classes, or more primitive pairs than staged: global memory
           const float4* pp = a.prims_f32 + (size_t)s_ppo[r] * 4;
           for (int q = 0; q < ppn; ++q) prim(pp[4 * q], pp[4 * q + 1], pp[4 * q + 2], pp[4 * q + 3]);
         }
@@ -364,10 +368,12 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       }
       // every lane is past its reads of the other buffer (the previous
       // iteration's closing __syncwarp), so it can take the next records
-      float4* nxt = s_pr[wid][(r + 1) & 1];
-      if (lane < n4n) nxt[lane] = pre0;
-      if (lane + 32 < n4n) nxt[lane + 32] = pre1;
-      __syncwarp();
+      if (STAGE) {
+        float4* nxt = s_pr[wid][(r + 1) & 1];
+        if (lane < n4n) nxt[lane] = pre0;
+        if (lane + 32 < n4n) nxt[lane + 32] = pre1;
+        __syncwarp();
+      }
     }
     if (active) {
 #pragma unroll
