@@ -202,6 +202,21 @@ int snk_build_K_device(snk_ctx *ctx, double *dK);
 /* Same into one host buffer per molecule. */
 int snk_build_K_batch(snk_ctx *ctx, double *const *K);
 
+/* Several densities of one molecule in one build (for example the alpha and
+ * beta densities of an unrestricted calculation): K_d = sn-K of P_d for each
+ * d (Eqs. fmat, gmat, usym_k, sn_k with D = P_d), from one evaluation of every
+ * 3c-CP block contracted with every F_d (Eq. gmat).  The screen of Eq.
+ * (sp_set) runs once on sum_d |P_d|, an upper bound of each density's
+ * estimates, so the kept blocks serve all densities.  n_dens in
+ * 1..SNK_MAX_DENSITIES; P[d] host, N_b x N_b row-major, each symmetric
+ * (SNK_ERR_NOT_SYMMETRIC otherwise).  Handles made by snk_create only
+ * (SNK_ERR_UNSUPPORTED for several molecules); snk_build_K_multi writes K[d]
+ * (host) for every loaded density.  snk_set_density loads one density again;
+ * graph capture (options.graph) applies to one density only. */
+enum { SNK_MAX_DENSITIES = 2 };
+int snk_set_density_multi(snk_ctx *ctx, int32_t n_dens, const double *const *P);
+int snk_build_K_multi(snk_ctx *ctx, double *const *K);
+
 /* Autotuner of the integral kernels (after snk_set_density): for every
  * (class, precision) list, times the kernel on the batches of the last
  * workspace chunk for runs of 2..128 shell pairs per 128-point tile and keeps

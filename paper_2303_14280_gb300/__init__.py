@@ -45,8 +45,10 @@ SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molec
            "snk_build_K_device", "snk_build_K_batch", "snk_autotune", "snk_set_stream", "snk_get_stats",
            "snk_n_functions", "snk_last_error", "snk_status_string", "snk_destroy", "snk_debug_boys",
            "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc",
-           "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad"]
+           "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad",
+           "snk_set_density_multi", "snk_build_K_multi"]
 MLP_FEATURES, MLP_WEIGHTS = 16, 9473
+MAX_DENSITIES = 2
 
 
 class SnkError(RuntimeError):
@@ -123,6 +125,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
                          "snk_set_density_batch", "snk_build_K_batch"):
                 getattr(L, name).argtypes = [_P, _P]
             L.snk_autotune.argtypes = [_P, _I32]
+            L.snk_set_density_multi.argtypes = [_P, ctypes.c_int32, _P]
+            L.snk_build_K_multi.argtypes = [_P, _P]
             L.snk_set_stream.argtypes = [_P, _P]
             L.snk_get_stats.argtypes = [_P, ctypes.POINTER(SnkStats)]
             L.snk_n_functions.argtypes = [_P]
@@ -290,6 +294,7 @@ class Engine:
         self.nfs = [int(L.snk_molecule_functions(h, m)) for m in range(self.n_mol)]
         self.nf = int(L.snk_n_functions(h))
         self.packed = sum(n * n for n in self.nfs)
+        self.n_dens = 1
         self._stream = None
 
     # -- plumbing ---------------------------------------------------------
@@ -318,8 +323,17 @@ class Engine:
     # -- the sn-K build ---------------------------------------------------
     def set_density(self, P):
         """P: NumPy array (N_b x N_b, or the packed blocks), a list of NumPy
-        arrays (one per molecule), or a torch CUDA tensor (packed), float64,
-        symmetric."""
+        arrays (one per molecule of a batch handle; for a single-molecule
+        handle, up to MAX_DENSITIES densities built together), or a torch
+        CUDA tensor (packed), float64, symmetric."""
+        self.n_dens = 1
+        if isinstance(P, (list, tuple)) and not self.batched:
+            arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in P]
+            assert all(a.size == self.packed for a in arrs)
+            ptrs = (_P * len(arrs))(*[a.ctypes.data for a in arrs])
+            self._check(lib().snk_set_density_multi(self._h, len(arrs), ptrs), "snk_set_density_multi")
+            self.n_dens = len(arrs)
+            return
         if isinstance(P, (list, tuple)):
             arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in P]
             assert [a.shape for a in arrs] == [(n, n) for n in self.nfs]
@@ -338,6 +352,11 @@ class Engine:
         """Host K (NumPy; a list of per-molecule arrays for a batch) by default;
         with out = a CUDA tensor (packed blocks) the build writes there and
         returns it once the work is enqueued on the engine's stream."""
+        if self.n_dens > 1:
+            Ks = [np.empty((self.nf, self.nf)) for _ in range(self.n_dens)]
+            ptrs = (_P * len(Ks))(*[k.ctypes.data for k in Ks])
+            self._check(lib().snk_build_K_multi(self._h, ptrs), "snk_build_K_multi")
+            return Ks
         if out is not None and _is_cuda_tensor(out):
             assert out.element_size() == 8 and out.is_contiguous() and out.numel() == self.packed
             self._check(lib().snk_build_K_device(self._h, _P(out.data_ptr())), "snk_build_K_device")

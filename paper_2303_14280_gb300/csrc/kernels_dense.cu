@@ -628,14 +628,16 @@ template <int MODE>
 __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THREADS, MODE >= 2 ? 2 : 3)
     fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P, const float2* __restrict__ P2,
                  const int* __restrict__ xfunc, const int* __restrict__ sfunc, const double* __restrict__ fcomp,
-                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32, int part) {
+                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32, int part,
+                 int dens) {
   const BatchDesc bd = batches[blockIdx.z];
   int c0, c1;
   part_range(bd, part, c0, c1);
   const int m0 = blockIdx.x * TM, n0 = c0 + blockIdx.y * TN;
   if (m0 >= bd.ldq || n0 >= c1) return;
-  double* F = ws + bd.foff;
-  float* F32 = ws32 ? ws32 + bd.foff32 : nullptr;
+  const int64_t dofs = (int64_t)dens * bd.ldq * bd.nS;  // density d's F / G block
+  double* F = ws + bd.foff + dofs;
+  float* F32 = ws32 ? ws32 + bd.foff32 + dofs : nullptr;
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   const double* fc = fcomp + bd.mf0;
@@ -674,19 +676,20 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THR
 template <int MODE>
 __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THREADS, MODE >= 2 ? 2 : 3)
     kgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc, const int* __restrict__ sfunc,
-                 const double* __restrict__ ws, double* __restrict__ Khat, int part) {
+                 const double* __restrict__ ws, double* __restrict__ Khat, int part, int dens) {
   const BatchDesc bd = batches[blockIdx.z];
   int r0, r1;
   part_range(bd, part, r0, r1);
   const int m0 = r0 + blockIdx.x * TM, n0 = blockIdx.y * TN;
   if (m0 >= r1 || n0 >= bd.nB) return;
+  const int64_t dofs = (int64_t)dens * bd.ldq * bd.nS;  // density d's G block
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   double* Km = Khat + bd.pk_off;
   auto st = [&](int m, int n, double c) { atomicAdd(&Km[(int64_t)sf[m] * bd.nfm + xf[n]], c); };
   if (MODE == 2 || MODE == 3) {
     const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
-    const float2* G2 = reinterpret_cast<const float2*>(ws + bd.goff);
+    const float2* G2 = reinterpret_cast<const float2*>(ws + bd.goff) + dofs;
     auto la = [&](int m, int k) { return G2[(int64_t)m * bd.ldq + k]; };
     auto lb = [&](int k, int n) { return X2[(int64_t)n * bd.ldq + k]; };
     if (MODE == 2) {
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THR
     }
   } else {
     const double* X = ws + bd.xoff;
-    const double* G = ws + bd.goff;
+    const double* G = ws + bd.goff + dofs;
     auto la = [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; };
     auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
     if (MODE == 1)
@@ -730,6 +733,15 @@ __global__ void gen_tiles_kernel(const BatchDesc* __restrict__ batches, const in
     t.k1 = base + min(n, (r + 1) * run);
     t.i0 = sl * kPointTile;
     out[u] = t;
+  }
+}
+
+// out[e] = sum_d |P_d[e]|: the screen's single bound for several densities.
+__global__ void abs_sum_kernel(const double* __restrict__ P, int n_dens, int64_t n, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int d = 0; d < n_dens; ++d) v += fabs(P[d * n + e]);
+    out[e] = v;
   }
 }
 
@@ -834,27 +846,28 @@ cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc, const double* fcomp,
-                         const double* w, double* ws, float* ws32, int mode, int part) {
+                         const double* w, double* ws, float* ws32, int mode, int part, int dens) {
   if (nbatch == 0 || max_ldq == 0 || max_nS == 0) return cudaSuccess;
   dim3 grid((max_ldq + TM - 1) / TM, (max_nS + TN - 1) / TN, nbatch);
   switch (mode) {
-    case 1: fgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part); break;
-    case 2: fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part); break;
-    case 3: fgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part); break;
-    default: fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part);
+    case 1: fgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens); break;
+    case 2: fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens); break;
+    case 3: fgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens); break;
+    default: fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part) {
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part,
+                         int dens) {
   if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
   dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
   switch (mode) {
-    case 1: kgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part); break;
-    case 2: kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part); break;
-    case 3: kgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part); break;
-    default: kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part);
+    case 1: kgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens); break;
+    case 2: kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens); break;
+    case 3: kgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens); break;
+    default: kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens);
   }
   return cudaGetLastError();
 }
@@ -863,6 +876,13 @@ cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batch
                              const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles) {
   if (nbatch == 0) return cudaSuccess;
   gen_tiles_kernel<<<dim3(nbatch, kNumLists), 256, 0, st>>>(batches, counts, list_off, tstart, runs, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_abs_sum(cudaStream_t st, const double* P, int n_dens, int64_t n, double* out) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  abs_sum_kernel<<<grid, 256, 0, st>>>(P, n_dens, n, out);
   return cudaGetLastError();
 }
 

@@ -94,7 +94,9 @@ __device__ __forceinline__ void pair_xi(const PairHdr& h, const PrimPair* __rest
   C::hrr(acc, h.ABx, h.ABy, h.ABz, xi);
 }
 
-template <int LA, int LB>
+// ND densities share every Xi block: F and G of density d sit d ldq nS
+// doubles after the batch's first block.
+template <int LA, int LB, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
@@ -113,52 +115,64 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
     const BatchDesc bd = a.batches[tile.batch];
     const int i = tile.i0 + threadIdx.x;
     if (i >= bd.q) continue;
-    const int64_t ldq = bd.ldq;
+    const int64_t ldq = bd.ldq, dstr = (int64_t)bd.ldq * bd.nS;
     const double cx = a.xyz[3 * (bd.p0 + i)], cy = a.xyz[3 * (bd.p0 + i) + 1], cz = a.xyz[3 * (bd.p0 + i) + 2];
     const double* F = a.ws + bd.foff + i;
     double* G = a.ws + bd.goff + i;
     const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
-    double ga[NA], fa[NA];
+    double ga[ND][NA], fa[ND][NA];
     int cur = -1, cola = 0;
     for (int k = tile.k0; k < tile.k1; ++k) {
       const PairHdr h = a.pairs[a.pairlist[k]];
       if (h.sa != cur) {
         if (cur >= 0) {
 #pragma unroll
-          for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
+          for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int u = 0; u < NA; ++u) atomicAdd(G + d * dstr + (cola + u) * ldq, ga[d][u]);
         }
         cur = h.sa;
         cola = cmap[cur];
 #pragma unroll
-        for (int u = 0; u < NA; ++u) {
-          ga[u] = 0.0;
-          fa[u] = F[(cola + u) * ldq];
-        }
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+          for (int u = 0; u < NA; ++u) {
+            ga[d][u] = 0.0;
+            fa[d][u] = F[d * dstr + (cola + u) * ldq];
+          }
       }
       const int colb = cmap[h.sb];
       if (cola < 0 || colb < 0) continue;  // cannot happen: the screen marks both shells of a kept pair
-      double fb[NB];
+      double fb[ND][NB];
 #pragma unroll
-      for (int v = 0; v < NB; ++v) fb[v] = F[(colb + v) * ldq];
+      for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int v = 0; v < NB; ++v) fb[d][v] = F[d * dstr + (colb + v) * ldq];
       double xi[NA * NB];
       pair_xi<LA, LB>(h, a.prims, s_tab, cx, cy, cz, xi);
 #pragma unroll
-      for (int u = 0; u < NA; ++u)
+      for (int d = 0; d < ND; ++d)
 #pragma unroll
-        for (int v = 0; v < NB; ++v) ga[u] = fma(xi[u * NB + v], fb[v], ga[u]);
+        for (int u = 0; u < NA; ++u)
+#pragma unroll
+          for (int v = 0; v < NB; ++v) ga[d][u] = fma(xi[u * NB + v], fb[d][v], ga[d][u]);
       if (h.sa != h.sb) {
 #pragma unroll
-        for (int v = 0; v < NB; ++v) {
-          double g = 0.0;
+        for (int d = 0; d < ND; ++d)
 #pragma unroll
-          for (int u = 0; u < NA; ++u) g = fma(xi[u * NB + v], fa[u], g);
-          atomicAdd(G + (colb + v) * ldq, g);
-        }
+          for (int v = 0; v < NB; ++v) {
+            double g = 0.0;
+#pragma unroll
+            for (int u = 0; u < NA; ++u) g = fma(xi[u * NB + v], fa[d][u], g);
+            atomicAdd(G + d * dstr + (colb + v) * ldq, g);
+          }
       }
     }
     if (cur >= 0) {
 #pragma unroll
-      for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ga[u]);
+      for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int u = 0; u < NA; ++u) atomicAdd(G + d * dstr + (cola + u) * ldq, ga[d][u]);
     }
   }
 }
@@ -210,7 +224,7 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
 // no barrier per pair) with the product centre split into hi + lo floats, and
 // P - r_i is formed as (P_hi - r_hi) + (P_lo - r_lo) so that it is accurate to
 // FP32 relative to |P - r_i| however far the molecule sits from the origin.
-template <int LA, int LB, bool HRR_DS>
+template <int LA, int LB, bool HRR_DS, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
@@ -266,16 +280,16 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]);
       cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
     }
-    const int64_t ldq = bd.ldq;
+    const int64_t ldq = bd.ldq, dstr = (int64_t)bd.ldq * bd.nS;  // density d's F / G: + d dstr
     const float* F = a.ws32 + bd.foff32 + i;
     float* G = a.ws32 + bd.goff32 + i;
     double* G64 = a.ws + bd.goff + i;
     const bool g64 = a.f32_g64 != 0;
-    auto gadd = [&](int col, float v) {
+    auto gadd = [&](int d, int col, float v) {
       if (g64)
-        atomicAdd(G64 + col * ldq, (double)v);
+        atomicAdd(G64 + d * dstr + col * ldq, (double)v);
       else
-        atomicAdd(G + col * ldq, v);
+        atomicAdd(G + d * dstr + col * ldq, v);
     };
     if (STAGE) {  // the first pair's records
       const int n4 = min(s_ppn[0], kStage) * 4;
@@ -283,10 +297,12 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       for (int e = lane; e < n4; e += 32) s_pr[wid][0][e] = src[e];
       __syncwarp();
     }
-    float ga[NA], fa[NA], fn[NB];
+    float ga[ND][NA], fa[ND][NA], fn[ND][NB];
     int cur = -1, cola = 0;
 #pragma unroll
-    for (int v = 0; v < NB; ++v) fn[v] = active ? F[(s_cb[0] + v) * ldq] : 0.f;
+    for (int d = 0; d < ND; ++d)
+#pragma unroll
+      for (int v = 0; v < NB; ++v) fn[d][v] = active ? F[d * dstr + (s_cb[0] + v) * ldq] : 0.f;
     for (int r = 0; r < nrun; ++r) {
       const float4* rec = s_pr[STAGE ? wid : 0][r & 1];
       float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
@@ -297,28 +313,36 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         if (lane < n4n) pre0 = src[lane];
         if (lane + 32 < n4n) pre1 = src[lane + 32];
       }
-      float fb[NB];
+      float fb[ND][NB];
 #pragma unroll
-      for (int v = 0; v < NB; ++v) fb[v] = fn[v];
+      for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int v = 0; v < NB; ++v) fb[d][v] = fn[d][v];
       if (active && r + 1 < nrun) {
         const int cn = s_cb[r + 1];
 #pragma unroll
-        for (int v = 0; v < NB; ++v) fn[v] = F[(cn + v) * ldq];
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+          for (int v = 0; v < NB; ++v) fn[d][v] = F[d * dstr + (cn + v) * ldq];
       }
       const int sa = s_sa[r];
       if (active) {
         if (sa != cur) {
           if (cur >= 0) {
 #pragma unroll
-            for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
+            for (int d = 0; d < ND; ++d)
+#pragma unroll
+              for (int u = 0; u < NA; ++u) gadd(d, cola + u, ga[d][u]);
           }
           cur = sa;
           cola = s_ca[r];
 #pragma unroll
-          for (int u = 0; u < NA; ++u) {
-            ga[u] = 0.f;
-            fa[u] = F[(cola + u) * ldq];
-          }
+          for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int u = 0; u < NA; ++u) {
+              ga[d][u] = 0.f;
+              fa[d][u] = F[d * dstr + (cola + u) * ldq];
+            }
         }
         float acc[C::NACC];
 #pragma unroll
@@ -352,18 +376,22 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
           C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
         }
 #pragma unroll
-        for (int u = 0; u < NA; ++u)
+        for (int d = 0; d < ND; ++d)
 #pragma unroll
-          for (int v = 0; v < NB; ++v) ga[u] = fmaf(xi[u * NB + v], fb[v], ga[u]);
+          for (int u = 0; u < NA; ++u)
+#pragma unroll
+            for (int v = 0; v < NB; ++v) ga[d][u] = fmaf(xi[u * NB + v], fb[d][v], ga[d][u]);
         if (sa != s_sb[r]) {
           const int colb = s_cb[r];
 #pragma unroll
-          for (int v = 0; v < NB; ++v) {
-            float g = 0.f;
+          for (int d = 0; d < ND; ++d)
 #pragma unroll
-            for (int u = 0; u < NA; ++u) g = fmaf(xi[u * NB + v], fa[u], g);
-            gadd(colb + v, g);
-          }
+            for (int v = 0; v < NB; ++v) {
+              float g = 0.f;
+#pragma unroll
+              for (int u = 0; u < NA; ++u) g = fmaf(xi[u * NB + v], fa[d][u], g);
+              gadd(d, colb + v, g);
+            }
         }
       }
       // every lane is past its reads of the other buffer (the previous
@@ -377,7 +405,9 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     }
     if (active) {
 #pragma unroll
-      for (int u = 0; u < NA; ++u) gadd(cola + u, ga[u]);
+      for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int u = 0; u < NA; ++u) gadd(d, cola + u, ga[d][u]);
     }
   }
 }
@@ -465,7 +495,7 @@ __device__ __forceinline__ void pair_xi_ds(const PairHdr& h, const float2* __res
 // The FP64 lists of the mixed form in ds arithmetic: same tiles, tickets,
 // contraction and FP64 G atomics as integral_kernel; F is read in FP64 and
 // split, each G update is rounded to FP64 once.
-template <int LA, int LB>
+template <int LA, int LB, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_ds(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
@@ -484,13 +514,13 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_ds(IntegralArgs a
     const BatchDesc bd = a.batches[tile.batch];
     const int i = tile.i0 + threadIdx.x;
     if (i >= bd.q) continue;
-    const int64_t ldq = bd.ldq;
+    const int64_t ldq = bd.ldq, dstr = (int64_t)bd.ldq * bd.nS;
     const ds cx = ds_from(a.xyz[3 * (bd.p0 + i)]), cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]),
              cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
     const double* F = a.ws + bd.foff + i;
     double* G = a.ws + bd.goff + i;
     const int* cmap = a.colmap + bd.cm_off - bd.ms0;
-    ds ga[NA], fa[NA];
+    ds ga[ND][NA], fa[ND][NA];
     int cur = -1, cola = 0;
     for (int k = tile.k0; k < tile.k1; ++k) {
       const int p = a.pairlist[k];
@@ -498,40 +528,52 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_ds(IntegralArgs a
       if (h.sa != cur) {
         if (cur >= 0) {
 #pragma unroll
-          for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ds_to(ga[u]));
+          for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int u = 0; u < NA; ++u) atomicAdd(G + d * dstr + (cola + u) * ldq, ds_to(ga[d][u]));
         }
         cur = h.sa;
         cola = cmap[cur];
 #pragma unroll
-        for (int u = 0; u < NA; ++u) {
-          ga[u] = ds_make(0.f, 0.f);
-          fa[u] = ds_from(F[(cola + u) * ldq]);
-        }
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+          for (int u = 0; u < NA; ++u) {
+            ga[d][u] = ds_make(0.f, 0.f);
+            fa[d][u] = ds_from(F[d * dstr + (cola + u) * ldq]);
+          }
       }
       const int colb = cmap[h.sb];
       if (cola < 0 || colb < 0) continue;  // cannot happen: the screen marks both shells of a kept pair
-      ds fb[NB];
+      ds fb[ND][NB];
 #pragma unroll
-      for (int v = 0; v < NB; ++v) fb[v] = ds_from(F[(colb + v) * ldq]);
+      for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int v = 0; v < NB; ++v) fb[d][v] = ds_from(F[d * dstr + (colb + v) * ldq]);
       ds xi[NA * NB];
       pair_xi_ds<LA, LB>(h, a.prims_ds, a.pair_ab + 4 * (size_t)p, s_tab2, cx, cy, cz, xi);
 #pragma unroll
-      for (int u = 0; u < NA; ++u)
+      for (int d = 0; d < ND; ++d)
 #pragma unroll
-        for (int v = 0; v < NB; ++v) ga[u] = fma(xi[u * NB + v], fb[v], ga[u]);
+        for (int u = 0; u < NA; ++u)
+#pragma unroll
+          for (int v = 0; v < NB; ++v) ga[d][u] = fma(xi[u * NB + v], fb[d][v], ga[d][u]);
       if (h.sa != h.sb) {
 #pragma unroll
-        for (int v = 0; v < NB; ++v) {
-          ds g = ds_make(0.f, 0.f);
+        for (int d = 0; d < ND; ++d)
 #pragma unroll
-          for (int u = 0; u < NA; ++u) g = fma(xi[u * NB + v], fa[u], g);
-          atomicAdd(G + (colb + v) * ldq, ds_to(g));
-        }
+          for (int v = 0; v < NB; ++v) {
+            ds g = ds_make(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < NA; ++u) g = fma(xi[u * NB + v], fa[d][u], g);
+            atomicAdd(G + d * dstr + (colb + v) * ldq, ds_to(g));
+          }
       }
     }
     if (cur >= 0) {
 #pragma unroll
-      for (int u = 0; u < NA; ++u) atomicAdd(G + (cola + u) * ldq, ds_to(ga[u]));
+      for (int d = 0; d < ND; ++d)
+#pragma unroll
+        for (int u = 0; u < NA; ++u) atomicAdd(G + d * dstr + (cola + u) * ldq, ds_to(ga[d][u]));
     }
   }
 }
@@ -648,30 +690,25 @@ constexpr size_t kSmem32 = sizeof(float) * kBoysRowsF * kBoysColsF;
 
 // list < kNumClasses: FP64 kernel of that class; otherwise the FP32 kernel of
 // class list - kNumClasses.
+template <class K>
+cudaError_t launch_kernel(K kernel, size_t smem, cudaStream_t st, const IntegralArgs& a, int grid) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kernel<<<grid, kIntThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LA, int LB, int ND>
+cudaError_t launch_class_nd(cudaStream_t st, bool f32, const IntegralArgs& a, int grid) {
+  if (f32 && a.f32_hrr_ds) return launch_kernel(integral_kernel_f32<LA, LB, true, ND>, kSmem32, st, a, grid);
+  if (f32) return launch_kernel(integral_kernel_f32<LA, LB, false, ND>, kSmem32, st, a, grid);
+  if (a.hi_ds) return launch_kernel(integral_kernel_ds<LA, LB, ND>, kSmem64, st, a, grid);
+  return launch_kernel(integral_kernel<LA, LB, ND>, kSmem64, st, a, grid);
+}
+
 template <int LA, int LB>
 cudaError_t launch_class(cudaStream_t st, bool f32, const IntegralArgs& a, int grid) {
-  if (f32 && a.f32_hrr_ds) {
-    cudaError_t e = cudaFuncSetAttribute(integral_kernel_f32<LA, LB, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
-    if (e != cudaSuccess) return e;
-    integral_kernel_f32<LA, LB, true><<<grid, kIntThreads, kSmem32, st>>>(a);
-  } else if (f32) {
-    cudaError_t e = cudaFuncSetAttribute(integral_kernel_f32<LA, LB, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem32);
-    if (e != cudaSuccess) return e;
-    integral_kernel_f32<LA, LB, false><<<grid, kIntThreads, kSmem32, st>>>(a);
-  } else if (a.hi_ds) {
-    cudaError_t e =
-        cudaFuncSetAttribute(integral_kernel_ds<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
-    if (e != cudaSuccess) return e;
-    integral_kernel_ds<LA, LB><<<grid, kIntThreads, kSmem64, st>>>(a);
-  } else {
-    cudaError_t e =
-        cudaFuncSetAttribute(integral_kernel<LA, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem64);
-    if (e != cudaSuccess) return e;
-    integral_kernel<LA, LB><<<grid, kIntThreads, kSmem64, st>>>(a);
-  }
-  return cudaGetLastError();
+  return a.n_dens == 2 ? launch_class_nd<LA, LB, 2>(st, f32, a, grid) : launch_class_nd<LA, LB, 1>(st, f32, a, grid);
 }
 
 template <class K>
@@ -683,12 +720,17 @@ int ctas_for(K kernel, size_t smem, int num_sms) {
   return per_sm * num_sms;
 }
 
+template <int LA, int LB, int ND>
+int max_ctas_nd(bool f32, bool ds, bool hrr_ds, int num_sms) {
+  if (f32 && hrr_ds) return ctas_for(integral_kernel_f32<LA, LB, true, ND>, kSmem32, num_sms);
+  return f32  ? ctas_for(integral_kernel_f32<LA, LB, false, ND>, kSmem32, num_sms)
+         : ds ? ctas_for(integral_kernel_ds<LA, LB, ND>, kSmem64, num_sms)
+              : ctas_for(integral_kernel<LA, LB, ND>, kSmem64, num_sms);
+}
+
 template <int LA, int LB>
-int max_ctas(bool f32, bool ds, bool hrr_ds, int num_sms) {
-  if (f32 && hrr_ds) return ctas_for(integral_kernel_f32<LA, LB, true>, kSmem32, num_sms);
-  return f32  ? ctas_for(integral_kernel_f32<LA, LB, false>, kSmem32, num_sms)
-         : ds ? ctas_for(integral_kernel_ds<LA, LB>, kSmem64, num_sms)
-              : ctas_for(integral_kernel<LA, LB>, kSmem64, num_sms);
+int max_ctas(bool f32, bool ds, bool hrr_ds, int nd, int num_sms) {
+  return nd == 2 ? max_ctas_nd<LA, LB, 2>(f32, ds, hrr_ds, num_sms) : max_ctas_nd<LA, LB, 1>(f32, ds, hrr_ds, num_sms);
 }
 
 }  // namespace
@@ -707,15 +749,15 @@ cudaError_t launch_integrals(cudaStream_t st, int list, const IntegralArgs& a, i
   return cudaErrorInvalidValue;
 }
 
-int integral_max_ctas(int list, int num_sms, bool ds, bool hrr_ds) {
+int integral_max_ctas(int list, int num_sms, bool ds, bool hrr_ds, int n_dens) {
   const bool f32 = list >= kNumClasses;
   switch (list % kNumClasses) {
-    case 0: return max_ctas<0, 0>(f32, ds, hrr_ds, num_sms);
-    case 1: return max_ctas<1, 0>(f32, ds, hrr_ds, num_sms);
-    case 2: return max_ctas<1, 1>(f32, ds, hrr_ds, num_sms);
-    case 3: return max_ctas<2, 0>(f32, ds, hrr_ds, num_sms);
-    case 4: return max_ctas<2, 1>(f32, ds, hrr_ds, num_sms);
-    case 5: return max_ctas<2, 2>(f32, ds, hrr_ds, num_sms);
+    case 0: return max_ctas<0, 0>(f32, ds, hrr_ds, n_dens, num_sms);
+    case 1: return max_ctas<1, 0>(f32, ds, hrr_ds, n_dens, num_sms);
+    case 2: return max_ctas<1, 1>(f32, ds, hrr_ds, n_dens, num_sms);
+    case 3: return max_ctas<2, 0>(f32, ds, hrr_ds, n_dens, num_sms);
+    case 4: return max_ctas<2, 1>(f32, ds, hrr_ds, n_dens, num_sms);
+    case 5: return max_ctas<2, 2>(f32, ds, hrr_ds, n_dens, num_sms);
   }
   return num_sms;
 }

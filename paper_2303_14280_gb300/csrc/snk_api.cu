@@ -77,7 +77,9 @@ struct snk_ctx {
 
   // density-dependent state
   bool have_density = false;
-  DevBuf<double> P, ft, sym, Khat, K;
+  int n_dens = 1;  // densities loaded (P, P2, Khat hold n_dens packed blocks)
+  int ctas_nd = 0;  // density count the persistent grids (max_ctas) were sized for
+  DevBuf<double> P, Pscr, ft, sym, Khat, K;  // Pscr: sum_d |P_d| for the screen of several densities
   DevBuf<float2> P2;  // (hi, lo) pairs of P for the double-FP32 GEMM
   DevBuf<int> counts, list, list2, sfunc, colmap, tickets;  // list2: rewrite target of the learned screen
   DevBuf<long long> ppcounts;
@@ -268,6 +270,15 @@ int make_tiles(snk_ctx* c, cudaStream_t st) {
   return SNK_OK;
 }
 
+// Persistent-grid size of every list's integral kernel (resident CTAs per SM
+// x SMs) for the kernels the options and the density count select.
+void set_max_ctas(snk_ctx* c) {
+  const bool ds = c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals;
+  for (int k = 0; k < kNumLists; ++k)
+    c->max_ctas[k] = integral_max_ctas(k, c->num_sms, ds, c->opt.fp32_hrr_ds != 0, c->n_dens);
+  c->ctas_nd = c->n_dens;
+}
+
 // Density-dependent part of set_density once P is on the device.
 int screen_and_plan(snk_ctx* c) {
   Setup& s = c->s;
@@ -277,18 +288,30 @@ int screen_and_plan(snk_ctx* c) {
   c->have_density = false;
   c->graph_valid = false;
   c->launches_density = 0;
+  if (c->ctas_nd != c->n_dens) set_max_ctas(c);
   SNK_CK(c, cudaEventRecord(c->ev_screen0, st));
   // symmetry check of every molecule block
-  SNK_CK(c, c->sym.ensure(2));
-  SNK_CK(c, cudaMemsetAsync(c->sym.p, 0, 2 * sizeof(double), st));
-  SNK_CK(c, launch_symcheck(st, c->mols.p, s.n_mol, s.packed, c->P.p, c->sym.p));
-  ++c->launches_density;
-  double hsym[2];
+  SNK_CK(c, c->sym.ensure(2 * SNK_MAX_DENSITIES));
+  SNK_CK(c, cudaMemsetAsync(c->sym.p, 0, 2 * SNK_MAX_DENSITIES * sizeof(double), st));
+  for (int d = 0; d < c->n_dens; ++d) {
+    SNK_CK(c, launch_symcheck(st, c->mols.p, s.n_mol, s.packed, c->P.p + (size_t)d * s.packed, c->sym.p + 2 * d));
+    ++c->launches_density;
+  }
+  double hsym[2 * SNK_MAX_DENSITIES];
   SNK_CK(c, cudaMemcpyAsync(hsym, c->sym.p, sizeof(hsym), cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaStreamSynchronize(st));
-  if (!(hsym[0] <= 1e-12 * hsym[1]))
-    return fail(c, std::isfinite(hsym[0]) ? SNK_ERR_NOT_SYMMETRIC : SNK_ERR_UNSUPPORTED,
-                "density matrix is not symmetric (or not finite)");
+  for (int d = 0; d < c->n_dens; ++d)
+    if (!(hsym[2 * d] <= 1e-12 * hsym[2 * d + 1]))
+      return fail(c, std::isfinite(hsym[2 * d]) ? SNK_ERR_NOT_SYMMETRIC : SNK_ERR_UNSUPPORTED,
+                  "density matrix " + std::to_string(d) + " is not symmetric (or not finite)");
+  // the screen of several densities bounds them all with sum_d |P_d|
+  const double* Pscreen = c->P.p;
+  if (c->n_dens > 1) {
+    SNK_CK(c, c->Pscr.ensure((size_t)std::max<int64_t>(s.packed, 1)));
+    SNK_CK(c, launch_abs_sum(st, c->P.p, c->n_dens, s.packed, c->Pscr.p));
+    ++c->launches_density;
+    Pscreen = c->Pscr.p;
+  }
   const int nbx = std::max(nb, 1);
   const size_t cmn = (size_t)std::max<int64_t>(s.cm_total, 1);
   // F-tilde and the pair screen, Eqs. (exx_fmat_approx), (sp_set)
@@ -304,7 +327,7 @@ int screen_and_plan(snk_ctx* c) {
   for (int j = 0; j < nb; ++j) c->hbatch[j] = geometry_desc(s, j);
   SNK_CK(c, upload(c->batch, c->hbatch, st));
   if (screen != SNK_SCREEN_NONE) {
-    SNK_CK(c, launch_ftilde(st, c->mols.p, s.n_mol, c->max_nf, c->max_nb, c->batch.p, c->P.p, c->phit_f.p,
+    SNK_CK(c, launch_ftilde(st, c->mols.p, s.n_mol, c->max_nf, c->max_nb, c->batch.p, Pscreen, c->phit_f.p,
                             c->fshell.p, c->ft.p));
     ++c->launches_density;
   }
@@ -414,8 +437,8 @@ int screen_and_plan(snk_ctx* c) {
   double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0, gflops_hi = 0.0;
   int64_t kept[2] = {0, 0}, pair_points = 0;
   for (int j = 0; j < nb; ++j) {
-    gflops += 4.0 * bd[j].q * (double)bd[j].nB * bd[j].nS;
-    gflops_hi += 4.0 * bd[j].q * (double)bd[j].nB * bd[j].nS_hi;
+    gflops += 4.0 * c->n_dens * bd[j].q * (double)bd[j].nB * bd[j].nS;
+    gflops_hi += 4.0 * c->n_dens * bd[j].q * (double)bd[j].nB * bd[j].nS_hi;
     for (int k = 0; k < kNumLists; ++k) {
       const int cls = k % kNumClasses;
       const int la = cls >= 3 ? 2 : (cls >= 1 ? 1 : 0), lb = cls - la * (la + 1) / 2;
@@ -434,12 +457,14 @@ int screen_and_plan(snk_ctx* c) {
   // FP32 copies of F and G in the mixed form
   int j = 0;
   int64_t need = 1, need32 = 1;
+  const int nd = c->n_dens;
   while (j < nb) {
     snk_ctx::Chunk ch;
     ch.b0 = j;
     int64_t xo = 0, fo = 0;
     while (j < nb) {
-      int64_t xs = (int64_t)bd[j].ldq * bd[j].nB, fs = (int64_t)bd[j].ldq * bd[j].nS;
+      // F and G of density d at foff / goff + d ldq nS
+      int64_t xs = (int64_t)bd[j].ldq * bd[j].nB, fs = (int64_t)nd * bd[j].ldq * bd[j].nS;
       int64_t bytes = (xo + xs + 2 * (fo + fs)) * 8 + (mixed ? 2 * (fo + fs) * 4 : 0);
       if (j > ch.b0 && bytes > c->ws_budget) break;
       xo += xs;
@@ -454,7 +479,7 @@ int screen_and_plan(snk_ctx* c) {
     ch.g32off = g32cur;
     ch.g32n = mixed ? fo : 0;
     for (int t = ch.b0; t < ch.b1; ++t) {
-      const int64_t fs = (int64_t)bd[t].ldq * bd[t].nS;
+      const int64_t fs = (int64_t)nd * bd[t].ldq * bd[t].nS;
       bd[t].xoff = xcur;
       xcur += (int64_t)bd[t].ldq * bd[t].nB;
       bd[t].foff = fcur;
@@ -481,8 +506,9 @@ int screen_and_plan(snk_ctx* c) {
 
   if (int rc = make_tiles(c, st)) return rc;
   SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
-  SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(s.packed, 1)));
-  if (mixed && c->opt.gemm != SNK_GEMM_FP64) SNK_CK(c, c->P2.ensure((size_t)std::max<int64_t>(s.packed, 1)));
+  SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(c->n_dens * s.packed, 1)));
+  if (mixed && c->opt.gemm != SNK_GEMM_FP64)
+    SNK_CK(c, c->P2.ensure((size_t)std::max<int64_t>(c->n_dens * s.packed, 1)));
   SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
   SNK_CK(c, cudaStreamSynchronize(st));
 
@@ -537,6 +563,7 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.hi_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals) ? 1 : 0;
   a.f32_g64 = c->opt.fp32_g64 ? 1 : 0;
   a.f32_hrr_ds = c->opt.fp32_hrr_ds ? 1 : 0;
+  a.n_dens = c->n_dens;
   return a;
 }
 
@@ -550,12 +577,14 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   const int fmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 1)) ? 1 : 0;
   const int kmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 2)) ? 1 : 0;
   const int gpart = split ? 1 : 0;  // with split: df32 on the high-tier columns, then mode 3 on the rest
+  const int nd = c->n_dens;
+  const int64_t pk = s.packed;
   int ev = 0;
   c->launches_build = 0;
   if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
-  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)std::max<int64_t>(s.packed, 1), st));
+  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)std::max<int64_t>(nd * pk, 1), st));
   if (df32) {  // P2 is allocated with the density (no allocation inside a graph capture)
-    SNK_CK(c, launch_split_df32_copy(st, c->P.p, s.packed, c->P2.p));
+    SNK_CK(c, launch_split_df32_copy(st, c->P.p, nd * pk, c->P2.p));
     ++c->launches_build;
   }
   SNK_CK(c, cudaMemsetAsync(c->tickets.p, 0, sizeof(int) * c->tickets.n, st));
@@ -572,14 +601,16 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       ++c->launches_build;
     }
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
-    // F_j = X_j P (w and component factors folded in), Eq. (batch_local_exx)
-    SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->P2.p, c->xfunc.p, c->sfunc.p, c->fcomp.p,
-                           c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode, gpart));
-    ++c->launches_build;
-    if (split) {
-      SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, c->P2.p, c->xfunc.p, c->sfunc.p,
-                             c->fcomp.p, c->w.p, c->ws.p, c->ws32.p, 3, 2));
+    // F_j = X_j P_d (w and component factors folded in), Eq. (batch_local_exx)
+    for (int d = 0; d < nd; ++d) {
+      SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
+                             c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode, gpart, d));
       ++c->launches_build;
+      if (split) {
+        SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
+                               c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, c->ws32.p, 3, 2, d));
+        ++c->launches_build;
+      }
     }
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
     if (mixed && !c->opt.fp32_g64) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
@@ -594,7 +625,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       }
       if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
     }
-    // the FP32 pairs' G into the FP64 G, then Kt += G_j^T X_j, Eq. (usym_k)
+    // the FP32 pairs' G into the FP64 G, then Kt_d += G_dj^T X_j, Eq. (usym_k)
     if (mixed && ch.g32n > 0 && !c->opt.fp32_g64) {
       SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
       ++c->launches_build;
@@ -603,25 +634,30 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       SNK_CK(c, launch_split_df32(st, c->ws.p + ch.goff, ch.gbytes / 8));
       ++c->launches_build;
     }
-    SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p, kmode,
-                           gpart));
-    ++c->launches_build;
-    if (split) {
-      SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p, 3, 2));
+    for (int d = 0; d < nd; ++d) {
+      SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p + d * pk,
+                             kmode, gpart, d));
       ++c->launches_build;
+      if (split) {
+        SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p,
+                               c->Khat.p + d * pk, 3, 2, d));
+        ++c->launches_build;
+      }
     }
     if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
   }
-  // K = (Kt + Kt^T) / 2 in every molecule block, Eq. (sn_k)
-  SNK_CK(c, launch_finish(st, c->mols.p, s.n_mol, s.packed, c->Khat.p, c->fcomp.p, dK));
-  ++c->launches_build;
+  // K_d = (Kt_d + Kt_d^T) / 2 in every molecule block, Eq. (sn_k)
+  for (int d = 0; d < nd; ++d) {
+    SNK_CK(c, launch_finish(st, c->mols.p, s.n_mol, s.packed, c->Khat.p + d * pk, c->fcomp.p, dK + d * pk));
+    ++c->launches_build;
+  }
   if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
   return SNK_OK;
 }
 
 int build(snk_ctx* c, double* dK) {
   if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_build_K called before snk_set_density");
-  if (!c->opt.graph) {
+  if (!c->opt.graph || c->n_dens > 1) {
     if (int rc = ensure_events(c, c->chunks.size() * kPhaseEvents + 2)) return rc;
     if (int rc = enqueue_build(c, c->stream, dK, true)) return rc;
     c->built = true;
@@ -721,7 +757,7 @@ int autotune(snk_ctx* c, int32_t* runs_out) {
   }
   const bool graph = c->opt.graph;
   c->opt.graph = 0;
-  SNK_CK(c, c->K.ensure((size_t)std::max<int64_t>(c->s.packed, 1)));
+  SNK_CK(c, c->K.ensure((size_t)std::max<int64_t>(c->n_dens * c->s.packed, 1)));
   int rc = build(c, c->K.p);
   c->opt.graph = graph;
   if (rc != SNK_OK) return rc;
@@ -913,9 +949,7 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
        }()) != SNK_OK)
     return rc;
   if ((rc = geometry_screen(cp)) != SNK_OK) return rc;
-  const bool ds = cp->opt.precision == SNK_PREC_MIXED && cp->opt.ds_integrals;
-  for (int k = 0; k < kNumLists; ++k)
-    cp->max_ctas[k] = integral_max_ctas(k, cp->num_sms, ds, cp->opt.fp32_hrr_ds != 0);
+  set_max_ctas(cp);
   std::memset(&cp->st, 0, sizeof(cp->st));
   cp->st.n_points = s.npts;
   cp->st.n_batches = cp->nbatch;
@@ -982,9 +1016,41 @@ int snk_set_density(snk_ctx* c, const double* P) {
   if (!P) return fail(c, SNK_ERR_INVALID_ARG, "NULL density");
   const size_t n = (size_t)c->s.packed;
   c->have_density = false;
+  c->n_dens = 1;
   SNK_CK(c, c->P.ensure(std::max<size_t>(n, 1)));
   if (n) SNK_CK(c, cudaMemcpyAsync(c->P.p, P, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
   return screen_and_plan(c);
+}
+
+int snk_set_density_multi(snk_ctx* c, int32_t n_dens, const double* const* P) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (n_dens < 1 || n_dens > SNK_MAX_DENSITIES || !P)
+    return fail(c, SNK_ERR_INVALID_ARG, "need 1.." + std::to_string(SNK_MAX_DENSITIES) + " densities");
+  if (c->s.n_mol != 1) return fail(c, SNK_ERR_UNSUPPORTED, "several densities need a single-molecule handle");
+  for (int d = 0; d < n_dens; ++d)
+    if (!P[d]) return fail(c, SNK_ERR_INVALID_ARG, "NULL density " + std::to_string(d));
+  const size_t n = (size_t)c->s.packed;
+  c->have_density = false;
+  c->n_dens = n_dens;
+  SNK_CK(c, c->P.ensure(std::max<size_t>(n * n_dens, 1)));
+  for (int d = 0; d < n_dens; ++d)
+    if (n) SNK_CK(c, cudaMemcpyAsync(c->P.p + d * n, P[d], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  return screen_and_plan(c);
+}
+
+int snk_build_K_multi(snk_ctx* c, double* const* K) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!K) return fail(c, SNK_ERR_INVALID_ARG, "NULL output list");
+  for (int d = 0; d < c->n_dens; ++d)
+    if (!K[d]) return fail(c, SNK_ERR_INVALID_ARG, "NULL output " + std::to_string(d));
+  const size_t n = (size_t)c->s.packed;
+  SNK_CK(c, c->K.ensure(std::max<size_t>(n * c->n_dens, 1)));
+  int rc = build(c, c->K.p);
+  if (rc != SNK_OK) return rc;
+  for (int d = 0; d < c->n_dens; ++d)
+    if (n) SNK_CK(c, cudaMemcpyAsync(K[d], c->K.p + d * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  return SNK_OK;
 }
 
 int snk_set_density_device(snk_ctx* c, const double* dP) {
@@ -992,6 +1058,7 @@ int snk_set_density_device(snk_ctx* c, const double* dP) {
   if (!dP) return fail(c, SNK_ERR_INVALID_ARG, "NULL density");
   const size_t n = (size_t)c->s.packed;
   c->have_density = false;
+  c->n_dens = 1;
   SNK_CK(c, c->P.ensure(std::max<size_t>(n, 1)));
   if (n) SNK_CK(c, cudaMemcpyAsync(c->P.p, dP, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
   return screen_and_plan(c);
@@ -1001,6 +1068,7 @@ int snk_set_density_batch(snk_ctx* c, const double* const* P) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!P) return fail(c, SNK_ERR_INVALID_ARG, "NULL density list");
   c->have_density = false;
+  c->n_dens = 1;
   SNK_CK(c, c->P.ensure(std::max<size_t>((size_t)c->s.packed, 1)));
   for (int m = 0; m < c->s.n_mol; ++m) {
     if (!P[m]) return fail(c, SNK_ERR_INVALID_ARG, "NULL density for molecule " + std::to_string(m));
@@ -1011,15 +1079,24 @@ int snk_set_density_batch(snk_ctx* c, const double* const* P) {
   return screen_and_plan(c);
 }
 
+// The single-output builds write one packed K: several loaded densities need
+// snk_build_K_multi.
+int one_density(snk_ctx* c) {
+  return c->n_dens == 1 ? SNK_OK
+                        : fail(c, SNK_ERR_BAD_STATE, "several densities are loaded: use snk_build_K_multi");
+}
+
 int snk_build_K_device(snk_ctx* c, double* dK) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!dK) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
+  if (int rc = one_density(c)) return rc;
   return build(c, dK);
 }
 
 int snk_build_K(snk_ctx* c, double* K) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!K) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
+  if (int rc = one_density(c)) return rc;
   const size_t n = (size_t)c->s.packed;
   SNK_CK(c, c->K.ensure(std::max<size_t>(n, 1)));
   int rc = build(c, c->K.p);
@@ -1031,6 +1108,7 @@ int snk_build_K(snk_ctx* c, double* K) {
 
 int snk_build_K_batch(snk_ctx* c, double* const* K) {
   if (!c) return SNK_ERR_INVALID_ARG;
+  if (int rc = one_density(c)) return rc;
   if (!K) return fail(c, SNK_ERR_INVALID_ARG, "NULL output list");
   for (int m = 0; m < c->s.n_mol; ++m)
     if (!K[m]) return fail(c, SNK_ERR_INVALID_ARG, "NULL output for molecule " + std::to_string(m));
@@ -1269,6 +1347,7 @@ int learn_collect(snk_ctx* c, int stride, int64_t cap, float* feat, float* lab, 
     return fail(c, SNK_ERR_INVALID_ARG, "snk_learn_collect: bad arguments");
   *n_out = 0;
   if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_learn_collect called before snk_set_density");
+  if (c->n_dens != 1) return fail(c, SNK_ERR_BAD_STATE, "snk_learn_collect needs one density");
   if (c->opt.screen == SNK_SCREEN_LEARNED && c->mlp_loaded)
     return fail(c, SNK_ERR_BAD_STATE, "snk_learn_collect needs the rigorous screen's lists (screen != learned)");
   const int nb = c->nbatch, nbx = std::max(nb, 1);
@@ -1310,7 +1389,7 @@ int learn_collect(snk_ctx* c, int stride, int64_t cap, float* feat, float* lab, 
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
     SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nullptr, c->xfunc.p, c->sfunc.p, c->fcomp.p,
-                           c->w.p, c->ws.p, nullptr, 0, 0));
+                           c->w.p, c->ws.p, nullptr, 0, 0, 0));
     SNK_CK(c, launch_xmax(st, db, nbc, c->ws.p, dxmax.p));
     for (int k = 0; k < kNumLists; ++k) {
       std::vector<Tile> ht;

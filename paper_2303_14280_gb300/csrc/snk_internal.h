@@ -220,15 +220,20 @@ cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 // hold (hi, lo) float pairs in place of the doubles, see launch_split_df32).
 // mode 3: split-TF32 on the hi floats of (hi, lo) operands, FP32 partial sums
 // of 64 terms folded into double-FP32.  part: 0 all F / G columns, 1 the
-// high-tier columns [0, nS_hi), 2 the rest.
+// high-tier columns [0, nS_hi), 2 the rest.  dens: which density's F / G
+// block of each batch (at foff / goff + dens ldq nS).
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc,
-                         const double* fcomp, const double* w, double* ws, float* ws32, int mode, int part);
+                         const double* fcomp, const double* w, double* ws, float* ws32, int mode, int part,
+                         int dens);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part);
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part,
+                         int dens);
 // In place, each double of buf[0, n) becomes the float pair (fl32(v), fl32(v - fl32(v))).
 cudaError_t launch_split_df32(cudaStream_t st, double* buf, int64_t n);
 cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n, float2* dst);
+// out = sum_d |P_d| over n_dens consecutive arrays of n doubles.
+cudaError_t launch_abs_sum(cudaStream_t st, const double* P, int n_dens, int64_t n, double* out);
 cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* Khat,
                           const double* fcomp, double* K);
 cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* P,
@@ -261,10 +266,11 @@ struct IntegralArgs {
   int hi_ds;
   int f32_g64;  // FP32 lists add into the FP64 G (ws + goff) instead of the FP32 copy
   int f32_hrr_ds;  // FP32 lists run the HRR in double-FP32
+  int n_dens;      // densities: F and G of density d at foff / goff (+32) + d ldq nS
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
-int integral_max_ctas(int cls, int num_sms, bool ds, bool hrr_ds);
+int integral_max_ctas(int cls, int num_sms, bool ds, bool hrr_ds, int n_dens);
 cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const PrimPair* prims,
                            const double* boys, int64_t n, const double* xyz, double* xi);
 cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, const double* T,

@@ -312,3 +312,39 @@ def test_fp32_tier_accumulation_and_hrr_variants(snk):
         assert np.max(np.abs(K - Kref)) <= 1e-8
         assert np.max(np.abs(K - K.T)) == 0.0
     assert np.max(np.abs(K1 - K0)) <= 1e-9 and np.max(np.abs(K2 - K0)) <= 1e-9
+
+
+def test_two_densities_in_one_build(snk, chain4):
+    """Several densities share every 3c-CP block (one screen on sum_d |P_d|):
+    each K_d matches the oracle's K of P_d and the single-density build, in the
+    plain and the mixed form; wrong counts and single-output builds are refused."""
+    P2 = synth.make_density(chain4.mol, chain4.basis, 3, 4242, sigma=None)
+    Ks = snk.Engine(chain4.basis, chain4.grid, screen="none")
+    Ks.set_density([chain4.P, P2])
+    K1, K2 = Ks.build_K()
+    for K, P in ((K1, chain4.P), (K2, P2)):
+        assert np.max(np.abs(K - oracle.snk_K(chain4.basis, chain4.grid, P))) <= TOL_K
+    Ks.close()
+
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Pb = synth.make_density(p.mol, p.basis, 14, 78)
+    refs = [oracle.snk_K(p.basis, p.grid, P) for P in (p.P, Pb)]
+    for form, tol in ((dict(), TOL_K),
+                      (dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, ds_integrals=1, gemm="split"), 1e-8)):
+        eng = snk.Engine(p.basis, p.grid, batch_max=300, **form)
+        eng.set_density([p.P, Pb])
+        Kd = eng.build_K()
+        st = eng.stats()
+        assert len(Kd) == 2 and st["gemm_flops"] > 0
+        for K, Kr in zip(Kd, refs):
+            assert np.max(np.abs(K - Kr)) <= tol
+            assert np.max(np.abs(K - K.T)) == 0.0
+        Kone = np.empty((p.basis.n_functions,) * 2)
+        rc = snk.lib().snk_build_K(eng._h, snk._P(Kone.ctypes.data))
+        assert rc == -4                             # one output for two loaded densities
+        eng.set_density(p.P)                        # back to one density
+        assert np.max(np.abs(eng.build_K() - refs[0])) <= tol
+        with pytest.raises(snk.SnkError) as e:
+            eng.set_density([p.P, Pb, p.P])
+        assert e.value.status == -1
+        eng.close()
