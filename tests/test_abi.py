@@ -37,6 +37,11 @@ def test_options_defaults():
     import paper_2303_14280_gb300 as snk
     o = snk.options()
     assert o.batch_max == 4096 and o.eps_E == 1e-12 and o.screen == 1 and o.precision == 0
+    # the plain FP64 form unless a form is asked for
+    assert o.gemm == 0 and o.ds_integrals == 0 and o.tensor_gemms == 0 and o.graph == 0
+    assert o.fp32_g64 == 0 and o.fp32_hrr_ds == 0 and o.distance_bound == 1
+    assert o.learned_skip == -11.0 and o.learned_fp32 == -99.0 and o.fp32_bound == 1e-6
+    assert snk.options(gemm="split").gemm == 2 and snk.options(precision="mixed").precision == 1
 
 
 def test_generated_os_code_is_current():
@@ -78,3 +83,31 @@ def test_null_handle_calls_fail_cleanly():
     assert L.snk_build_K(None, None) == -1
     assert L.snk_last_error(None) == b"NULL handle"
     L.snk_destroy(None)
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program built with gcc."""
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "snk.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("cname,pyname", [("snk_options", "SnkOptions"), ("snk_stats", "SnkStats"),
+                                          ("snk_basis", "SnkBasis"), ("snk_grid", "SnkGrid")])
+def test_binding_structs_match_the_header_layout(cname, pyname, tmp_path):
+    """The ctypes mirrors of the header structs have the C compiler's size and
+    every field at the C compiler's offset."""
+    import paper_2303_14280_gb300 as snk
+    cls = getattr(snk, pyname)
+    fields = [f[0] for f in cls._fields_]
+    size, offs = _c_layout(cname, fields, tmp_path)
+    assert ctypes.sizeof(cls) == size
+    for f, off in zip(fields, offs):
+        assert getattr(cls, f).offset == off, f
