@@ -2,9 +2,10 @@
 //   collocation X_j (Eq. collocation), the geometry-only batch maxima of
 //   Eq. (exx_fmat_approx), F-tilde = |P| Phi-tilde (Eq. exx_fmat_approx) as
 //   a GEMM over batches, the sn-LinK pair screen with per-batch compaction
-//   (Eq. sp_set), the products F_j = X_j P (Eq. batch_local_exx) and
-//   Kt += G_j^T X_j (Eq. usym_k) in FP64 or as split-TF32 tensor-core
-//   products, and the symmetrisation of Eq. (sn_k).
+//   (Eq. sp_set), the integral tiles, the products F_j = X_j P (Eq.
+//   batch_local_exx) and Kt += G_j^T X_j (Eq. usym_k) in FP64, double-FP32
+//   or split-TF32 tensor-core tiles (one F / G block per density), and the
+//   symmetrisation of Eq. (sn_k).
 //
 // Several molecules can share one handle: every batch knows its molecule, P
 // and K are packed per molecule (row-major N_b,m^2 blocks), and column lists

@@ -17,7 +17,10 @@
 // GB300 issues FP64 at 2 DFMA per SM per clock (1/64 of FP32), so the kernel
 // is FP64-pipe bound by construction: table lookups, index arithmetic, F loads
 // and the G atomics (L2 reductions, ~600 G/s) all hide under the DFMA stream,
-// and the generated VRR/HRR minimise the FP64 instruction count.
+// and the generated VRR/HRR minimise the FP64 instruction count.  The mixed
+// form adds an FP32 kernel for its low-estimate pairs and a double-FP32 one
+// (ds_arith.cuh) for the rest; all three take the number of densities sharing
+// each 3c-CP block as a template parameter.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -220,10 +223,13 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
 
 // Primitive pair in FP32, its product centre relative to the batch centre.
 // The FP32 lists of the mixed form.  Primitive-pair data come as one 64-byte
-// FP32 record per primitive pair (four broadcast 16-byte loads, no staging and
-// no barrier per pair) with the product centre split into hi + lo floats, and
-// P - r_i is formed as (P_hi - r_hi) + (P_lo - r_lo) so that it is accurate to
-// FP32 relative to |P - r_i| however far the molecule sits from the origin.
+// FP32 record per primitive pair with the product centre split into hi + lo
+// floats, and P - r_i is formed as (P_hi - r_hi) + (P_lo - r_lo) so that it is
+// accurate to FP32 relative to |P - r_i| however far the molecule sits from
+// the origin.  A tile's pair headers, columns and R_a - R_b are staged in
+// shared memory once per tile (one barrier per tile); the next pair's F is
+// loaded while the current pair computes; for the light classes each warp
+// also stages the pair's records (below).
 template <int LA, int LB, bool HRR_DS, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
