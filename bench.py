@@ -87,6 +87,8 @@ def make_problems(name, device=None):
     import synth
     if name == "batch64":
         return [synth.multi_molecule(m, device=device) for m in range(64)]
+    if name == "batch64_small":
+        return [synth.small_molecule(m, device=device) for m in range(64)]
     return [getattr(synth, name)(device=device)]
 
 
@@ -98,6 +100,9 @@ def workload_config(name, probs):
     if name == "batch64":
         desc = (f"batch64: 64 molecules of 6-60 atoms ({nat} atoms, {nf} Cartesian functions up to d, {npts} grid "
                 f"points, 40-50 MK radial x 75-160 angular points per atom, Becke), 20% occupied columns")
+    elif name == "batch64_small":
+        desc = (f"batch64_small: 64 molecules of 4-12 atoms ({nat} atoms, {nf} Cartesian functions up to d, {npts} "
+                f"grid points, 40 MK radial x 75 angular points per atom, Becke), 20% occupied columns")
     else:
         p = probs[0]
         desc = (f"{name}: {nat} atoms ({nh} O-like, {nat - nh} H-like), {nf} Cartesian functions up to d, "
@@ -333,7 +338,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,  # cluster24: a small case of cluster96's shape for profiles
-                    choices=["cluster24", "cluster96", "cluster256", "cluster512", "batch64"])
+                    choices=["cluster24", "cluster96", "cluster256", "cluster512", "batch64", "batch64_small"])
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -355,7 +360,7 @@ def main():
     snk.lib()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    batch = args.workload == "batch64"
+    batch = args.workload.startswith("batch64")
     probs = make_problems(args.workload, device=dev)
     n_mol = len(probs)
 

@@ -326,6 +326,15 @@ def cluster512(device=None) -> Problem:
     return cluster(512, 105, device=device)
 
 
+def small_molecule(m: int, device=None) -> Problem:
+    """Molecule m of a batch of small molecules: 4..12 atoms, 40 radial x
+    (5 x 15) angular points per atom, drawn from seed 5000 + m."""
+    seed = 5000 + m
+    rng = np.random.default_rng(seed)
+    n_atoms = int(rng.integers(4, 13))
+    return cluster(n_atoms, seed, n_r=40, n_theta=5, n_phi=15, device=device)
+
+
 def multi_molecule(m: int, device=None) -> Problem:
     """Molecule m of the 64-molecule batch: 6..60 atoms, N_r in {40, 50},
     angular rule in {5x15, 8x15, 8x20}, all drawn from seed 2000 + m."""
