@@ -17,6 +17,17 @@
  * exx_fmat_approx, batch_local_exx).  A is evaluated by the Obara-Saika
  * recursions of App. A (Eqs. vrr, hrr), contracted with F on the fly.
  *
+ * Forms (all through the same calls, selected by snk_options):
+ *   - plain: FP64 throughout (the default);
+ *   - mixed precision: blocks with a small sn-LinK estimate in FP32, the rest
+ *     in FP64 or double-FP32 (hi + lo float pairs), the two products in FP64,
+ *     double-FP32 or split-TF32 tensor-core tiles; G and K accumulated in FP64;
+ *   - batched: many molecules in one handle (snk_create_batch), one launch per
+ *     phase, optional CUDA-graph replay and autotuned tiles;
+ *   - learned screen: a small MLP, trained by the library's own kernels,
+ *     skips blocks and picks the precision tier behind the rigorous screen;
+ *   - several densities of one molecule in one build (snk_set_density_multi).
+ *
  * Conventions
  *   - Units: bohr and hartree.  K is the bare exchange matrix: no -c_x factor
  *     and no closed-shell factor (P is used as given).
