@@ -348,3 +348,29 @@ def test_two_densities_in_one_build(snk, chain4):
             eng.set_density([p.P, Pb, p.P])
         assert e.value.status == -1
         eng.close()
+
+
+@pytest.mark.parametrize("recipe", ["small", "scale"])
+def test_rigorous_pair_bound_holds(snk, recipe):
+    """The screen's bound of max_r |A_ab(r)| (C9: product-centre expansion and
+    the potential of a positive charge peaking at its centre) is never below
+    the oracle's integrals: every shell pair of a six-atom molecule, at the
+    atoms, the pair centre and random points near and far."""
+    mol = synth.make_cluster_molecule(6, 31)
+    basis = synth.make_basis(mol, recipe, 31)
+    grid = synth.make_grid(mol, 6, 2, 4)
+    eng = snk.Engine(basis, grid)
+    rng = np.random.default_rng(9)
+    worst = 0.0
+    for sa in range(basis.n_shells):
+        for sb in range(sa + 1):
+            bound = eng.debug_pair_bound(sa, sb)
+            mid = 0.5 * (basis.center[sa] + basis.center[sb])
+            pts = np.concatenate([mid[None], basis.center[[sa, sb]], mid + rng.normal(size=(8, 3)) * 0.3,
+                                  mid + rng.normal(size=(8, 3)) * 2.0, mid + rng.normal(size=(4, 3)) * 8.0])
+            amax = max(float(np.max(np.abs(oracle.shell_A(basis, sa, sb, r)))) for r in pts)
+            assert amax <= bound * (1.0 + 1e-12), (sa, sb, amax, bound)
+            if bound > 0.0:   # a zero bound (product factor below the double range) has zero integrals
+                worst = max(worst, amax / bound)
+    eng.close()
+    assert 0.0 < worst <= 1.0 + 1e-12   # the bound is attained (s-s pairs at their product centre)
