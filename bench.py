@@ -176,6 +176,24 @@ def golden_err(name, K):
     return float(np.max(np.abs(K[mu, nu] - ref)))
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the oracle timings."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def cpu_oracle_rate(p, target_s: float = 12.0, seed: int = 0):
     """The oracle on a bounded random sample of grid points; returns
     (builds/s scaled to the full grid, threads, sample description)."""
@@ -234,7 +252,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.workload, probs),
-            "cpu_baseline": {"value": value, "unit": "K-builds/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "K-builds/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "K-builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -504,7 +523,8 @@ def main():
             [p.grid.n_points for p in probs]))])
         if batch:
             sample += " (largest molecule of the batch; molecule builds/s)"
-        line["cpu_baseline"] = {"value": rate, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": rate, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
+                                "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
