@@ -155,9 +155,16 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
 
 
 def options(**kw) -> SnkOptions:
+    """snk_options from the library defaults and keyword overrides: any field
+    of snk_options (include/snk.h), `eps` for eps_basis = eps_E = eps_K, and
+    names for screen ("none", "link", "learned"), precision ("fp64", "mixed")
+    and gemm ("fp64", "df32", "split").  Unknown keys raise ValueError."""
     o = SnkOptions()
     lib().snk_options_default(ctypes.byref(o))
+    fields = {f[0] for f in SnkOptions._fields_} - {"reserved"}
     for k, v in kw.items():
+        if k != "eps" and k not in fields:
+            raise ValueError(f"unknown option {k!r}; options are eps, {', '.join(sorted(fields))}")
         if k == "screen" and isinstance(v, str):
             v = SCREEN[v]
         if k == "precision" and isinstance(v, str):

@@ -42,6 +42,8 @@ def test_options_defaults():
     assert o.fp32_g64 == 0 and o.fp32_hrr_ds == 0 and o.distance_bound == 1
     assert o.learned_skip == -11.0 and o.learned_fp32 == -99.0 and o.fp32_bound == 1e-6
     assert snk.options(gemm="split").gemm == 2 and snk.options(precision="mixed").precision == 1
+    with pytest.raises(ValueError):
+        snk.options(gemmm="split")            # a misspelled option is an error, not a no-op
 
 
 def test_generated_os_code_is_current():
