@@ -1,7 +1,8 @@
 """A plain C99 program against include/snk.h and libsnk.so (no GPU needed):
 the header compiles as C, the library links, and the host-side paths of the
 boundary behave as documented (defaults, argument and input validation,
-status strings)."""
+status strings).  Every refused input below is rejected before any device
+call, so the program also runs where no GPU is present."""
 import os
 import subprocess
 
@@ -34,9 +35,27 @@ int main(void) {
   snk_grid g = {1, xyz, w, &gatom};
   CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_UNSUPPORTED && ctx == NULL);
 
-  /* a bad option is refused before any device work */
+  /* inputs the library cannot use are refused before any device work */
   l = 0;
+  exps[0] = -1.0;                                           /* non-positive exponent */
+  CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_UNSUPPORTED && ctx == NULL);
+  exps[0] = 1.0;
+  coefs[0] = 0.0;                                           /* contraction of zero norm */
+  CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_UNSUPPORTED && ctx == NULL);
+  coefs[0] = 1.0;
+  w[0] = 0.0 / 0.0;                                         /* non-finite weight */
+  CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_UNSUPPORTED && ctx == NULL);
+  w[0] = 1.0;
+  nprim = 17;                                               /* more primitives than supported */
+  CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_UNSUPPORTED && ctx == NULL);
+  nprim = 1;
+
+  /* a bad option is refused before any device work */
   o.gemm = 7;
+  CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_INVALID_ARG);
+  snk_options_default(&o);
+  o.learned_fp32 = -4.0;
+  o.batch_max = 0;
   CHECK(snk_create(&b, &g, &o, &ctx) == SNK_ERR_INVALID_ARG);
 
   CHECK(snk_set_density(NULL, NULL) == SNK_ERR_INVALID_ARG);
