@@ -22,8 +22,13 @@ Forms:
    autotuned tiles, every pair and GEMM in double-FP32 for the 1e-10 target,
    against 64 separate plain FP64 builds)
 
-Default workload: the 96-atom cluster (992 functions, 768,000 points).  Other
-workloads: --workload cluster256 | cluster512 | batch64.
+Default workload: the 512-atom cluster (5,280 functions, 4,096,000 points).
+Its plain FP64 build (~23 minutes) cannot run beside the chosen form's steps,
+so the plain arm is timed on the grid points of every 16th atom (a stated,
+cost-stratified subset whose batches are those of the full build) and scaled
+to the full build phase by phase with the full build's own screened work.
+Other workloads: --workload cluster96 | cluster256 | batch64 | batch64_small
+(their plain arm runs in full).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -48,7 +53,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sn-K K-builds/s at stated max|ΔK|: chosen form vs plain FP64, same GB300"
-WORKLOAD = "cluster96"
+WORKLOAD = "cluster512"
 # ALU peaks of GB300 (152 SMs at the 2070 MHz maximum SM clock): FP64 as the
 # recipe's nominal 1.25 TFLOP/s; FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz.
 # A DFMA / FFMA microbenchmark on this pool measured 1.19 and 73.2 TFLOP/s.
@@ -57,10 +62,26 @@ FP32_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12
 DF32_OPS_PER_MAC = 12      # FP32 instructions per double-FP32 multiply-add (GEMM tiles)
 DS_OPS_PER_FLOP = 7.5      # ds fused multiply-add: 15 FP32 instructions for 2 flops
 FP32_INSTR_RATE = 152 * 128 * 2.07e9 / 1e12   # T FP32 lane-instructions/s
+FP64_DFMA_MEASURED = 1.19  # TFLOP/s, a DFMA microbenchmark on one GB300 of this machine
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+HBM_MEASURED = _measured_peaks().get("hbm_gbs")
+HBM_PEAK = float(HBM_MEASURED or 6800.0)
 PLAIN = dict()
 CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1)
-GOLDEN = {"cluster96": os.path.join(ROOT, "tests", "golden", "cluster96_K_entries.txt"),
-          "cluster256": os.path.join(ROOT, "tests", "golden", "cluster256_K_entries.txt")}
+GOLDEN = {n: os.path.join(ROOT, "tests", "golden", f"{n}_K_entries.txt")
+          for n in ("cluster96", "cluster256", "cluster512")}
+# workloads whose plain FP64 build is too slow to repeat beside the chosen
+# form: the plain arm runs on every k-th atom's grid points (see plain_subset)
+PLAIN_SUBSET = {"cluster512": 16}
 
 
 def dist_env():
@@ -338,7 +359,8 @@ def timed(runner, steps, warmup, stream, barrier):
         runner.step()
         for s in runner.stats():        # per-phase times from the library's events on the same stream
             for k in ("ms_integrals", "ms_integrals_fp32", "ms_fgemm", "ms_kgemm", "ms_screen", "ms_collocation",
-                      "ms_finish", "integral_flops", "flops_fp32", "gemm_flops", "kernel_launches", "integrals"):
+                      "ms_finish", "integral_flops", "flops_fp32", "gemm_flops", "kernel_launches", "integrals",
+                      "colloc_bytes"):
                 acc[k] = acc.get(k, 0.0) + float(s[k])
     e1.record(stream)
     torch.cuda.synchronize()
@@ -346,13 +368,72 @@ def timed(runner, steps, warmup, stream, barrier):
     return e0.elapsed_time(e1), acc
 
 
+def subset_atoms(p, k):
+    """Every k-th atom of the molecule in a cost-stratified order (heavy atoms
+    first, each kind by distance from the centre), starting at k // 2."""
+    xyz, Z = p.mol.xyz, p.mol.Z
+    r = np.linalg.norm(xyz - xyz.mean(axis=0), axis=1)
+    order = sorted(range(Z.shape[0]), key=lambda a: (-int(Z[a]), float(r[a]), a))
+    return sorted(order[k // 2::k])
+
+
+def plain_subset(snk, p, k, stream, barrier, warmup, dev):
+    """The plain FP64 build on the grid points of every k-th atom (its own
+    octree batches, basis screen and pair lists are those of the full build:
+    batching is per atom), scaled to the full grid phase by phase with the
+    full build's own screened work: integrals by FP64 integral flops, the two
+    products by their flops, collocation by points, the screen measured on the
+    full grid.  Returns (ms per full build estimated, details, K of the
+    subset, the subset problem)."""
+    import synth
+    import torch
+    full = snk.Engine(p.basis, p.grid, **PLAIN)
+    full.set_stream(stream)
+    Pd = torch.from_numpy(p.P).to(dev)
+    full.set_density(Pd)
+    torch.cuda.synchronize()
+    sf = full.stats()
+    full.close()
+    atoms = subset_atoms(p, k)
+    mask = np.isin(p.grid.atom, atoms)
+    sub = synth.Problem(p.name + f"_every{k}th_atom", p.mol, p.basis,
+                        synth.Grid(xyz=p.grid.xyz[mask], w=p.grid.w[mask], atom=p.grid.atom[mask]), p.P, p.meta)
+    run = Runner(snk, [sub], dict(PLAIN), False, dev, stream)
+    ms, acc = timed(run, 1, warmup, stream, barrier)
+    ss = run.stats()[0]
+    K = run.Ks()[0]
+    run.close()
+    r_int = sf["integral_flops"] / max(ss["integral_flops"], 1.0)
+    r_gemm = sf["gemm_flops"] / max(ss["gemm_flops"], 1.0)
+    r_pts = sf["n_points"] / max(ss["n_points"], 1)
+    est = (sf["ms_screen"] + acc["ms_integrals"] * r_int + (acc["ms_fgemm"] + acc["ms_kgemm"]) * r_gemm +
+           acc["ms_collocation"] * r_pts + acc["ms_finish"] + max(ms - acc["ms_screen"] - acc["ms_integrals"] -
+                                                                  acc["ms_fgemm"] - acc["ms_kgemm"] -
+                                                                  acc["ms_collocation"] - acc["ms_finish"], 0.0))
+    info = {"method": (f"plain FP64 build timed on the grid points of every {k}th atom ({len(atoms)} of "
+                       f"{p.mol.Z.shape[0]} atoms, heavy then light, each by distance from the centre, from "
+                       f"offset {k // 2}); per-atom batching makes its batches, basis screen and pair lists those of "
+                       "the full build; scaled phase by phase with the full build's own screened work "
+                       "(integrals x FP64 integral flops, products x their flops, collocation x points; the "
+                       "screen timed on the full grid)"),
+            "subset_points": int(ss["n_points"]), "full_points": int(sf["n_points"]),
+            "subset_ms": ms, "ratio_integral_flops": r_int, "ratio_gemm_flops": r_gemm,
+            "integral_flops_full": sf["integral_flops"], "pairs_kept_full": int(sf["pairs_kept"]),
+            "ms_integrals_subset": acc["ms_integrals"], "integral_flops_subset": ss["integral_flops"]}
+    return est, info, K, sub
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="host-API steps of the e2e measurement (default: min(steps, 3))")
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--plain-warmup", type=int, default=None)
+    ap.add_argument("--plain-subset", type=int, default=None,
+                    help="run the plain FP64 arm on every k-th atom (default: 16 for cluster512, else off)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -382,6 +463,9 @@ def main():
     batch = args.workload.startswith("batch64")
     probs = make_problems(args.workload, device=dev)
     n_mol = len(probs)
+    subset_k = args.plain_subset if args.plain_subset is not None else PLAIN_SUBSET.get(args.workload)
+    if batch:
+        subset_k = None
 
     # ---- chosen form
     learned = None
@@ -412,11 +496,12 @@ def main():
     K_ch = ch.Ks()
 
     # e2e through the C ABI with host buffers (P upload and K download inside)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 3)
     Ph, Kh = ch.host_buffers()
     barrier()
     torch.cuda.synchronize()
     t = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         if batch:
             ch.engs[0].set_density(Ph[0])
             Kh = [ch.engs[0].build_K()]
@@ -425,25 +510,42 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
-    e2e_value = job_throughput(e2e_s * 1e3, args.steps, world, n_mol if batch else 1)
+    e2e_value = job_throughput(e2e_s * 1e3, e2e_steps, world, n_mol if batch else 1)
     nbytes = sum(p.P.nbytes for p in probs)
     ch_create = ch.create_s
     ch.close()
 
-    # ---- plain FP64 beside it
-    pl = Runner(snk, probs, dict(PLAIN), False, dev, stream)
-    ps = args.plain_steps if args.plain_steps is not None else args.steps
-    pw = args.plain_warmup if args.plain_warmup is not None else args.warmup
-    ms_pl, acc_pl = timed(pl, ps, pw, stream, barrier)
-    ms_pl = max_over_ranks(ms_pl, dist, dev)
-    value_pl = job_throughput(ms_pl, ps, world, n_mol)
-    K_pl = pl.Ks()
-    st_pl = pl.stats()
-    pl.close()
+    # ---- plain FP64 beside it: the full build, or its stated subset scaled to the full build
+    pw = args.plain_warmup if args.plain_warmup is not None else (1 if subset_k else args.warmup)
+    err_ch_pl_sub = None
+    acc_pl = None
+    if subset_k:
+        est_ms, plain_info, K_sub, subp = plain_subset(snk, probs[0], subset_k, stream, barrier, pw, dev)
+        ms_pl = max_over_ranks(est_ms, dist, dev)
+        ps = 1
+        value_pl = job_throughput(ms_pl, 1, world, 1)
+        # the chosen form on the same subset grid, against the plain K there (every entry)
+        sub_ch = Runner(snk, [subp], chosen_opts, False, dev, stream, learned)
+        sub_ch.step()
+        torch.cuda.synchronize()
+        err_ch_pl_sub = float(np.max(np.abs(sub_ch.Ks()[0] - K_sub)))
+        sub_ch.close()
+        K_pl = None
+        pairs_pl = plain_info["pairs_kept_full"]
+    else:
+        pl = Runner(snk, probs, dict(PLAIN), False, dev, stream)
+        ps = args.plain_steps if args.plain_steps is not None else args.steps
+        ms_pl, acc_pl = timed(pl, ps, pw, stream, barrier)
+        ms_pl = max_over_ranks(ms_pl, dist, dev) / ps
+        value_pl = job_throughput(ms_pl * ps, ps, world, n_mol)
+        K_pl = pl.Ks()
+        pairs_pl = sum(s["pairs_kept"] for s in pl.stats())
+        pl.close()
+        plain_info = {"method": f"full plain FP64 builds, {ps} timed after {pw} warm-up"}
 
-    dK_ch_pl = max(float(np.max(np.abs(a - b))) for a, b in zip(K_ch, K_pl))
+    dK_ch_pl = max(float(np.max(np.abs(a - b))) for a, b in zip(K_ch, K_pl)) if K_pl is not None else None
     err_ch = golden_err(args.workload, K_ch[0]) if not batch else None
-    err_pl = golden_err(args.workload, K_pl[0]) if not batch else None
+    err_pl = golden_err(args.workload, K_pl[0]) if (not batch and K_pl is not None) else None
 
     # ---- rooflines of the chosen step's kernels (library events, same stream)
     n = args.steps
@@ -475,7 +577,28 @@ def main():
         else:
             kern["fgemm_kgemm_fp64"] = {"ms_per_step": gms / n, "bound": "alu", "achieved": a, "peak": FP64_PEAK,
                                         "unit": "TFLOP/s", "frac": a / FP64_PEAK}
-    dom = max(kern, key=lambda k: kern[k]["ms_per_step"]) if kern else None
+    if acc.get("ms_collocation", 0) > 0 and acc.get("colloc_bytes", 0) > 0:
+        a = acc["colloc_bytes"] / (acc["ms_collocation"] * 1e-3) / 1e9
+        kern["collocation_kernel"] = {"ms_per_step": acc["ms_collocation"] / n, "bound": "hbm", "achieved": a,
+                                      "peak": HBM_PEAK, "unit": "GB/s", "frac": a / HBM_PEAK,
+                                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if HBM_MEASURED else
+                                      "fallback 6800 GB/s"}
+    # the plain arm's FP64 integral kernel against the FP64 pipe
+    plain_kernel = None
+    if subset_k:
+        if plain_info["ms_integrals_subset"] > 0:
+            a = plain_info["integral_flops_subset"] / (plain_info["ms_integrals_subset"] * 1e-3) / 1e12
+            plain_kernel = {"ms": plain_info["ms_integrals_subset"], "achieved": a, "unit": "TFLOP/s",
+                            "peak": FP64_PEAK, "frac": a / FP64_PEAK, "frac_of_measured_dfma": a / FP64_DFMA_MEASURED,
+                            "on": "the plain subset build"}
+    elif acc_pl and acc_pl["ms_integrals"] > 0:
+        a = acc_pl["integral_flops"] / (acc_pl["ms_integrals"] * 1e-3) / 1e12
+        plain_kernel = {"ms_per_step": acc_pl["ms_integrals"] / ps, "achieved": a, "unit": "TFLOP/s",
+                        "peak": FP64_PEAK, "frac": a / FP64_PEAK, "frac_of_measured_dfma": a / FP64_DFMA_MEASURED}
+    if plain_kernel:
+        kern["plain_integral_kernel_fp64"] = dict(plain_kernel, bound="alu")
+    dom = max((k for k in kern if k != "plain_integral_kernel_fp64"), key=lambda k: kern[k]["ms_per_step"],
+              default=None)
     roof = None
     if dom:
         d = kern[dom]
@@ -493,10 +616,10 @@ def main():
         "config": workload_config(args.workload, probs),
         "form": form,
         "max_abs_dK": {"chosen_vs_oracle_entries": err_ch, "plain_vs_oracle_entries": err_pl,
-                       "chosen_vs_plain_full": dK_ch_pl,
+                       "chosen_vs_plain_full": dK_ch_pl, "chosen_vs_plain_on_plain_subset_grid": err_ch_pl_sub,
                        "stated_tolerance": 1e-10 if batch else 1e-8},
-        "plain_fp64": {"value": value_pl, "unit": unit, "ms_per_step": ms_pl / ps, "steps": ps, "warmup": pw,
-                       "pairs_kept": sum(s["pairs_kept"] for s in st_pl)},
+        "plain_fp64": dict({"value": value_pl, "unit": unit, "ms_per_step": ms_pl, "steps": ps, "warmup": pw,
+                            "pairs_kept": pairs_pl}, **plain_info),
         "speedup_vs_plain_fp64": value / value_pl,
         "integrals_per_s": acc["integrals"] / (ms * 1e-3),
         "phases_ms_per_step": {k: acc[k] / n for k in ("ms_screen", "ms_collocation", "ms_fgemm", "ms_integrals",
@@ -513,7 +636,8 @@ def main():
         "roofline": roof,
         "clocks": clocks,
         "gpu_launches": int(acc["kernel_launches"]),
-        "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": e2e_steps},
     }
     if batch:
         line["autotuned_pairs_per_tile"] = ch.runs

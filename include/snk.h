@@ -170,6 +170,8 @@ typedef struct {
   double gemm_flops_hi;        /* the part of gemm_flops on high-tier columns / rows
                                   (SNK_GEMM_SPLIT; equal to gemm_flops otherwise)   */
   double ms_integrals_class_fp32[6]; /* FP32-tier kernel time per class            */
+  double colloc_bytes;         /* bytes of X the collocation kernel writes per build:
+                                  sum_j ldq_j |B_j| x 8 (ldq_j = |Q_j| padded to 128) */
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,
@@ -238,6 +240,29 @@ int snk_autotune(snk_ctx *ctx, int32_t *runs);
 /* Stream for all later work on this handle (a cudaStream_t; NULL = the legacy
  * default stream). */
 int snk_set_stream(snk_ctx *ctx, void *stream);
+
+/* Device memory hook (Sec. II.F, Alg. 1: the workspaces of the batches that
+ * saturate device memory).  After this call every device buffer of the
+ * handle -- geometry tables, density, screen lists, batch workspaces, K --
+ * comes from alloc(bytes, user) and goes back through free(ptr, user), so a
+ * host such as PyTorch's caching allocator owns all of the handle's memory.
+ *   - alloc must return device memory of the handle's device, aligned to 256
+ *     bytes, or NULL; NULL makes the call that needed the memory return
+ *     SNK_ERR_OOM (the handle stays usable: set_density again, e.g. after a
+ *     different allocator was set).  A block that is not 256-byte aligned is
+ *     handed back and the call returns SNK_ERR_CUDA.
+ *   - free is called only after the handle's stream has drained, so the block
+ *     can be reused at once; it is also called from snk_destroy.
+ *   - alloc = free = NULL goes back to cudaMalloc / cudaFree.  One of them NULL
+ *     alone is SNK_ERR_INVALID_ARG.
+ * Buffers that exist already are moved into the new allocator's memory (on
+ * failure SNK_ERR_OOM and the handle keeps its old buffers); the loaded
+ * density is dropped, so snk_set_density must be called again before a
+ * build.  Every block is released the way it was obtained, even when the
+ * allocator changes later. */
+typedef void *(*snk_alloc_fn)(size_t bytes, void *user);
+typedef void (*snk_free_fn)(void *ptr, void *user);
+int snk_set_allocator(snk_ctx *ctx, snk_alloc_fn alloc, snk_free_fn free, void *user);
 
 int snk_get_stats(const snk_ctx *ctx, snk_stats *stats);
 int64_t snk_n_functions(const snk_ctx *ctx);
@@ -327,7 +352,10 @@ int snk_debug_batches(snk_ctx *ctx, int64_t *n_batches, int32_t *counts, int64_t
  * the library holds until the process exits.
  *   - n > 4096 returns SNK_ERR_INVALID_ARG; split larger point sets.
  *   - The first call on a device looks the scratch address up (set-up, once
- *     per device); make that first call before any stream capture.
+ *     per device) and keeps it for the life of the process's CUDA context;
+ *     make that first call before any stream capture.
+ *   - The current device must be the handle's device (SNK_ERR_BAD_STATE
+ *     otherwise).
  *   - The work is enqueued on the handle's stream (snk_set_stream) and the
  *     call returns without waiting.
  *   - All calls share the one scratch array and it keeps the last call's

@@ -62,10 +62,12 @@ def lib():
             L.oracle_snk_K.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, _D, ctypes.c_int]
             L.oracle_snk_K_entries.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int,
                                                             _I, _I, _D, ctypes.c_int]
+            L.oracle_g_rows.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int, _I, _D,
+                                                     ctypes.c_int]
             L.oracle_mlp_forward.argtypes = [_D, _D, ctypes.c_long, _D]
             L.oracle_mlp_loss_grad.argtypes = [_D, _D, _D, ctypes.c_long, ctypes.c_double, _D, _D]
             for name in ("oracle_normalise", "oracle_collocation", "oracle_shell_A", "oracle_eri_K",
-                         "oracle_snk_K", "oracle_snk_K_entries", "oracle_mlp_forward", "oracle_mlp_loss_grad"):
+                         "oracle_snk_K", "oracle_snk_K_entries", "oracle_g_rows", "oracle_mlp_forward", "oracle_mlp_loss_grad"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -184,6 +186,40 @@ def snk_K_entries(basis, grid, P, mu, nu, nthreads: int = 0) -> np.ndarray:
                                       int(mu.shape[0]), _ip(mu), _ip(nu), _dp(out), int(nthreads)),
            "snk_K_entries")
     return out
+
+
+def snk_K_entries_blocked(basis, grid, P, mu, nu, block: int = 16384, nthreads: int = 0,
+                          progress=None) -> np.ndarray:
+    """The same entries as snk_K_entries, over blocks of grid points: per
+    block Phi (Eq. collocation, oracle C), F = Phi P (Eq. fmat) as a library
+    matrix product, the G rows of the wanted functions (Eq. gmat, oracle C),
+    and the partial sums Kt_{mu nu} = sum_i G_{mu i} Phi_{nu i} (Eq. usym_k);
+    finally K = (Kt + Kt^T) / 2 per entry (Eq. sn_k).  For grids where
+    streaming P once per point would dominate."""
+    keep, args = _basis_args(basis)
+    mu, nu = _i32(mu), _i32(nu)
+    P = _f64(P)
+    funs = np.unique(np.concatenate([mu, nu])).astype(np.int32)
+    col = {int(f): t for t, f in enumerate(funs)}
+    im = np.array([col[int(x)] for x in mu], dtype=np.int64)
+    inn = np.array([col[int(x)] for x in nu], dtype=np.int64)
+    s1 = np.zeros(mu.shape[0])
+    s2 = np.zeros(mu.shape[0])
+    n = grid.w.shape[0]
+    for i0 in range(0, n, block):
+        xyz = _f64(grid.xyz[i0:i0 + block]).reshape(-1, 3)
+        w = _f64(grid.w[i0:i0 + block])
+        phi = collocation(basis, xyz)                 # (b, nf)
+        F = np.ascontiguousarray(phi @ P.T)            # F[i][lam] = sum_nu P_{lam nu} Phi_{nu i}
+        G = np.zeros((w.shape[0], funs.shape[0]))
+        _check(lib().oracle_g_rows(*args, ctypes.c_long(w.shape[0]), _dp(xyz), _dp(w), _dp(F),
+                                   int(funs.shape[0]), _ip(funs), _dp(G), int(nthreads)), "g_rows")
+        ph = phi[:, funs]
+        s1 += np.einsum("ik,ik->k", G[:, im], ph[:, inn])
+        s2 += np.einsum("ik,ik->k", G[:, inn], ph[:, im])
+        if progress is not None:
+            progress(min(n, i0 + block), n)
+    return 0.5 * (s1 + s2)
 
 
 MLP_WEIGHTS = 16 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1

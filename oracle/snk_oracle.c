@@ -724,6 +724,43 @@ int oracle_snk_K_entries(int n_shells, const int *l, const int *nprim, const dou
   return 0;
 }
 
+/* The G rows (Eq. gmat) of the listed functions at every point of a block,
+ * given the block's F (Eq. fmat: F[i][lambda], npts x nf row-major), which
+ * the caller forms with a library matrix product F = Phi P.  G is written
+ * npts x nfun row-major: G[i][t] = G_{fun[t]}(r_i).  Used by the blocked
+ * entries mode for large grids, where streaming P once per point (the
+ * per-point routines above) would dominate the oracle's time. */
+int oracle_g_rows(int n_shells, const int *l, const int *nprim, const double *center, const double *exps,
+                  const double *coefs, long npts, const double *xyz, const double *w, const double *F,
+                  int nfun, const int *fun, double *G, int nthreads) {
+  obasis b;
+  if (obasis_init(&b, n_shells, l, nprim, center, exps, coefs)) return -1;
+  int nf = b.n_func, nt = n_threads_or_default(nthreads);
+  char *want = (char *)calloc(n_shells, 1);
+  for (int t = 0; t < nfun; ++t) {
+    if (fun[t] < 0 || fun[t] >= nf) {
+      free(want);
+      obasis_free(&b);
+      return -1;
+    }
+    for (int s = 0; s < n_shells; ++s)
+      if (fun[t] >= b.foff[s] && fun[t] < b.foff[s + 1]) want[s] = 1;
+  }
+#pragma omp parallel num_threads(nt)
+  {
+    double *Gp = (double *)malloc(sizeof(double) * nf);
+#pragma omp for schedule(dynamic, 16)
+    for (long i = 0; i < npts; ++i) {
+      g_point(&b, xyz + 3 * i, w[i], F + (size_t)i * nf, want, Gp);
+      for (int t = 0; t < nfun; ++t) G[(size_t)i * nfun + t] = Gp[fun[t]];
+    }
+    free(Gp);
+  }
+  free(want);
+  obasis_free(&b);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* MLP of the learned block screen: plain FP64 forward, loss and gradient   */
 /* by backpropagation, for checks of the GPU training kernels.              */

@@ -46,7 +46,7 @@ SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molec
            "snk_n_functions", "snk_last_error", "snk_status_string", "snk_destroy", "snk_debug_boys",
            "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc",
            "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad",
-           "snk_set_density_multi", "snk_build_K_multi"]
+           "snk_set_density_multi", "snk_build_K_multi", "snk_set_allocator"]
 MLP_FEATURES, MLP_WEIGHTS = 16, 9473
 MAX_DENSITIES = 2
 
@@ -90,12 +90,15 @@ class SnkStats(ctypes.Structure):
                 ("flops_class", ctypes.c_double * 6), ("pairs_kept_fp32", ctypes.c_int64),
                 ("integrals_fp32", ctypes.c_double), ("flops_fp32", ctypes.c_double),
                 ("ms_integrals_fp32", ctypes.c_double), ("pairs_learned_skipped", ctypes.c_int64),
-                ("gemm_flops_hi", ctypes.c_double), ("ms_integrals_class_fp32", ctypes.c_double * 6)]
+                ("gemm_flops_hi", ctypes.c_double), ("ms_integrals_class_fp32", ctypes.c_double * 6),
+                ("colloc_bytes", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I32 = ctypes.POINTER(ctypes.c_int32)
 _P = ctypes.c_void_p
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 def lib_path() -> str:
@@ -128,6 +131,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
             L.snk_set_density_multi.argtypes = [_P, ctypes.c_int32, _P]
             L.snk_build_K_multi.argtypes = [_P, _P]
             L.snk_set_stream.argtypes = [_P, _P]
+            L.snk_set_allocator.argtypes = [_P, ALLOC_FN, FREE_FN, _P]
             L.snk_get_stats.argtypes = [_P, ctypes.POINTER(SnkStats)]
             L.snk_n_functions.argtypes = [_P]
             L.snk_n_functions.restype = ctypes.c_int64
@@ -194,6 +198,15 @@ def debug_boys(T, nmax: int) -> np.ndarray:
 
 def _is_cuda_tensor(x) -> bool:
     return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _current_device():
+    """The CUDA device current in torch (the one snk_create binds the handle to)."""
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:
+        return None
 
 
 def _fptr(a):
@@ -303,6 +316,8 @@ class Engine:
         self.packed = sum(n * n for n in self.nfs)
         self.n_dens = 1
         self._stream = None
+        self._alloc_cbs = None      # ctypes callbacks of set_allocator, kept alive with the handle
+        self.device_index = _current_device()
 
     # -- plumbing ---------------------------------------------------------
     def _check(self, rc, what):
@@ -312,8 +327,59 @@ class Engine:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().snk_destroy(self._h)
+            lib().snk_destroy(self._h)   # may still call the allocator's free
             self._h = None
+        self._alloc_cbs = None
+
+    def set_allocator(self, alloc=None, free=None):
+        """snk_set_allocator: alloc(nbytes) -> device address (int, 0 for
+        failure) and free(address) take over every device buffer of the handle;
+        both None goes back to cudaMalloc.  The loaded density is dropped (call
+        set_density again).  An exception inside alloc counts as a failed
+        allocation (SNK_ERR_OOM)."""
+        if (alloc is None) != (free is None):
+            raise ValueError("give both alloc and free, or neither")
+        if alloc is None:
+            self._check(lib().snk_set_allocator(self._h, ALLOC_FN(), FREE_FN(), None), "snk_set_allocator")
+            self._alloc_cbs = None
+            return
+
+        def _a(nbytes, user):
+            try:
+                return int(alloc(int(nbytes)) or 0) or None
+            except Exception:
+                return None
+
+        def _f(ptr, user):
+            try:
+                free(int(ptr))
+            except Exception:
+                pass
+
+        cbs = (ALLOC_FN(_a), FREE_FN(_f))
+        self._check(lib().snk_set_allocator(self._h, cbs[0], cbs[1], None), "snk_set_allocator")
+        old, self._alloc_cbs = self._alloc_cbs, cbs
+        del old
+
+    def use_torch_allocator(self):
+        """Route every device buffer of the handle through PyTorch's caching
+        allocator (torch.empty on the engine's device), so that torch owns and
+        accounts all of the library's memory."""
+        import torch
+        dev = torch.device("cuda", self.device_index)
+        blocks = {}
+
+        def alloc(nbytes):
+            t = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            blocks[t.data_ptr()] = t
+            return t.data_ptr()
+
+        def free(ptr):
+            blocks.pop(ptr, None)
+
+        self.set_allocator(alloc, free)
+        self._torch_blocks = blocks
+        return blocks
 
     def __del__(self):
         try:
@@ -425,9 +491,24 @@ class Engine:
         cannot allocate device memory.  xyz (n, 3) and out (n, n_a, n_b) are
         contiguous float64 CUDA tensors owned by the caller; n <= 4096.  The
         work is enqueued on the engine's stream; the call does not wait."""
-        assert _is_cuda_tensor(xyz) and _is_cuda_tensor(out)
-        assert xyz.is_contiguous() and out.is_contiguous() and xyz.element_size() == 8 and out.element_size() == 8
+        import torch
+        if not (_is_cuda_tensor(xyz) and _is_cuda_tensor(out)):
+            raise ValueError("xyz and out must be CUDA tensors")
+        if xyz.dtype != torch.float64 or out.dtype != torch.float64:
+            raise ValueError("xyz and out must be float64")
+        if not (xyz.is_contiguous() and out.is_contiguous()):
+            raise ValueError("xyz and out must be contiguous")
+        if xyz.device.index != self.device_index or out.device.index != self.device_index:
+            raise ValueError(f"xyz and out must be on cuda:{self.device_index}, the engine's device")
+        if not (0 <= int(sa) < self._l.shape[0] and 0 <= int(sb) < self._l.shape[0]):
+            raise ValueError(f"shell index out of range 0..{self._l.shape[0] - 1}")
+        na = (int(self._l[sa]) + 1) * (int(self._l[sa]) + 2) // 2
+        nb = (int(self._l[sb]) + 1) * (int(self._l[sb]) + 2) // 2
+        if xyz.dim() != 2 or xyz.shape[1] != 3:
+            raise ValueError(f"xyz must be (n, 3), got {tuple(xyz.shape)}")
         n = xyz.shape[0]
+        if tuple(out.shape) != (n, na, nb):
+            raise ValueError(f"out must be {(n, na, nb)}, got {tuple(out.shape)}")
         self._check(lib().snk_shell_A_noalloc(self._h, int(sa), int(sb), int(n), _P(xyz.data_ptr()),
                                               _P(out.data_ptr())), "snk_shell_A_noalloc")
         return out

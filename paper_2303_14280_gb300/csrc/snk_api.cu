@@ -16,6 +16,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "snk_internal.h"
@@ -24,21 +26,69 @@ using namespace snk;
 
 namespace {
 
+// Device allocator of a handle: the caller's hook (snk_set_allocator) or, with
+// alloc == nullptr, cudaMalloc / cudaFree.  Memory from the hook is handed
+// back only after the handle's stream has drained, so a stream-ordered pool
+// may reuse it at once.
+struct Allocator {
+  snk_alloc_fn alloc = nullptr;
+  snk_free_fn free = nullptr;
+  void* user = nullptr;
+  const cudaStream_t* stream = nullptr;
+};
+
+// A device buffer that remembers how its block was allocated, so that it is
+// always released the same way even after the handle's allocator changed.
 template <class T>
 struct DevBuf {
+  using value_type = T;
   T* p = nullptr;
   size_t n = 0;
-  ~DevBuf() {
-    if (p) cudaFree(p);
+  const Allocator* al = nullptr;  // allocator for future blocks (nullptr: cudaMalloc)
+  Allocator owner{};              // how p was allocated (owner.alloc == nullptr: cudaMalloc)
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) {
+      if (owner.alloc) {
+        if (owner.stream) cudaStreamSynchronize(*owner.stream);
+        owner.free(p, owner.user);
+      } else {
+        cudaFree(p);
+      }
+    }
+    p = nullptr;
+    n = 0;
+    owner = Allocator{};
+  }
+  // a new block of count elements from allocator a (or cudaMalloc), not yet owned
+  static cudaError_t raw(const Allocator* a, size_t count, T** out) {
+    const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+    *out = nullptr;
+    if (a && a->alloc) {
+      void* q = a->alloc(bytes, a->user);
+      if (!q) return cudaErrorMemoryAllocation;
+      if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {  // the kernels rely on cudaMalloc's alignment
+        a->free(q, a->user);
+        return cudaErrorMisalignedAddress;
+      }
+      *out = static_cast<T*>(q);
+      return cudaSuccess;
+    }
+    return cudaMalloc(out, bytes);
   }
   cudaError_t ensure(size_t count) {
     if (count <= n && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-    cudaError_t e = cudaMalloc(&p, sizeof(T) * std::max<size_t>(count, 1));
-    if (e == cudaSuccess) n = count;
-    return e;
+    release();
+    T* q = nullptr;
+    cudaError_t e = raw(al, count, &q);
+    if (e != cudaSuccess) return e;
+    p = q;
+    n = count;
+    owner = (al && al->alloc) ? *al : Allocator{};
+    return cudaSuccess;
   }
 };
 
@@ -55,6 +105,7 @@ struct snk_ctx {
   snk_options opt;
   int device = 0, num_sms = 0;
   cudaStream_t stream = nullptr;
+  Allocator alloc;  // device memory of every buffer below (snk_set_allocator)
   std::string err;
   int nbatch = 0;
   int64_t ws_budget = 0;
@@ -117,7 +168,25 @@ struct snk_ctx {
   bool built = false, built_graph = false;
   snk_stats st;
 
+  // every device buffer of the handle, for binding and moving them
+  template <class F>
+  void for_each_buffer(F f) {
+    f(l), f(poff), f(nprim), f(foff), f(fshell), f(bshell), f(bshell_col), f(xfunc);
+    f(center), f(exps), f(d), f(fcomp), f(xyz), f(w), f(boys), f(bound), f(qbound), f(bcenter), f(bradius);
+    f(phit_f), f(phit_b);
+    f(boys_f), f(boys_ds), f(prims_ds), f(pair_ab), f(prims_f32);
+    f(pairs), f(prims), f(mols), f(mlp_w), f(shell_feat), f(keep);
+    f(P), f(Pscr), f(ft), f(sym), f(Khat), f(K), f(P2);
+    f(counts), f(list), f(list2), f(sfunc), f(colmap), f(tickets), f(ppcounts), f(sflag), f(list_off), f(tstart);
+    f(batch), f(tiles), f(ws), f(ws32);
+  }
+  snk_ctx() {
+    alloc.stream = &stream;
+    for_each_buffer([this](auto& b) { b.al = &alloc; });
+  }
+
   ~snk_ctx() {
+    if (gstream) cudaStreamSynchronize(gstream);
     for (auto e : events) cudaEventDestroy(e);
     if (ev_screen0) cudaEventDestroy(ev_screen0);
     if (ev_screen1) cudaEventDestroy(ev_screen1);
@@ -434,11 +503,12 @@ int screen_and_plan(snk_ctx* c) {
   // counts for the statistics: integrals and algorithmic flops per list
   double per_prim[kNumClasses], per_pair[kNumClasses];
   for (int k = 0; k < kNumClasses; ++k) class_flops(k, &per_prim[k], &per_pair[k]);
-  double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0, gflops_hi = 0.0;
+  double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0, gflops_hi = 0.0, xbytes = 0.0;
   int64_t kept[2] = {0, 0}, pair_points = 0;
   for (int j = 0; j < nb; ++j) {
     gflops += 4.0 * c->n_dens * bd[j].q * (double)bd[j].nB * bd[j].nS;
     gflops_hi += 4.0 * c->n_dens * bd[j].q * (double)bd[j].nB * bd[j].nS_hi;
+    xbytes += 8.0 * bd[j].ldq * (double)bd[j].nB;
     for (int k = 0; k < kNumLists; ++k) {
       const int cls = k % kNumClasses;
       const int la = cls >= 3 ? 2 : (cls >= 1 ? 1 : 0), lb = cls - la * (la + 1) / 2;
@@ -529,6 +599,7 @@ int screen_and_plan(snk_ctx* c) {
   }
   S.gemm_flops = gflops;
   S.gemm_flops_hi = gflops_hi;
+  S.colloc_bytes = xbytes;
   S.n_chunks = (int64_t)c->chunks.size();
   S.workspace_bytes = (int64_t)(c->ws.n * 8 + c->ws32.n * 4);
   float ms = 0.f;
@@ -1135,6 +1206,60 @@ int snk_set_stream(snk_ctx* c, void* stream) {
   return SNK_OK;
 }
 
+int snk_set_allocator(snk_ctx* c, snk_alloc_fn alloc, snk_free_fn free_fn, void* user) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(c, SNK_ERR_INVALID_ARG, "snk_set_allocator: alloc and free must both be set or both be NULL");
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  if (c->gstream) SNK_CK(c, cudaStreamSynchronize(c->gstream));
+  Allocator nal;
+  nal.alloc = alloc;
+  nal.free = alloc ? free_fn : nullptr;
+  nal.user = alloc ? user : nullptr;
+  nal.stream = &c->stream;
+  // move every existing buffer: first all new blocks (all or none), then the copies
+  std::vector<std::pair<void*, size_t>> fresh;
+  cudaError_t err = cudaSuccess;
+  c->for_each_buffer([&](auto& b) {
+    if (err != cudaSuccess || !b.p) return;
+    typename std::remove_reference<decltype(b)>::type::value_type* q = nullptr;
+    err = std::remove_reference<decltype(b)>::type::raw(&nal, b.n, &q);
+    if (err == cudaSuccess) fresh.emplace_back(q, sizeof(*q) * b.n);
+  });
+  if (err != cudaSuccess) {
+    for (auto& f : fresh) {
+      if (nal.alloc)
+        nal.free(f.first, nal.user);
+      else
+        cudaFree(f.first);
+    }
+    return cuda_fail(c, err, "snk_set_allocator: moving the handle's buffers");
+  }
+  size_t k = 0;
+  c->for_each_buffer([&](auto& b) {
+    if (err != cudaSuccess || !b.p) return;
+    auto* q = static_cast<typename std::remove_reference<decltype(b)>::type::value_type*>(fresh[k++].first);
+    err = cudaMemcpyAsync(q, b.p, sizeof(*q) * b.n, cudaMemcpyDeviceToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    const size_t n = b.n;
+    b.release();
+    b.p = q;
+    b.n = n;
+    b.owner = nal.alloc ? nal : Allocator{};
+  });
+  c->alloc = nal;
+  // captured graphs and the screen arguments hold the old addresses
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->graph_valid = false;
+  c->have_density = false;
+  c->built = false;
+  if (err != cudaSuccess) return cuda_fail(c, err, "snk_set_allocator: copying the handle's buffers");
+  return SNK_OK;
+}
+
 int snk_get_stats(const snk_ctx* c, snk_stats* out) {
   if (!c || !out) return SNK_ERR_INVALID_ARG;
   snk_ctx* m = const_cast<snk_ctx*>(c);
@@ -1261,17 +1386,15 @@ static __device__ __align__(256) double g_xi_scratch[kNoAllocMaxPoints * 36];
 std::mutex g_scratch_mutex;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_xi_scratch on the current device, looked up once per
-// device (host code cannot use the symbol's name as a device pointer).
-cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of g_xi_scratch on device dev, which must be the current
+// device; looked up once per device (host code cannot use the symbol's name
+// as a device pointer) and kept for the life of the process's CUDA context.
+cudaError_t scratch_for_device(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_xi_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_xi_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = static_cast<double*>(p);
   }
@@ -1303,8 +1426,13 @@ extern "C" int snk_shell_A_noalloc(snk_ctx* c, int32_t sa, int32_t sb, int64_t n
   if (n > kNoAllocMaxPoints)
     return fail(c, SNK_ERR_INVALID_ARG,
                 "snk_shell_A_noalloc: n exceeds the 4096-point scratch; split the points into calls of at most 4096");
+  int cur = -1;
+  SNK_CK(c, cudaGetDevice(&cur));
+  if (cur != c->device)
+    return fail(c, SNK_ERR_BAD_STATE,
+                "snk_shell_A_noalloc: the current device is not the one the handle was created on");
   double* scratch = nullptr;
-  SNK_CK(c, scratch_for_current_device(&scratch));
+  SNK_CK(c, scratch_for_device(c->device, &scratch));
   if (n == 0) return SNK_OK;
   const int na = ncart(s.l[sa]), nb = ncart(s.l[sb]);
   const int p = pair_id(s, sa, sb);

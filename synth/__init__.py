@@ -15,7 +15,11 @@ Units: coordinates are drawn in Angstrom and returned in bohr.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
+import threading
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -196,9 +200,54 @@ def _becke_s(mu):
     return 0.5 * (1.0 - f)
 
 
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BECKE_SRC = os.path.join(_HERE, "becke.c")
+_BECKE_LIB = os.path.join(_HERE, "_build", "libsynth_becke.so")
+_becke_lib = None
+_becke_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile becke.c (the fused CPU Becke partition) with gcc."""
+    os.makedirs(os.path.dirname(_BECKE_LIB), exist_ok=True)
+    if (not force and os.path.exists(_BECKE_LIB)
+            and os.path.getmtime(_BECKE_LIB) >= os.path.getmtime(_BECKE_SRC)):
+        return _BECKE_LIB
+    tmp = _BECKE_LIB + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-o", tmp, _BECKE_SRC, "-lm"],
+                   check=True)
+    os.replace(tmp, _BECKE_LIB)
+    return _BECKE_LIB
+
+
+def _becke_cpu(points, owner, atoms_xyz):
+    global _becke_lib
+    with _becke_lock:
+        if _becke_lib is None:
+            L = ctypes.CDLL(build())
+            D, I = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+            L.synth_becke.argtypes = [ctypes.c_long, D, I, ctypes.c_int, D, D, ctypes.c_int]
+            L.synth_becke.restype = ctypes.c_int
+            _becke_lib = L
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    own = np.ascontiguousarray(owner, dtype=np.int32)
+    A = np.ascontiguousarray(atoms_xyz, dtype=np.float64)
+    out = np.empty(pts.shape[0])
+    D = ctypes.POINTER(ctypes.c_double)
+    rc = _becke_lib.synth_becke(pts.shape[0], pts.ctypes.data_as(D), own.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                A.shape[0], A.ctypes.data_as(D), out.ctypes.data_as(D), 0)
+    if rc != 0:
+        raise RuntimeError(f"synth_becke failed (rc={rc})")
+    return out
+
+
 def becke_weights(points, owner, atoms_xyz, chunk: int = 4096, device=None):
     """Becke fuzzy-cell partition weight of each point for its own atom
-    (three-fold iterated polynomial, no atomic-size adjustment)."""
+    (three-fold iterated polynomial, no atomic-size adjustment).  On the CPU
+    (device None) the fused C routine of becke.c computes it; on a GPU the
+    same formula runs as torch tensor operations."""
+    if device is None:
+        return _becke_cpu(points, owner, atoms_xyz)
     import torch
     dev = torch.device(device) if device is not None else torch.device("cpu")
     A = torch.as_tensor(atoms_xyz, dtype=torch.float64, device=dev)
