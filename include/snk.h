@@ -94,7 +94,7 @@ typedef struct {
 
 typedef enum { SNK_PREC_FP64 = 0, SNK_PREC_MIXED = 1 } snk_precision;
 typedef enum { SNK_SCREEN_NONE = 0, SNK_SCREEN_LINK = 1, SNK_SCREEN_LEARNED = 2 } snk_screen_mode;
-typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1, SNK_GEMM_SPLIT = 2 } snk_gemm_mode;
+typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1, SNK_GEMM_SPLIT = 2, SNK_GEMM_TC = 3 } snk_gemm_mode;
 
 typedef struct {
   double eps_basis;        /* epsilon_B of Eq. (basis_screen); <= 0 keeps all   */
@@ -126,6 +126,15 @@ typedef struct {
                               in a batch's FP64-tier pairs and split-TF32 tensor-core
                               products (FP32 partial sums of 64 terms folded into
                               double-FP32) for the shells only FP32-tier pairs use;
+                              SNK_GEMM_TC, both products on the tcgen05 tensor cores
+                              as sums of bf16 slice products: every operand cut into
+                              slices on a fixed-point grid per row and run of 256
+                              reduction indices, each run's low-order products
+                              accumulated exactly in FP32 and the runs summed in
+                              double-FP32 -- 5 slices (15 products, ~2^-40 of the
+                              run maxima) for the F columns and G rows of shells in
+                              a batch's FP64-tier pairs, 3 slices (6 products,
+                              ~2^-24) for the rest; single-molecule handles;
                               not combined with tensor_gemms (SNK_ERR_INVALID_ARG) */
   int32_t ds_integrals;    /* mixed form: 1 runs the integrals of the pairs above
                               fp32_bound in double-FP32 arithmetic (hi + lo float
@@ -142,6 +151,9 @@ typedef struct {
                               double-FP32) tier whose predicted log10 contribution
                               is below this moves to the FP32 tier; default -99
                               (off)                                             */
+  int32_t tc_slices_hi;    /* SNK_GEMM_TC: bf16 slices per operand for the high-tier
+                              columns / rows, 3..6 (default 5: 15 slice products)  */
+  int32_t tc_slices_lo;    /* SNK_GEMM_TC: the same for the rest, 3..6 (default 3) */
   double reserved[3];
 } snk_options;
 
@@ -172,6 +184,12 @@ typedef struct {
   double ms_integrals_class_fp32[6]; /* FP32-tier kernel time per class            */
   double colloc_bytes;         /* bytes of X the collocation kernel writes per build:
                                   sum_j ldq_j |B_j| x 8 (ldq_j = |Q_j| padded to 128) */
+  double ms_gemm_split;        /* last build: operand preparation of both products
+                                  (slicing, splitting, the FP32-tier G merge)       */
+  double ms_gemm_hi;           /* last build: both products, high-tier columns / rows */
+  double ms_gemm_lo;           /* last build: both products, the remaining ones      */
+  double gemm_tc_flops;        /* SNK_GEMM_TC: bf16 tensor-core flops issued per build
+                                  (2 M N K per slice product, padded tile sizes)     */
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,
@@ -332,6 +350,14 @@ int snk_debug_shell_A(snk_ctx *ctx, int32_t sa, int32_t sb, int64_t n, const dou
 /* Host-side rigorous bound of max_r |A_{mu lam}(r)| over the shell pair
  * (sa, sb) (the A-tilde of Eq. exx_fmat_approx). */
 int snk_debug_pair_bound(snk_ctx *ctx, int32_t sa, int32_t sb, double *bound);
+
+/* The split-product tensor-core GEMM of SNK_GEMM_TC on plain matrices:
+ * C = A B^T with A (M x K) and B (N x K) row-major host doubles, C (M x N)
+ * row-major host, each operand cut into `slices` (3..6) bf16 slices per row and
+ * run of 256 columns (Sec. II.C, Eq. fmat, and Sec. II.D, Eq. usym_k, are
+ * this product with the operands of a grid batch). */
+int snk_debug_tc_gemm(int32_t M, int32_t N, int32_t K, const double *A, const double *B, int32_t slices,
+                      double *C);
 
 /* Octree batches: n_batches, then for each batch the point count; the
  * permutation from batch order to input order (n_points entries). */

@@ -26,7 +26,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Engine", "SnkError", "lib", "options", "debug_boys", "SYMBOLS"]
+__all__ = ["Engine", "SnkError", "lib", "options", "debug_boys", "debug_tc_gemm", "SYMBOLS"]
 
 _lib = None
 _lock = threading.Lock()
@@ -36,7 +36,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported input", -3: "density
           -4: "bad call order", -5: "out of memory", -6: "CUDA error", -7: "device wait timed out"}
 SCREEN = {"none": 0, "link": 1, "learned": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
-GEMM = {"fp64": 0, "df32": 1, "split": 2}
+GEMM = {"fp64": 0, "df32": 1, "split": 2, "tc": 3}
 LISTS = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
 # every entry point declared in include/snk.h
@@ -46,7 +46,7 @@ SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molec
            "snk_n_functions", "snk_last_error", "snk_status_string", "snk_destroy", "snk_debug_boys",
            "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc",
            "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad",
-           "snk_set_density_multi", "snk_build_K_multi", "snk_set_allocator"]
+           "snk_set_density_multi", "snk_build_K_multi", "snk_set_allocator", "snk_debug_tc_gemm"]
 MLP_FEATURES, MLP_WEIGHTS = 16, 9473
 MAX_DENSITIES = 2
 
@@ -76,7 +76,8 @@ class SnkOptions(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("tensor_gemms", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("learned_skip", ctypes.c_double), ("gemm", ctypes.c_int32), ("ds_integrals", ctypes.c_int32),
                 ("fp32_g64", ctypes.c_int32), ("fp32_hrr_ds", ctypes.c_int32),
-                ("learned_fp32", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
+                ("learned_fp32", ctypes.c_double), ("tc_slices_hi", ctypes.c_int32),
+                ("tc_slices_lo", ctypes.c_int32), ("reserved", ctypes.c_double * 3)]
 
 
 class SnkStats(ctypes.Structure):
@@ -91,7 +92,8 @@ class SnkStats(ctypes.Structure):
                 ("integrals_fp32", ctypes.c_double), ("flops_fp32", ctypes.c_double),
                 ("ms_integrals_fp32", ctypes.c_double), ("pairs_learned_skipped", ctypes.c_int64),
                 ("gemm_flops_hi", ctypes.c_double), ("ms_integrals_class_fp32", ctypes.c_double * 6),
-                ("colloc_bytes", ctypes.c_double)]
+                ("colloc_bytes", ctypes.c_double), ("ms_gemm_split", ctypes.c_double),
+                ("ms_gemm_hi", ctypes.c_double), ("ms_gemm_lo", ctypes.c_double), ("gemm_tc_flops", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -142,6 +144,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
             L.snk_destroy.argtypes = [_P]
             L.snk_destroy.restype = None
             L.snk_debug_boys.argtypes = [ctypes.c_int64, _D, ctypes.c_int, _D]
+            L.snk_debug_tc_gemm.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _D, _D, ctypes.c_int32,
+                                            _D]
             L.snk_debug_shell_A.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D]
             L.snk_debug_pair_bound.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _D]
             L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), _I32, ctypes.c_int64,
@@ -162,7 +166,7 @@ def options(**kw) -> SnkOptions:
     """snk_options from the library defaults and keyword overrides: any field
     of snk_options (include/snk.h), `eps` for eps_basis = eps_E = eps_K, and
     names for screen ("none", "link", "learned"), precision ("fp64", "mixed")
-    and gemm ("fp64", "df32", "split").  Unknown keys raise ValueError."""
+    and gemm ("fp64", "df32", "split", "tc").  Unknown keys raise ValueError."""
     o = SnkOptions()
     lib().snk_options_default(ctypes.byref(o))
     fields = {f[0] for f in SnkOptions._fields_} - {"reserved"}
@@ -194,6 +198,19 @@ def debug_boys(T, nmax: int) -> np.ndarray:
     if rc != SNK_OK:
         raise SnkError(rc)
     return out
+
+
+def debug_tc_gemm(A, B, slices=5) -> np.ndarray:
+    """C = A B^T by the split-product tensor-core GEMM (test export)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if A.ndim != 2 or B.ndim != 2 or A.shape[1] != B.shape[1]:
+        raise ValueError("A (M, K) and B (N, K) with the same K")
+    C = np.zeros((A.shape[0], B.shape[0]))
+    rc = lib().snk_debug_tc_gemm(A.shape[0], B.shape[0], A.shape[1], _dptr(A), _dptr(B), int(slices), _dptr(C))
+    if rc != SNK_OK:
+        raise SnkError(rc, "snk_debug_tc_gemm")
+    return C
 
 
 def _is_cuda_tensor(x) -> bool:

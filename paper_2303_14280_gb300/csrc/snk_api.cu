@@ -96,7 +96,8 @@ struct DevBuf {
 // the autotuner replaces these per list
 constexpr int kPairsPerTile[kNumClasses] = {64, 32, 16, 16, 8, 8};
 constexpr int kRunCandidates[] = {2, 4, 8, 16, 32, 64, 128};
-constexpr int kPhaseEvents = 3 + kNumLists;  // per chunk: collocation, F GEMM, integral lists, K GEMM
+// per chunk: collocation, F operands, F high tier, F rest, integral lists, K operands, K high tier, K rest
+constexpr int kPhaseEvents = 7 + kNumLists;
 
 }  // namespace
 
@@ -140,6 +141,11 @@ struct snk_ctx {
   DevBuf<Tile> tiles;
   DevBuf<double> ws;
   DevBuf<float> ws32;
+  // tensor-core products (SNK_GEMM_TC): bf16 slice arena, split and product jobs, error flag
+  DevBuf<uint8_t> arena;
+  DevBuf<OzSplitJob> ozsplit;
+  DevBuf<OzGemmJob> ozjobs;
+  DevBuf<int> ozerr;
   std::vector<int> hcounts;
   std::vector<long long> hpp;
   std::vector<int64_t> hlist_off;
@@ -150,6 +156,10 @@ struct snk_ctx {
     int64_t bytes = 0, xn = 0, goff = 0, gbytes = 0, g32off = 0, g32n = 0;
     int max_ldq = 0, max_nS = 0, max_nB = 0, max_nBshell = 0;
     int64_t tile_off[kNumLists] = {0}, tile_n[kNumLists] = {0};
+    // SNK_GEMM_TC: split jobs of the F and K phases, product jobs of F hi, F lo, K hi, K lo
+    int ozs_off[2] = {0, 0}, ozs_n[2] = {0, 0}, ozs_rows[2] = {0, 0}, ozs_k[2] = {0, 0};
+    int ozg_off[4] = {0, 0, 0, 0}, ozg_n[4] = {0, 0, 0, 0}, ozg_tiles[4] = {0, 0, 0, 0};
+    int64_t arena_bytes = 0;
   };
   std::vector<Chunk> chunks;
   int max_ctas[kNumLists] = {0};
@@ -178,7 +188,7 @@ struct snk_ctx {
     f(pairs), f(prims), f(mols), f(mlp_w), f(shell_feat), f(keep);
     f(P), f(Pscr), f(ft), f(sym), f(Khat), f(K), f(P2);
     f(counts), f(list), f(list2), f(sfunc), f(colmap), f(tickets), f(ppcounts), f(sflag), f(list_off), f(tstart);
-    f(batch), f(tiles), f(ws), f(ws32);
+    f(batch), f(tiles), f(ws), f(ws32), f(arena), f(ozsplit), f(ozjobs), f(ozerr);
   }
   snk_ctx() {
     alloc.stream = &stream;
@@ -348,8 +358,121 @@ void set_max_ctas(snk_ctx* c) {
   c->ctas_nd = c->n_dens;
 }
 
+int check_device_flags(snk_ctx* c);
+
+// Split and product jobs of the tensor-core GEMMs (SNK_GEMM_TC) for every
+// chunk: where each operand's slices go in the chunk's arena (the F phase and
+// the K phase reuse the same arena), and the (batch, tier, density) products
+// with their tile numbering.  Operands of a tier with no rows are left out.
+int plan_tc(snk_ctx* c, double* tc_flops) {
+  const auto& bd = c->hbatch;
+  const int nd = c->n_dens;
+  const int64_t pk = c->s.packed;
+  const int S_store = std::max(c->opt.tc_slices_hi, c->opt.tc_slices_lo);
+  std::vector<OzSplitJob> sj;
+  std::vector<OzGemmJob> gj;
+  *tc_flops = 0.0;
+  for (auto& ch : c->chunks) {
+    std::vector<OzGemmJob> g[4];
+    for (int phase = 0; phase < 2; ++phase) {
+      ch.ozs_off[phase] = (int)sj.size();
+      int64_t cur = 0;
+      int max_rows = 0, max_k = 0;
+      auto add_split = [&](int mode, int R, int K, int ld, int r0, const BatchDesc& b, int64_t src) -> int64_t {
+        OzSplitJob J{};
+        J.mode = mode;
+        J.R = R;
+        J.K = K;
+        J.S = S_store;
+        J.ld = ld;
+        J.r0 = r0;
+        J.sf_off = b.sfunc_off;
+        J.xf_off = b.xfunc_off;
+        J.src_off = src;
+        J.dst_off = cur;
+        sj.push_back(J);
+        max_rows = std::max(max_rows, R);
+        max_k = std::max(max_k, K);
+        const int64_t at = cur;
+        cur += oz_operand_bytes(R, K, S_store);
+        return at;
+      };
+      for (int t = ch.b0; t < ch.b1; ++t) {
+        const BatchDesc& b = bd[t];
+        const int hiS = b.nS_hi, loS = b.nS - b.nS_hi;
+        if (b.q == 0 || b.nB == 0 || b.nS == 0) continue;
+        const int64_t xs = phase == 0 ? add_split(0, b.q, b.nB, b.ldq, 0, b, b.xoff)    // X_j, rows = points
+                                      : add_split(1, b.nB, b.q, b.ldq, 0, b, b.xoff);   // X_j, rows = functions
+        for (int d = 0; d < nd; ++d) {
+          const int64_t dofs = (int64_t)d * b.ldq * b.nS;
+          for (int tier = 0; tier < 2; ++tier) {
+            const int rows = tier == 0 ? hiS : loS, r0 = tier == 0 ? 0 : hiS;
+            if (rows == 0) continue;
+            OzGemmJob G{};
+            G.batch = t;
+            G.Sa = G.Sb = S_store;
+            G.c0 = r0;
+            if (phase == 0) {  // F[:, S_j tier] = X_j P[B_j, S_j tier]
+              const int64_t ps = add_split(2, rows, b.nB, b.nfm, r0, b, b.pk_off + d * pk);
+              G.a_off = xs;
+              G.b_off = ps;
+              G.RTa = oz_row_tiles(b.q);
+              G.RTb = oz_row_tiles(rows);
+              G.KT = oz_k_tiles(b.nB);
+              G.kind = 0;
+              G.m_lim = b.ldq;
+              G.n_lim = rows;
+              G.out_off = b.foff + dofs;
+              G.out_off32 = b.foff32 + dofs;
+            } else {  // Kt[S_j tier, B_j] += G_j[:, S_j tier]^T X_j
+              const int64_t gs = add_split(1, rows, b.q, b.ldq, r0, b, b.goff + dofs);
+              G.a_off = gs;
+              G.b_off = xs;
+              G.RTa = oz_row_tiles(rows);
+              G.RTb = oz_row_tiles(b.nB);
+              G.KT = oz_k_tiles(b.q);
+              G.kind = 1;
+              G.m_lim = rows;
+              G.n_lim = b.nB;
+              G.out_off = b.pk_off + d * pk;
+            }
+            const int sl = tier == 0 ? c->opt.tc_slices_hi : c->opt.tc_slices_lo;
+            const int products = sl * (sl + 1) / 2;
+            *tc_flops += 2.0 * products * 128.0 * G.RTa * 128.0 * G.RTb * 32.0 * G.KT;
+            g[phase * 2 + tier].push_back(G);
+          }
+        }
+      }
+      ch.ozs_n[phase] = (int)sj.size() - ch.ozs_off[phase];
+      ch.ozs_rows[phase] = max_rows;
+      ch.ozs_k[phase] = max_k;
+      if (cur > ch.arena_bytes)
+        return fail(c, SNK_ERR_INVALID_ARG, "internal: slice arena of a chunk smaller than its operands");
+    }
+    for (int k = 0; k < 4; ++k) {
+      ch.ozg_off[k] = (int)gj.size();
+      int tiles = 0;
+      for (auto& G : g[k]) {
+        G.tile0 = tiles;
+        tiles += G.RTa * G.RTb;
+        gj.push_back(G);
+      }
+      ch.ozg_n[k] = (int)g[k].size();
+      ch.ozg_tiles[k] = tiles;
+    }
+  }
+  if (sj.empty()) sj.push_back(OzSplitJob{});
+  if (gj.empty()) gj.push_back(OzGemmJob{});
+  SNK_CK(c, upload(c->ozsplit, sj, c->stream));
+  SNK_CK(c, upload(c->ozjobs, gj, c->stream));
+  SNK_CK(c, c->ozerr.ensure(1));
+  SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), c->stream));
+  return SNK_OK;
+}
+
 // Density-dependent part of set_density once P is on the device.
 int screen_and_plan(snk_ctx* c) {
+  if (int rc = check_device_flags(c)) return rc;  // a failure of an earlier asynchronous build
   Setup& s = c->s;
   const int nb = c->nbatch;
   const cudaStream_t st = c->stream;
@@ -476,7 +599,10 @@ int screen_and_plan(snk_ctx* c) {
 
   // shells of V_j -> F / G columns (molecule-local function indices); with
   // the split GEMMs the shells of high-tier pairs come first, [0, nS_hi)
-  const bool split = mixed && c->opt.gemm == SNK_GEMM_SPLIT;
+  const bool tc = mixed && c->opt.gemm == SNK_GEMM_TC;
+  const bool split = mixed && (c->opt.gemm == SNK_GEMM_SPLIT || tc);
+  if (tc && s.n_mol != 1)
+    return fail(c, SNK_ERR_UNSUPPORTED, "gemm = SNK_GEMM_TC needs a single-molecule handle");
   std::vector<int> hcolmap(cmn, -1), hsfunc;
   auto& bd = c->hbatch;
   c->chunks.clear();
@@ -526,21 +652,38 @@ int screen_and_plan(snk_ctx* c) {
   // chunks under the workspace budget (Alg. 1): X, F, G in doubles, plus the
   // FP32 copies of F and G in the mixed form
   int j = 0;
-  int64_t need = 1, need32 = 1;
+  int64_t need = 1, need32 = 1, need_arena = 0;
   const int nd = c->n_dens;
+  // slice-arena bytes of one batch for the F phase (X_j and P[S_j, B_j] per
+  // density, split by tier) and the K phase (X_j and G_j rows per density)
+  const int S_store = std::max(c->opt.tc_slices_hi, c->opt.tc_slices_lo);
+  auto oz_bytes = [&](const BatchDesc& b, int phase) -> int64_t {
+    const int hiS = b.nS_hi, loS = b.nS - b.nS_hi, S5 = S_store;
+    if (phase == 0)
+      return oz_operand_bytes(b.q, b.nB, S5) +
+             (int64_t)nd * (oz_operand_bytes(hiS, b.nB, S5) + oz_operand_bytes(loS, b.nB, S5));
+    return oz_operand_bytes(b.nB, b.q, S5) +
+           (int64_t)nd * (oz_operand_bytes(hiS, b.q, S5) + oz_operand_bytes(loS, b.q, S5));
+  };
   while (j < nb) {
     snk_ctx::Chunk ch;
     ch.b0 = j;
-    int64_t xo = 0, fo = 0;
+    int64_t xo = 0, fo = 0, af = 0, ak = 0;
     while (j < nb) {
       // F and G of density d at foff / goff + d ldq nS
       int64_t xs = (int64_t)bd[j].ldq * bd[j].nB, fs = (int64_t)nd * bd[j].ldq * bd[j].nS;
       int64_t bytes = (xo + xs + 2 * (fo + fs)) * 8 + (mixed ? 2 * (fo + fs) * 4 : 0);
+      const int64_t ozf = tc ? oz_bytes(bd[j], 0) : 0, ozk = tc ? oz_bytes(bd[j], 1) : 0;
+      bytes += std::max(af + ozf, ak + ozk);
       if (j > ch.b0 && bytes > c->ws_budget) break;
       xo += xs;
       fo += fs;
+      af += ozf;
+      ak += ozk;
       ++j;
     }
+    ch.arena_bytes = std::max(af, ak);
+    need_arena = std::max(need_arena, ch.arena_bytes);
     ch.b1 = j;
     int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0, g32cur = fo;
     ch.xn = xo;
@@ -573,6 +716,11 @@ int screen_and_plan(snk_ctx* c) {
   SNK_CK(c, c->ws.ensure((size_t)need));
   if (mixed) SNK_CK(c, c->ws32.ensure((size_t)need32));
   SNK_CK(c, upload(c->batch, bd, st));
+  double tc_flops = 0.0;
+  if (tc) {
+    if (int rc = plan_tc(c, &tc_flops)) return rc;
+    SNK_CK(c, c->arena.ensure((size_t)std::max<int64_t>(need_arena, 16)));
+  }
 
   if (int rc = make_tiles(c, st)) return rc;
   SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
@@ -600,6 +748,7 @@ int screen_and_plan(snk_ctx* c) {
   S.gemm_flops = gflops;
   S.gemm_flops_hi = gflops_hi;
   S.colloc_bytes = xbytes;
+  S.gemm_tc_flops = tc_flops;
   S.n_chunks = (int64_t)c->chunks.size();
   S.workspace_bytes = (int64_t)(c->ws.n * 8 + c->ws32.n * 4);
   float ms = 0.f;
@@ -608,6 +757,21 @@ int screen_and_plan(snk_ctx* c) {
   c->have_density = true;
   c->built = false;
   return SNK_OK;
+}
+
+// The tensor-core products record a wait that ran out (1) or an operand
+// outside the slice arena (2) in a device flag; read and clear it once the
+// stream has drained.
+int check_device_flags(snk_ctx* c) {
+  if (!c->ozerr.p) return SNK_OK;
+  int h = 0;
+  SNK_CK(c, cudaMemcpyAsync(&h, c->ozerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  if (h == 0) return SNK_OK;
+  SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  if (h == 1) return fail(c, SNK_ERR_TIMEOUT, "a tensor-core product kernel gave up waiting on its pipeline");
+  return fail(c, SNK_ERR_CUDA, "a tensor-core product kernel found an operand outside its slice arena");
 }
 
 IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
@@ -643,6 +807,7 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
 int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   Setup& s = c->s;
   const bool mixed = c->opt.precision == SNK_PREC_MIXED;
+  const bool tc = mixed && c->opt.gemm == SNK_GEMM_TC;
   const bool split = mixed && c->opt.gemm == SNK_GEMM_SPLIT;
   const bool df32 = mixed && (c->opt.gemm == SNK_GEMM_DF32 || split);
   const int fmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 1)) ? 1 : 0;
@@ -652,7 +817,36 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   const int64_t pk = s.packed;
   int ev = 0;
   c->launches_build = 0;
-  if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  auto mark = [&]() -> cudaError_t { return timed ? cudaEventRecord(c->events[ev++], st) : cudaSuccess; };
+  // one tensor-core product launch over a chunk's jobs of kind k (F hi, F lo, K hi, K lo)
+  auto oz_gemm = [&](const snk_ctx::Chunk& ch, int k) -> cudaError_t {
+    if (ch.ozg_tiles[k] == 0) return cudaSuccess;
+    OzGemmArgs g;
+    g.jobs = c->ozjobs.p + ch.ozg_off[k];
+    g.n_jobs = ch.ozg_n[k];
+    g.n_tiles = ch.ozg_tiles[k];
+    g.arena = c->arena.p;
+    g.arena_bytes = (int64_t)c->arena.n;
+    g.batches = c->batch.p;
+    g.w = c->w.p;
+    g.fcomp = c->fcomp.p;
+    g.sfunc = c->sfunc.p;
+    g.xfunc = c->xfunc.p;
+    g.ws = c->ws.p;
+    g.ws32 = c->ws32.p;
+    g.Khat = c->Khat.p;
+    g.err = c->ozerr.p;
+    ++c->launches_build;
+    return launch_oz_gemm(st, (k & 1) ? c->opt.tc_slices_lo : c->opt.tc_slices_hi, g, c->num_sms);
+  };
+  auto oz_split = [&](const snk_ctx::Chunk& ch, int phase) -> cudaError_t {
+    if (ch.ozs_n[phase] == 0) return cudaSuccess;
+    ++c->launches_build;
+    return launch_oz_split(st, c->ozsplit.p + ch.ozs_off[phase], ch.ozs_n[phase], ch.ozs_rows[phase],
+                           ch.ozs_k[phase], c->ws.p, c->P.p, c->xfunc.p, c->sfunc.p, c->arena.p,
+                           (int64_t)c->arena.n, c->ozerr.p);
+  };
+  SNK_CK(c, mark());
   SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)std::max<int64_t>(nd * pk, 1), st));
   if (df32) {  // P2 is allocated with the density (no allocation inside a graph capture)
     SNK_CK(c, launch_split_df32_copy(st, c->P.p, nd * pk, c->P2.p));
@@ -667,17 +861,31 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
     ++c->launches_build;
-    if (df32) {  // X_j becomes (hi, lo) float pairs; both GEMMs read it so
+    SNK_CK(c, mark());
+    // operands of F_j = X_j P_d: bf16 slices of X_j and P[S_j, B_j], or X_j as (hi, lo) float pairs
+    if (tc) {
+      SNK_CK(c, oz_split(ch, 0));
+    } else if (df32) {
       SNK_CK(c, launch_split_df32(st, c->ws.p, ch.xn));
       ++c->launches_build;
     }
-    if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
-    // F_j = X_j P_d (w and component factors folded in), Eq. (batch_local_exx)
-    for (int d = 0; d < nd; ++d) {
-      SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
-                             c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode, gpart, d));
-      ++c->launches_build;
-      if (split) {
+    SNK_CK(c, mark());
+    // F_j = X_j P_d (w and component factors folded in), Eq. (batch_local_exx): high tier, then the rest
+    if (tc) {
+      SNK_CK(c, oz_gemm(ch, 0));
+    } else {
+      for (int d = 0; d < nd; ++d) {
+        SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
+                               c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode, gpart,
+                               d));
+        ++c->launches_build;
+      }
+    }
+    SNK_CK(c, mark());
+    if (tc) {
+      SNK_CK(c, oz_gemm(ch, 1));
+    } else if (split) {
+      for (int d = 0; d < nd; ++d) {
         SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
                                c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, c->ws32.p, 3, 2, d));
         ++c->launches_build;
@@ -685,7 +893,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     }
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
     if (mixed && !c->opt.fp32_g64) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
-    if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    SNK_CK(c, mark());
     // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, list by list
     for (int k = 0; k < kNumLists; ++k) {
       IntegralArgs a = integral_args(c, ci, k);
@@ -694,35 +902,47 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
         SNK_CK(c, launch_integrals(st, k, a, grid));
         ++c->launches_build;
       }
-      if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+      SNK_CK(c, mark());
     }
-    // the FP32 pairs' G into the FP64 G, then Kt_d += G_dj^T X_j, Eq. (usym_k)
+    // the FP32 pairs' G into the FP64 G, then the operands of Kt_d += G_dj^T X_j, Eq. (usym_k)
     if (mixed && ch.g32n > 0 && !c->opt.fp32_g64) {
       SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
       ++c->launches_build;
     }
-    if (df32) {
+    if (tc) {
+      SNK_CK(c, oz_split(ch, 1));
+    } else if (df32) {
       SNK_CK(c, launch_split_df32(st, c->ws.p + ch.goff, ch.gbytes / 8));
       ++c->launches_build;
     }
-    for (int d = 0; d < nd; ++d) {
-      SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p, c->Khat.p + d * pk,
-                             kmode, gpart, d));
-      ++c->launches_build;
-      if (split) {
+    SNK_CK(c, mark());
+    if (tc) {
+      SNK_CK(c, oz_gemm(ch, 2));
+    } else {
+      for (int d = 0; d < nd; ++d) {
+        SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p,
+                               c->Khat.p + d * pk, kmode, gpart, d));
+        ++c->launches_build;
+      }
+    }
+    SNK_CK(c, mark());
+    if (tc) {
+      SNK_CK(c, oz_gemm(ch, 3));
+    } else if (split) {
+      for (int d = 0; d < nd; ++d) {
         SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p,
                                c->Khat.p + d * pk, 3, 2, d));
         ++c->launches_build;
       }
     }
-    if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+    SNK_CK(c, mark());
   }
   // K_d = (Kt_d + Kt_d^T) / 2 in every molecule block, Eq. (sn_k)
   for (int d = 0; d < nd; ++d) {
     SNK_CK(c, launch_finish(st, c->mols.p, s.n_mol, s.packed, c->Khat.p + d * pk, c->fcomp.p, dK + d * pk));
     ++c->launches_build;
   }
-  if (timed) SNK_CK(c, cudaEventRecord(c->events[ev++], st));
+  SNK_CK(c, mark());
   return SNK_OK;
 }
 
@@ -792,14 +1012,16 @@ void collect_times(snk_ctx* c) {
   const int last = (int)c->chunks.size() * kPhaseEvents + 1;  // the event after the finish kernel
   if (cudaEventSynchronize(c->events[last]) != cudaSuccess) return;
   st.ms_collocation = st.ms_fgemm = st.ms_integrals = st.ms_kgemm = st.ms_integrals_fp32 = 0.0;
+  st.ms_gemm_split = st.ms_gemm_hi = st.ms_gemm_lo = 0.0;
   for (int k = 0; k < kNumClasses; ++k) st.ms_integrals_class[k] = st.ms_integrals_class_fp32[k] = 0.0;
   int ev = 0;
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const int e0 = ev;  // previous boundary
     st.ms_collocation += el(e0, e0 + 1);
-    st.ms_fgemm += el(e0 + 1, e0 + 2);
+    const double fs = el(e0 + 1, e0 + 2), fh = el(e0 + 2, e0 + 3), fl = el(e0 + 3, e0 + 4);
+    st.ms_fgemm += fs + fh + fl;
     for (int k = 0; k < kNumLists; ++k) {
-      const double t = el(e0 + 2 + k, e0 + 3 + k);
+      const double t = el(e0 + 4 + k, e0 + 5 + k);
       if (k < kNumClasses) {
         st.ms_integrals_class[k] += t;
         st.ms_integrals += t;
@@ -808,8 +1030,13 @@ void collect_times(snk_ctx* c) {
         st.ms_integrals_fp32 += t;
       }
     }
-    st.ms_kgemm += el(e0 + 2 + kNumLists, e0 + 3 + kNumLists);
-    ev = e0 + 3 + kNumLists;
+    const int e1 = e0 + 4 + kNumLists;
+    const double ks = el(e1, e1 + 1), kh = el(e1 + 1, e1 + 2), kl = el(e1 + 2, e1 + 3);
+    st.ms_kgemm += ks + kh + kl;
+    st.ms_gemm_split += fs + ks;
+    st.ms_gemm_hi += fh + kh;
+    st.ms_gemm_lo += fl + kl;
+    ev = e1 + 3;
   }
   st.ms_finish = el(ev, ev + 1);
   st.ms_build = el(0, ev + 1);
@@ -889,10 +1116,11 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   else
     snk_options_default(&c->opt);
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
-  if (c->opt.gemm < 0 || c->opt.gemm > 2 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
+  if (c->opt.gemm < 0 || c->opt.gemm > 3 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
       (c->opt.gemm != SNK_GEMM_FP64 && c->opt.tensor_gemms != 0) || c->opt.ds_integrals < 0 ||
       c->opt.ds_integrals > 1 || c->opt.fp32_g64 < 0 || c->opt.fp32_g64 > 1 ||
-      c->opt.fp32_hrr_ds < 0 || c->opt.fp32_hrr_ds > 1)
+      c->opt.fp32_hrr_ds < 0 || c->opt.fp32_hrr_ds > 1 || c->opt.tc_slices_hi < 3 || c->opt.tc_slices_hi > 6 ||
+      c->opt.tc_slices_lo < 3 || c->opt.tc_slices_lo > 6)
     return SNK_ERR_INVALID_ARG;
   for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
   int rc = build_setup(n_mol, bases, grids, &c->opt, &c->s, &c->err);
@@ -1055,6 +1283,8 @@ void snk_options_default(snk_options* o) {
   o->learned_fp32 = -99.0;
   o->graph = 0;
   o->learned_skip = -11.0;
+  o->tc_slices_hi = 5;
+  o->tc_slices_lo = 3;
 }
 
 const char* snk_status_string(int status) {
@@ -1121,7 +1351,7 @@ int snk_build_K_multi(snk_ctx* c, double* const* K) {
   for (int d = 0; d < c->n_dens; ++d)
     if (n) SNK_CK(c, cudaMemcpyAsync(K[d], c->K.p + d * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   SNK_CK(c, cudaStreamSynchronize(c->stream));
-  return SNK_OK;
+  return check_device_flags(c);
 }
 
 int snk_set_density_device(snk_ctx* c, const double* dP) {
@@ -1174,7 +1404,7 @@ int snk_build_K(snk_ctx* c, double* K) {
   if (rc != SNK_OK) return rc;
   if (n) SNK_CK(c, cudaMemcpyAsync(K, c->K.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   SNK_CK(c, cudaStreamSynchronize(c->stream));
-  return SNK_OK;
+  return check_device_flags(c);
 }
 
 int snk_build_K_batch(snk_ctx* c, double* const* K) {
@@ -1192,7 +1422,7 @@ int snk_build_K_batch(snk_ctx* c, double* const* K) {
                               c->stream));
   }
   SNK_CK(c, cudaStreamSynchronize(c->stream));
-  return SNK_OK;
+  return check_device_flags(c);
 }
 
 int snk_autotune(snk_ctx* c, int32_t* runs) {
@@ -1345,6 +1575,73 @@ int snk_debug_shell_A(snk_ctx* c, int32_t sa, int32_t sb, int64_t n, const doubl
         out[(size_t)i * na * nb + u * nb + v] = x * s.fcomp[s.foff[sa] + u] * s.fcomp[s.foff[sb] + v];
       }
   return SNK_OK;
+}
+
+int snk_debug_tc_gemm(int32_t M, int32_t N, int32_t K, const double* A, const double* B, int32_t slices,
+                      double* C) {
+  if (M < 0 || N < 0 || K < 0 || slices < 3 || slices > 6 || (M * (int64_t)K > 0 && !A) ||
+      (N * (int64_t)K > 0 && !B) || (M * (int64_t)N > 0 && !C))
+    return SNK_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return SNK_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SNK_ERR_CUDA;
+  const int64_t a_bytes = oz_operand_bytes(M, K, slices), b_bytes = oz_operand_bytes(N, K, slices);
+  DevBuf<double> src, out;
+  DevBuf<uint8_t> arena;
+  DevBuf<OzSplitJob> sj;
+  DevBuf<OzGemmJob> gj;
+  DevBuf<int> err;
+  if (src.ensure((size_t)(M + N) * std::max(K, 1)) || out.ensure((size_t)M * N) ||
+      arena.ensure((size_t)(a_bytes + b_bytes + 16)) || sj.ensure(2) || gj.ensure(1) || err.ensure(1))
+    return SNK_ERR_OOM;
+  OzSplitJob h[2] = {};
+  for (int i = 0; i < 2; ++i) {
+    h[i].mode = 1;
+    h[i].R = i == 0 ? M : N;
+    h[i].K = K;
+    h[i].S = slices;
+    h[i].ld = K;
+    h[i].src_off = i == 0 ? 0 : (int64_t)M * K;
+    h[i].dst_off = i == 0 ? 0 : a_bytes;
+  }
+  OzGemmJob g{};
+  g.a_off = 0;
+  g.b_off = a_bytes;
+  g.RTa = oz_row_tiles(M);
+  g.RTb = oz_row_tiles(N);
+  g.KT = oz_k_tiles(K);
+  g.Sa = g.Sb = slices;
+  g.kind = 2;
+  g.m_lim = M;
+  g.n_lim = N;
+  g.ldc = N;
+  if (cudaMemcpy(src.p, A, sizeof(double) * M * K, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(src.p + (int64_t)M * K, B, sizeof(double) * N * K, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(sj.p, h, sizeof(h), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(gj.p, &g, sizeof(g), cudaMemcpyHostToDevice) || cudaMemset(err.p, 0, sizeof(int)) ||
+      cudaMemset(out.p, 0, sizeof(double) * M * N))
+    return SNK_ERR_CUDA;
+  if (K > 0) {
+    if (launch_oz_split(0, sj.p, 2, std::max(M, N), K, src.p, src.p, nullptr, nullptr, arena.p,
+                        (int64_t)arena.n, err.p) != cudaSuccess)
+      return SNK_ERR_CUDA;
+    OzGemmArgs a{};
+    a.jobs = gj.p;
+    a.n_jobs = 1;
+    a.n_tiles = g.RTa * g.RTb;
+    a.arena = arena.p;
+    a.arena_bytes = (int64_t)arena.n;
+    a.ws = out.p;
+    a.err = err.p;
+    if (launch_oz_gemm(0, slices, a, sms) != cudaSuccess) return SNK_ERR_CUDA;
+  }
+  int herr = 0;
+  if (cudaMemcpy(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(C, out.p, sizeof(double) * M * N, cudaMemcpyDeviceToHost))
+    return SNK_ERR_CUDA;
+  return herr == 0 ? SNK_OK : (herr == 1 ? SNK_ERR_TIMEOUT : SNK_ERR_CUDA);
 }
 
 int snk_debug_pair_bound(snk_ctx* c, int32_t sa, int32_t sb, double* bound) {

@@ -286,6 +286,55 @@ cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batch
                              const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles);
 cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64);
 
+// ---------------------------------------------------------------- split-product tensor-core GEMMs
+
+// One operand of one batch to cut into bf16 fixed-point slices (pre-tiled
+// blocks of 128 rows x 32 reduction indices, S slices per block), element
+// (r, k), r < R, k < K:
+//   mode 0: ws[src_off + k ld + r]                      (X_j as F = X P's left operand)
+//   mode 1: ws[src_off + (r0 + r) ld + k]               (G_j rows, X_j rows: Kt = G^T X)
+//   mode 2: P[src_off + sfunc[sf_off + r0 + r] ld + xfunc[xf_off + k]]  (P[S_j, B_j], P symmetric)
+struct OzSplitJob {
+  int32_t mode, R, K, S, ld, r0, sf_off, xf_off;
+  int64_t src_off, dst_off;  // doubles into the source; bytes into the slice arena
+};
+
+// One product of one batch: C[m][n] = sum_k A[m][k] B[n][k] over the arena
+// operands at a_off / b_off (RTa / RTb row blocks, KT reduction blocks, Sa /
+// Sb slices stored per block); its RTa x RTb tiles are numbered from tile0.
+//   kind 0: F[(c0 + n) ldq + m] = w_m f_{c0+n} C (doubles at ws + out_off, floats at ws32 + out_off32)
+//   kind 1: Khat[out_off + sfunc[c0 + m] N_b,m + xfunc[n]] += C
+//   kind 2: ws[out_off + m ldc + n] = C (test export)
+struct OzGemmJob {
+  int64_t a_off, b_off, out_off, out_off32;
+  int32_t RTa, RTb, KT, Sa, Sb, tile0, batch, kind, m_lim, n_lim, c0, ldc;
+};
+
+struct OzGemmArgs {
+  const OzGemmJob* jobs;
+  int n_jobs, n_tiles;
+  const uint8_t* arena;
+  int64_t arena_bytes;
+  const BatchDesc* batches;
+  const double* w;
+  const double* fcomp;
+  const int* sfunc;
+  const int* xfunc;
+  double* ws;
+  float* ws32;
+  double* Khat;
+  int* err;  // set to 1 when a wait ran out, 2 when an operand lay outside the arena
+};
+
+int64_t oz_operand_bytes(int rows, int k, int slices);
+int oz_row_tiles(int rows);
+int oz_k_tiles(int k);
+cudaError_t launch_oz_split(cudaStream_t st, const OzSplitJob* jobs, int n_jobs, int max_rows, int max_k,
+                            const double* ws, const double* P, const int* xfunc, const int* sfunc, uint8_t* arena,
+                            int64_t arena_bytes, int* err);
+// slices: 3..6 (products of slice pairs i + j < slices)
+cudaError_t launch_oz_gemm(cudaStream_t st, int slices, const OzGemmArgs& args, int num_sms);
+
 // learned screen
 cudaError_t launch_labels(cudaStream_t st, int cls, const IntegralArgs& a, int grid, const int64_t* slot_base,
                           const int64_t* list_off, const double* xm, float* lab);
