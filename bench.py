@@ -75,8 +75,11 @@ def _measured_peaks():
 
 HBM_MEASURED = _measured_peaks().get("hbm_gbs")
 HBM_PEAK = float(HBM_MEASURED or 6800.0)
+BF16_MEASURED = _measured_peaks().get("bf16_tflops")
+BF16_PEAK = float(BF16_MEASURED or 1900.0)
 PLAIN = dict()
-CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1)
+CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="tc", tc_slices_hi=5, tc_slices_lo=4,
+              ds_integrals=1)
 GOLDEN = {n: os.path.join(ROOT, "tests", "golden", f"{n}_K_entries.txt")
           for n in ("cluster96", "cluster256", "cluster512")}
 # workloads whose plain FP64 build is too slow to repeat beside the chosen
@@ -360,7 +363,8 @@ def timed(runner, steps, warmup, stream, barrier):
         for s in runner.stats():        # per-phase times from the library's events on the same stream
             for k in ("ms_integrals", "ms_integrals_fp32", "ms_fgemm", "ms_kgemm", "ms_screen", "ms_collocation",
                       "ms_finish", "integral_flops", "flops_fp32", "gemm_flops", "kernel_launches", "integrals",
-                      "colloc_bytes"):
+                      "colloc_bytes", "ms_gemm_split", "ms_gemm_hi", "ms_gemm_lo", "gemm_tc_flops",
+                      "gemm_flops_hi"):
                 acc[k] = acc.get(k, 0.0) + float(s[k])
     e1.record(stream)
     torch.cuda.synchronize()
@@ -437,6 +441,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--gemm", default=None, choices=["split", "tc", "df32"],
+                    help="products of the chosen form (default: its own)")
+    ap.add_argument("--slices", default=None, help="tc: slices of the high and low tier, e.g. 5,3")
     ap.add_argument("--workload", default=WORKLOAD,  # cluster24: a small case of cluster96's shape for profiles
                     choices=["cluster24", "cluster96", "cluster256", "cluster512", "batch64", "batch64_small"])
     args = ap.parse_args()
@@ -476,9 +483,18 @@ def main():
                 "every pair's integrals and both GEMMs in double-FP32 (FP64-grade, ~1e-14 relative)")
     else:
         chosen_opts = dict(CHOSEN)
+        if args.gemm:
+            chosen_opts["gemm"] = args.gemm
+        if args.slices:
+            hi, lo = (int(x) for x in args.slices.split(","))
+            chosen_opts.update(tc_slices_hi=hi, tc_slices_lo=lo)
         form = ("mixed: rigorous sn-LinK at 1e-10, FP32 integrals for pairs with estimate < 3e-4, double-FP32 "
-                "integrals otherwise, GEMMs in double-FP32 for those pairs' shells and split-TF32 tensor-core "
-                "products for the rest, FP64 G and K accumulation")
+                "integrals otherwise; F = X P and Kt = G^T X on the tcgen05 tensor cores as sums of bf16 "
+                "fixed-point slice products (5 slices for the columns / rows of shells in double-FP32 pairs, 4 "
+                "for the rest, exact FP32 accumulation per 256-term run, double-FP32 run sums); FP64 G and K "
+                "accumulation")
+        if chosen_opts["gemm"] != "tc":
+            form = form.replace("on the tcgen05 tensor cores", f"with gemm={chosen_opts['gemm']} instead of")
         if not args.no_learned and os.path.exists(snk.SCREEN_WEIGHTS):
             learned, thr, meta = snk.trained_screen()
             thr32 = float(meta.get("fp32_threshold", -99.0))
@@ -567,7 +583,28 @@ def main():
             kern["integral_kernel"] = {"ms_per_step": ms64 / n, "bound": "alu", "achieved": a, "peak": FP64_PEAK,
                                        "unit": "TFLOP/s", "frac": a / FP64_PEAK}
     gms = acc["ms_fgemm"] + acc["ms_kgemm"]
-    if gms > 0:
+    if chosen_opts.get("gemm") == "tc" and gms > 0:
+        # tensor-core products against the measured bf16 peak: flops of the slice
+        # products issued (padded tiles), and the algorithmic FP64-equivalent rate
+        sh = chosen_opts.get("tc_slices_hi", 5)
+        sl = chosen_opts.get("tc_slices_lo", 3)
+        fh = acc["gemm_flops_hi"]
+        fl = acc["gemm_flops"] - fh
+        for name, ms_k, f64, prods in (("tc_gemm_hi", acc["ms_gemm_hi"], fh, sh * (sh + 1) // 2),
+                                       ("tc_gemm_lo", acc["ms_gemm_lo"], fl, sl * (sl + 1) // 2)):
+            if ms_k > 0:
+                a = f64 * prods / (ms_k * 1e-3) / 1e12
+                kern[name] = {"ms_per_step": ms_k / n, "bound": "tensor", "achieved": a, "peak": BF16_PEAK,
+                              "unit": "TFLOP/s (bf16 slice products, algorithmic sizes)", "frac": a / BF16_PEAK,
+                              "fp64_equivalent_tflops": f64 / (ms_k * 1e-3) / 1e12, "slice_products": prods,
+                              "peak_source": "MEASURED_PEAKS.json bf16_tflops" if BF16_MEASURED else
+                              "fallback 1900 TFLOP/s"}
+        if acc["ms_gemm_hi"] + acc["ms_gemm_lo"] > 0:
+            kern["tc_gemm_issued"] = {"tflops": acc["gemm_tc_flops"] / ((acc["ms_gemm_hi"] + acc["ms_gemm_lo"]) * 1e-3)
+                                      / 1e12, "note": "bf16 flops issued incl. tile padding, both tiers"}
+        kern["gemm_operand_split"] = {"ms_per_step": acc["ms_gemm_split"] / n, "bound": "hbm",
+                                      "note": "slicing X, P[S_j,B_j], G into bf16 blocks and the FP32-tier G merge"}
+    elif gms > 0:
         a = acc["gemm_flops"] / (gms * 1e-3) / 1e12
         if not batch:     # double-FP32 (12 FP32 instructions per multiply-add) and split-TF32 columns
             peak = FP32_PEAK / DF32_OPS_PER_MAC
@@ -597,8 +634,8 @@ def main():
                         "peak": FP64_PEAK, "frac": a / FP64_PEAK, "frac_of_measured_dfma": a / FP64_DFMA_MEASURED}
     if plain_kernel:
         kern["plain_integral_kernel_fp64"] = dict(plain_kernel, bound="alu")
-    dom = max((k for k in kern if k != "plain_integral_kernel_fp64"), key=lambda k: kern[k]["ms_per_step"],
-              default=None)
+    dom = max((k for k in kern if k != "plain_integral_kernel_fp64" and "achieved" in kern[k]),
+              key=lambda k: kern[k]["ms_per_step"], default=None)
     roof = None
     if dom:
         d = kern[dom]

@@ -55,6 +55,12 @@ __host__ __device__ __forceinline__ int oz_elem_offset(int r, int k) {
 }
 
 // ---------------------------------------------------------------- split
+//
+// All of the slicing runs in integer and FP32 arithmetic (FP64 issues at 1/64
+// of the FP32 rate on GB300): the run maximum is taken on the IEEE bit
+// patterns, and each value becomes the integer N = round(x 2^(T - e)),
+// T = 8 S, |N| <= 2^T, read off its significand and exponent with shifts,
+// whose balanced base-256 digits are the slices.
 
 __device__ __forceinline__ double oz_load(const OzSplitJob& j, const double* __restrict__ ws,
                                           const double* __restrict__ P, const int* __restrict__ xfunc,
@@ -67,65 +73,145 @@ __device__ __forceinline__ double oz_load(const OzSplitJob& j, const double* __r
   }
 }
 
-// One CTA per (job, row block, run of 256): the run's row maxima, then the
-// slices of every element, written in the pre-tiled layout.
-__global__ void __launch_bounds__(256) oz_split_kernel(const OzSplitJob* __restrict__ jobs,
-                                                       const double* __restrict__ ws, const double* __restrict__ P,
-                                                       const int* __restrict__ xfunc,
-                                                       const int* __restrict__ sfunc, uint8_t* __restrict__ arena,
-                                                       int64_t arena_bytes, int* __restrict__ err) {
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// e with max < 2^e from the bit pattern of a run's largest |x| (frexp's
+// exponent); 0 for runs below 2^-600, whose slices are then all zero
+__device__ __forceinline__ int oz_run_exponent(unsigned long long maxbits) {
+  const int ex = (int)(maxbits >> 52);
+  return ex >= 1023 - 600 ? ex - 1022 : 0;
+}
+
+// N = round(x 2^(T - e)) for |x| < 2^e (zero and subnormal x give 0)
+__device__ __forceinline__ long long oz_fixed(double x, int e, int T) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // x = +-m 2^(ex - 1075)
+  const int sh = 1075 + e - T - ex;  // > 4 whenever |x| < 2^e and T <= 48
+  if (sh > 60) return 0;
+  const long long n = sh > 0 ? (m + (1ll << (sh - 1))) >> sh : m << (-sh);
+  return (b >> 63) ? -n : n;
+}
+
+// the S slices of 8 values with the run exponent e, as bf16, stored 16 bytes
+// per slice at dst (one core-matrix row of each slice block)
+__device__ __forceinline__ void oz_emit8(const double* x, int e, int S, uint8_t* dst) {
+  const int T = 8 * S;
+  long long r[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) r[q] = oz_fixed(x[q], e, T);
+  for (int s = 0; s < S; ++s) {
+    const int k = T - 8 * (s + 1);
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      long long d;
+      if (k > 0) {
+        d = (r[q] + (1ll << (k - 1))) >> k;  // nearest digit (ties up), |d| <= 256
+        r[q] -= d * (1ll << k);
+      } else {
+        d = r[q];
+      }
+      v[q] = __float2bfloat16_rn(ldexpf((float)d, e - 8 * (s + 1)));  // exact: |d| <= 256
+    }
+    *reinterpret_cast<uint4*>(dst + (int64_t)s * kOzBlockBytes) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+__device__ __forceinline__ bool oz_job_fits(const OzSplitJob& j, int64_t arena_bytes, int* err) {
+  const int RT = (j.R + kOzRows - 1) / kOzRows, KT = (j.K + kOzKt - 1) / kOzKt;
+  if (j.dst_off < 0 || j.dst_off + (int64_t)RT * KT * j.S * kOzBlockBytes > arena_bytes || j.S > 6) {
+    atomicExch(err, 2);
+    return false;
+  }
+  return true;
+}
+
+// Column-major sources (mode 0): one CTA per (job, row block, run of 256);
+// the run's row maxima first (threads along the rows, coalesced), then the
+// slices of (row, 8 reduction indices) items.
+__global__ void __launch_bounds__(256) oz_split_cols_kernel(const OzSplitJob* __restrict__ jobs,
+                                                            const double* __restrict__ ws,
+                                                            uint8_t* __restrict__ arena, int64_t arena_bytes,
+                                                            int* __restrict__ err) {
   const OzSplitJob j = jobs[blockIdx.z];
+  if (j.mode != 0) return;
   const int rt = blockIdx.x, c = blockIdx.y;
   const int RT = (j.R + kOzRows - 1) / kOzRows, KT = (j.K + kOzKt - 1) / kOzKt;
   if (rt >= RT || c * kOzKtPerChunk >= KT) return;
-  // the job's blocks must lie inside the arena (checked on the host too)
-  if (j.dst_off < 0 || j.dst_off + (int64_t)RT * KT * j.S * kOzBlockBytes > arena_bytes) {
-    if (threadIdx.x == 0) atomicExch(err, 2);
-    return;
-  }
-  __shared__ double part[2][kOzRows];
+  if (!oz_job_fits(j, arena_bytes, err)) return;
+  __shared__ unsigned long long part[2][kOzRows];
   __shared__ int rexp[kOzRows];
   const int t = threadIdx.x;
   const int k_begin = c * kOzChunk;
+  const int r = t & (kOzRows - 1);
+  const int grow = rt * kOzRows + r;
   {
-    const int r = t & (kOzRows - 1), h = t >> 7;
-    double m = 0.0;
-    const int k0 = k_begin + h * (kOzChunk / 2);
-    for (int k = k0; k < k0 + kOzChunk / 2; ++k) m = fmax(m, fabs(oz_load(j, ws, P, xfunc, sfunc, rt * kOzRows + r, k)));
+    const int h = t >> 7;
+    unsigned long long m = 0;
+    const int k0 = k_begin + h * (kOzChunk / 2), k1 = min(k0 + kOzChunk / 2, j.K);
+    if (grow < j.R)
+      for (int k = k0; k < k1; ++k) {
+        const unsigned long long b = abs_bits(ws[j.src_off + (int64_t)k * j.ld + grow]);
+        m = b > m ? b : m;
+      }
     part[h][r] = m;
   }
   __syncthreads();
-  if (t < kOzRows) {
-    const double m = fmax(part[0][t], part[1][t]);
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |x| <= m < 2^e
-    rexp[t] = e;
-  }
+  if (t < kOzRows) rexp[t] = oz_run_exponent(part[0][t] > part[1][t] ? part[0][t] : part[1][t]);
   __syncthreads();
-  // (row, group of 8 reduction indices) items: 128 rows x 32 groups
-  for (int it = t; it < kOzRows * (kOzChunk / 8); it += 256) {
-    const int r = it & (kOzRows - 1), g = it >> 7;
+  for (int g = t >> 7; g < kOzChunk / 8; g += 2) {  // 128 rows x 32 groups of 8 reduction indices
     const int k = k_begin + g * 8;
-    if (k >= KT * kOzKt) continue;
-    const int e = rexp[r];
-    const double inv = ldexp(1.0, -e);
-    double u[8];
+    if (k >= KT * kOzKt) break;
+    double x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) u[q] = oz_load(j, ws, P, xfunc, sfunc, rt * kOzRows + r, k + q) * inv;
-    const int kt = k / kOzKt, kk = k % kOzKt;
-    uint8_t* blk = arena + j.dst_off + ((int64_t)rt * KT + kt) * j.S * kOzBlockBytes + oz_elem_offset(r, kk);
-    for (int s = 0; s < j.S; ++s) {
-      __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const double x = u[q] * 256.0;  // exact: a power of two
-        const double n = rint(x);       // |n| <= 256, the slice as an integer
-        u[q] = x - n;                   // exact remainder, |u| <= 1/2
-        v[q] = __float2bfloat16_rn(ldexpf((float)n, e - 8 * (s + 1)));
-      }
-      *reinterpret_cast<uint4*>(blk + (int64_t)s * kOzBlockBytes) = *reinterpret_cast<const uint4*>(v);
-    }
+    for (int q = 0; q < 8; ++q)
+      x[q] = (grow < j.R && k + q < j.K) ? ws[j.src_off + (int64_t)(k + q) * j.ld + grow] : 0.0;
+    const int kt = k / kOzKt;
+    oz_emit8(x, rexp[r], j.S,
+             arena + j.dst_off + ((int64_t)rt * KT + kt) * j.S * kOzBlockBytes + oz_elem_offset(r, k % kOzKt));
   }
+}
+
+// Row-major and gathered sources (modes 1, 2): one warp per (row, run of
+// 256); each lane loads 8 consecutive reduction indices, the warp reduces the
+// run maximum with shuffles, and the lane writes its 8 values' slices.
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(const OzSplitJob* __restrict__ jobs,
+                                                            const double* __restrict__ ws,
+                                                            const double* __restrict__ P,
+                                                            const int* __restrict__ xfunc,
+                                                            const int* __restrict__ sfunc,
+                                                            uint8_t* __restrict__ arena, int64_t arena_bytes,
+                                                            int* __restrict__ err) {
+  const OzSplitJob j = jobs[blockIdx.z];
+  if (j.mode == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RT = (j.R + kOzRows - 1) / kOzRows, KT = (j.K + kOzKt - 1) / kOzKt;
+  const int r = blockIdx.x * 8 + warp, c = blockIdx.y;  // row inside the padded operand
+  if (r >= RT * kOzRows || c * kOzKtPerChunk >= KT) return;
+  if (!oz_job_fits(j, arena_bytes, err)) return;
+  const int k = c * kOzChunk + lane * 8;
+  double x[8];
+  unsigned long long m = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    x[q] = oz_load(j, ws, P, xfunc, sfunc, r, k + q);
+    const unsigned long long b = abs_bits(x[q]);
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if (k >= KT * kOzKt) return;
+  const int kt = k / kOzKt;
+  oz_emit8(x, oz_run_exponent(m), j.S,
+           arena + j.dst_off + ((int64_t)(r / kOzRows) * KT + kt) * j.S * kOzBlockBytes +
+               oz_elem_offset(r % kOzRows, k % kOzKt));
 }
 
 // ---------------------------------------------------------------- PTX helpers
@@ -577,8 +663,13 @@ cudaError_t launch_oz_split(cudaStream_t st, const OzSplitJob* jobs, int n_jobs,
                             const double* ws, const double* P, const int* xfunc, const int* sfunc, uint8_t* arena,
                             int64_t arena_bytes, int* err) {
   if (n_jobs == 0 || max_rows == 0 || max_k == 0) return cudaSuccess;
-  dim3 grid((max_rows + kOzRows - 1) / kOzRows, (max_k + kOzChunk - 1) / kOzChunk, n_jobs);
-  oz_split_kernel<<<grid, 256, 0, st>>>(jobs, ws, P, xfunc, sfunc, arena, arena_bytes, err);
+  const int row_tiles = (max_rows + kOzRows - 1) / kOzRows, runs = (max_k + kOzChunk - 1) / kOzChunk;
+  // each kernel takes the jobs of its kind and returns at once for the others
+  oz_split_cols_kernel<<<dim3(row_tiles, runs, n_jobs), 256, 0, st>>>(jobs, ws, arena, arena_bytes, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_split_rows_kernel<<<dim3(row_tiles * (kOzRows / 8), runs, n_jobs), 256, 0, st>>>(jobs, ws, P, xfunc, sfunc,
+                                                                                        arena, arena_bytes, err);
   return cudaGetLastError();
 }
 

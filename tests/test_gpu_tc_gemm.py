@@ -28,9 +28,12 @@ def snk():
 
 
 def _bound(A, B, slices, chunk=256):
-    """Truncation bound of the fixed-point split: per run of `chunk` columns,
-    |dC_mn| <= (2 slices + 4) 2^(-8 slices) 4 max_run|A_m| max_run|B_n| per
-    term, summed over the run's terms."""
+    """Error bound of the split products, per run of `chunk` columns and
+    summed over runs: the truncation of the fixed-point slices, (2 slices + 4)
+    2^(-8 slices) 4 max_run|A_m| max_run|B_n| per term, plus the FP32
+    rounding of the accumulator that sums the products of level >= 2 (about
+    2^-16 of the run's scale, rounded at 2^-24 relative once per 16 terms and
+    product), bounded by 2^-36 4 max max per term."""
     M, K = A.shape
     N = B.shape[0]
     out = np.zeros((M, N))
@@ -39,7 +42,7 @@ def _bound(A, B, slices, chunk=256):
         bm = np.abs(B[:, c0:c0 + chunk]).max(axis=1)
         n = min(chunk, K - c0)
         out += n * np.outer(am, bm)
-    return (2 * slices + 4) * 2.0 ** (-8 * slices) * 4 * out
+    return ((2 * slices + 4) * 2.0 ** (-8 * slices) + 2.0 ** -36) * 4 * out
 
 
 @pytest.mark.parametrize("slices", [3, 4, 5, 6])
@@ -72,9 +75,23 @@ def test_random_products_within_the_slice_bound(snk, slices):
     bound = _bound(A, B, slices)
     assert np.all(err <= bound + 1e-300), np.max(err / (bound + 1e-300))
     assert np.all(C[5] == 0.0) and np.all(C[:, 7] == 0.0)
-    if slices >= 5:   # FP64-grade relative to the operand scales
+    if slices >= 5:   # far below FP32 relative to the operand scales
         rel = err / (np.abs(A) @ np.abs(B).T + 1e-300)
         assert np.median(rel) < 1e-11
+
+
+def test_tiny_and_subnormal_runs(snk):
+    """Runs whose largest value is subnormal, or far below every other run,
+    give finite results: their slices are zero."""
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(130, 600))
+    B = rng.normal(size=(70, 600))
+    A[:, :256] *= 1e-310
+    A[3] *= 1e-200
+    B[:, 300:] *= 1e-305
+    C = snk.debug_tc_gemm(A, B, 5)
+    assert np.all(np.isfinite(C))
+    assert np.max(np.abs(C - A @ B.T)) <= 1e-8 * np.max(np.abs(A @ B.T))
 
 
 def test_degenerate_shapes(snk):
@@ -105,7 +122,7 @@ def test_tensor_core_products_in_the_mixed_form(snk):
     assert 0 < st["gemm_flops_hi"] < st["gemm_flops"] and st["gemm_tc_flops"] > 0
     assert np.max(np.abs(Kt - Kref)) <= 1e-8
     assert np.max(np.abs(Kt - Kd)) <= 1e-8
-    assert np.max(np.abs(Kt - Kt.T)) == 0.0
+    assert np.max(np.abs(Kt - Kt.T)) == 0.0 and np.all(np.isfinite(Kt))
     Kc, sc = _gpu_K(snk, p, gemm="tc", workspace_bytes=1 << 20, **form)
     assert sc["n_chunks"] > 1 and np.max(np.abs(Kc - Kref)) <= 1e-8
     # every pair in the high tier: FP64-grade products (6 slices) keep the plain form's 1e-10
