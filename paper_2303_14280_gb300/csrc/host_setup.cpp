@@ -303,17 +303,31 @@ int build_setup_one(const snk_basis* basis, const snk_grid* grid, const snk_opti
       // left out; a pair with no primitive left is dropped
       double bnd = 0.0, qb = 0.0;
       std::vector<std::pair<int, int>> keep;
+      std::vector<double> kb;
       for (int k = s->poff[a]; k < s->poff[a + 1]; ++k)
         for (int m = s->poff[b]; m < s->poff[b + 1]; ++m) {
           double pa, pq;
           prim_pair_bounds(*s, a, b, k, m, &pa, &pq);
           if (pa >= kPrimPairTol) {
             keep.emplace_back(k, m);
+            kb.push_back(pa);
             bnd += pa;
             qb += pq;
           }
         }
       if (keep.empty()) continue;
+      // largest bound first (stable, so ties keep the input order); the FP32
+      // tier takes the leading ones down to kPrimPairRelTolF32 of the largest
+      std::vector<int> ord(keep.size());
+      for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return kb[x] > kb[y]; });
+      std::vector<std::pair<int, int>> sorted_keep;
+      int n32 = 0;
+      for (int q : ord) {
+        sorted_keep.push_back(keep[q]);
+        if (kb[q] >= kPrimPairRelTolF32 * kb[ord[0]]) ++n32;
+      }
+      keep.swap(sorted_keep);
       PairHdr h;
       h.sa = a;
       h.sb = b;
@@ -324,7 +338,8 @@ int build_setup_one(const snk_basis* basis, const snk_grid* grid, const snk_opti
       h.ABx = A[0] - B[0];
       h.ABy = A[1] - B[1];
       h.ABz = A[2] - B[2];
-      h.pad = 0.0;
+      h.pp_n32 = n32;
+      h.pad = 0;
       double ab2 = h.ABx * h.ABx + h.ABy * h.ABy + h.ABz * h.ABz;
       for (auto& km : keep) {
         {

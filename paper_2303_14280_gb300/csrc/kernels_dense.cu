@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
           hl[h.sb - bd.ms0] = 1;
         }
         n[prec] += 1;
-        pp[prec] += (unsigned long long)h.pp_n;
+        pp[prec] += (unsigned long long)(prec ? h.pp_n32 : h.pp_n);
       }
     }
     for (int prec = 0; prec < 2; ++prec) {

@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       const int p = a.pairlist[tile.k0 + r];
       const PairHdr h = a.pairs[p];
       s_ppo[r] = h.pp_off;
-      s_ppn[r] = h.pp_n;
+      s_ppn[r] = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
       s_sa[r] = h.sa;
       s_sb[r] = h.sb;
       s_ca[r] = cmap[h.sa];

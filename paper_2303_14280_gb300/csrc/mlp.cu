@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(128) learned_filter_kernel(ScreenArgs a, const
 // src[0, n) whose code equals `want` to dst[out...]; returns the new out.
 __device__ int append_coded(const int* __restrict__ src, const unsigned char* __restrict__ code, int n,
                             unsigned char want, int* __restrict__ dst, int out, const PairHdr* __restrict__ pairs,
-                            unsigned long long* s_pp, int* warp_tot) {
+                            bool fp32, unsigned long long* s_pp, int* warp_tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int base = 0; base < n; base += 256) {
     const int e = base + threadIdx.x;
@@ -445,7 +445,7 @@ __device__ int append_coded(const int* __restrict__ src, const unsigned char* __
     }
     if (k) {
       dst[out + before + __popc(bal & ((1u << lane) - 1u))] = v;
-      atomicAdd(s_pp, (unsigned long long)pairs[v].pp_n);
+      atomicAdd(s_pp, (unsigned long long)(fp32 ? pairs[v].pp_n32 : pairs[v].pp_n));
     }
     out += total;
     __syncthreads();  // warp_tot is rewritten by the next chunk
@@ -486,10 +486,11 @@ __global__ void __launch_bounds__(256) reorder_lists_kernel(const int* __restric
     if (threadIdx.x == 0) s_pp = 0ull;
     __syncthreads();
     const int start = out;
-    out = append_coded(src + s_off[k], keep + s_off[k], s_n[k], 1, dst + b0, out, pairs, &s_pp, warp_tot);
+    out = append_coded(src + s_off[k], keep + s_off[k], s_n[k], 1, dst + b0, out, pairs, k >= kNumClasses, &s_pp,
+                       warp_tot);
     if (k >= kNumClasses) {
       const int h = k - kNumClasses;
-      out = append_coded(src + s_off[h], keep + s_off[h], s_n[h], 2, dst + b0, out, pairs, &s_pp, warp_tot);
+      out = append_coded(src + s_off[h], keep + s_off[h], s_n[h], 2, dst + b0, out, pairs, true, &s_pp, warp_tot);
     }
     new_off[k] = b0 + start;
     new_n[k] = out - start;

@@ -43,6 +43,10 @@ constexpr int kMlpWeights = kMlpIn * kMlpHidden + kMlpHidden + 2 * (kMlpHidden *
 // Primitive pairs whose 3c-CP potential is below this everywhere are left out
 // of a shell pair (their total effect on K is below ~1e-14 for any basis here).
 constexpr double kPrimPairTol = 1e-20;
+// The FP32 tier of the mixed form leaves out a pair's primitive pairs whose
+// bound is below this fraction of its largest: at most 8 such terms change a
+// block by < 1e-7 of its bound, the resolution of the tier's FP32 arithmetic.
+constexpr double kPrimPairRelTolF32 = 1e-8;
 
 inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 inline int class_of(int la, int lb) {  // la >= lb
@@ -59,12 +63,14 @@ struct PrimPair {
   double k1, k2, k3;    // 1, 2, 3 times 1 / (2 zeta)
 };
 
-// Shell pair header.
+// Shell pair header.  The pair's primitive pairs are stored largest bound
+// first; the FP32 tier uses the first pp_n32 of them.
 struct PairHdr {
   int32_t sa, sb;       // shells; l(sa) >= l(sb)
   int32_t pp_off, pp_n; // primitive pairs
   double ABx, ABy, ABz; // R_a - R_b
-  double pad;
+  int32_t pp_n32;       // primitive pairs of the FP32 tier (bound >= kPrimPairRelTolF32 x the largest)
+  int32_t pad;
 };
 
 // Per grid batch, per build chunk.

@@ -1,6 +1,9 @@
-"""Full-size parity on the 96-atom workload (992 functions, 768,000 points) in
-the launch configuration bench.py times (default options): sampled entries
-against the stored oracle values, plus properties that hold at any size."""
+"""Full-size parity in the launch configurations bench.py times: the plain
+FP64 form and the chosen mixed form on the 96-atom workload (992 functions,
+768,000 points), the chosen form on the 256- and 512-atom workloads, each
+against sampled entries of the unscreened sn-K that the CPU oracle stored
+(heavy and light atoms, near and far-apart shells), plus properties that
+hold at any size."""
 import os
 
 import numpy as np
@@ -45,6 +48,77 @@ def test_fullsize_properties(built):
     assert 0 < st["pairs_kept"] <= st["n_pairs"] * st["n_batches"]
 
 
+GOLDEN96L = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster96_light_K_entries.txt")
+
+
+def _entries(path):
+    d = np.loadtxt(path)
+    return d[:, 0].astype(int), d[:, 1].astype(int), d[:, 2]
+
+
+def _chosen_K(p):
+    """K of the form bench.py times (its CHOSEN options and the shipped learned screen)."""
+    import bench
+    import paper_2303_14280_gb300 as snk
+    w, thr, meta = snk.trained_screen()
+    eng = snk.Engine(p.basis, p.grid, screen="learned", learned_skip=thr,
+                     learned_fp32=float(meta.get("fp32_threshold", -99.0)), **bench.CHOSEN)
+    eng.screen_load(w)
+    eng.set_density(p.P)
+    K = eng.build_K()
+    st = eng.stats()
+    eng.close()
+    return K, st
+
+
+@pytest.fixture(scope="module")
+def chosen96():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = synth.cluster96(device="cuda")
+    return p, _chosen_K(p)
+
+
+def test_light_atom_entries_match_oracle(built):
+    """Plain FP64 on H-like (2s1p) rows, near and far-apart, at full size."""
+    p, K, st = built
+    mu, nu, ref = _entries(GOLDEN96L)
+    assert np.max(np.abs(K[mu, nu] - ref)) <= 1e-10
+
+
+def test_chosen_form_matches_oracle_entries_96(chosen96):
+    """The chosen form (tensor-core products, FP32 and double-FP32 integrals,
+    learned screen) at full size against every stored 96-atom oracle entry:
+    heavy and light rows; target max|dK| <= 1e-8."""
+    p, (K, st) = chosen96
+    for path in (GOLDEN, GOLDEN96L):
+        mu, nu, ref = _entries(path)
+        assert np.max(np.abs(K[mu, nu] - ref)) <= 1e-8, path
+    assert np.max(np.abs(K - K.T)) == 0.0 and np.all(np.isfinite(K))
+    assert st["gemm_tc_flops"] > 0 and st["pairs_kept_fp32"] > 0
+
+
+GOLDEN512 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster512_K_entries.txt")
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN512), reason="cluster512 oracle entries not generated")
+def test_cluster512_chosen_form_matches_oracle_entries():
+    """The headline workload: the chosen form on 512 atoms (5,280 functions,
+    4,096,000 points) exactly as bench.py times it, against the stored oracle
+    entries (a heavy-atom d shell and an H-like atom's s and p shells);
+    target max|dK| <= 1e-8."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = synth.cluster512(device="cuda")
+    K, st = _chosen_K(p)
+    mu, nu, ref = _entries(GOLDEN512)
+    assert np.max(np.abs(K[mu, nu] - ref)) <= 1e-8
+    assert np.max(np.abs(K - K.T)) == 0.0 and np.all(np.isfinite(K))
+    assert st["n_points"] == 4096000 and st["n_functions"] == 5280
+
+
 GOLDEN256 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster256_K_entries.txt")
 
 
@@ -57,16 +131,8 @@ def test_cluster256_mixed_form_matches_oracle_entries():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import paper_2303_14280_gb300 as snk
     p = synth.cluster256(device="cuda")
-    w, thr, meta = snk.trained_screen()
-    eng = snk.Engine(p.basis, p.grid, eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", ds_integrals=1,
-                     screen="learned", learned_skip=thr, learned_fp32=float(meta.get("fp32_threshold", -99.0)))
-    eng.screen_load(w)
-    eng.set_density(p.P)
-    K = eng.build_K()
-    eng.close()
-    d = np.loadtxt(GOLDEN256)
-    mu, nu, ref = d[:, 0].astype(int), d[:, 1].astype(int), d[:, 2]
+    K, st = _chosen_K(p)
+    mu, nu, ref = _entries(GOLDEN256)
     assert np.max(np.abs(K[mu, nu] - ref)) <= 1e-8
     assert np.max(np.abs(K - K.T)) == 0.0
