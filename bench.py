@@ -14,10 +14,10 @@ Forms:
           weights and calibrated thresholds: skip, and move high-tier blocks
           with a small predicted contribution to FP32); pairs whose sn-LinK estimate is
           below 3e-4 run their integrals in FP32, the rest in double-FP32 (hi +
-          lo float pairs, ~1e-14 relative); F = X P and Kt = G^T X in
-          double-FP32 arithmetic for the columns of shells in double-FP32
-          pairs and as split-TF32 tensor-core products for the rest; G and K
-          accumulated in FP64
+          lo float pairs, ~1e-14 relative); F = X P and Kt = G^T X on the
+          tcgen05 tensor cores as bf16 fixed-point slice products (5 slices
+          for the columns of shells in double-FP32 pairs, 4 for the rest);
+          G and K accumulated in FP64
   (batch64: the 64 molecules in one handle, one launch per phase, CUDA graph,
    autotuned tiles, every pair and GEMM in double-FP32 for the 1e-10 target,
    against 64 separate plain FP64 builds)
@@ -78,7 +78,7 @@ HBM_PEAK = float(HBM_MEASURED or 6800.0)
 BF16_MEASURED = _measured_peaks().get("bf16_tflops")
 BF16_PEAK = float(BF16_MEASURED or 1900.0)
 PLAIN = dict()
-CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="tc", tc_slices_hi=5, tc_slices_lo=4,
+CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", tc_slices_hi=5, tc_slices_lo=4,
               ds_integrals=1)
 GOLDEN = {n: os.path.join(ROOT, "tests", "golden", f"{n}_K_entries.txt")
           for n in ("cluster96", "cluster256", "cluster512")}
@@ -441,9 +441,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--gemm", default=None, choices=["split", "tc", "df32"],
+    ap.add_argument("--gemm", default=None, choices=["split", "df32"],
                     help="products of the chosen form (default: its own)")
-    ap.add_argument("--slices", default=None, help="tc: slices of the high and low tier, e.g. 5,3")
+    ap.add_argument("--slices", default=None, help="split: slices of the high and low tier, e.g. 5,4")
     ap.add_argument("--workload", default=WORKLOAD,  # cluster24: a small case of cluster96's shape for profiles
                     choices=["cluster24", "cluster96", "cluster256", "cluster512", "batch64", "batch64_small"])
     args = ap.parse_args()
@@ -493,7 +493,7 @@ def main():
                 "fixed-point slice products (5 slices for the columns / rows of shells in double-FP32 pairs, 4 "
                 "for the rest, exact FP32 accumulation per 256-term run, double-FP32 run sums); FP64 G and K "
                 "accumulation")
-        if chosen_opts["gemm"] != "tc":
+        if chosen_opts["gemm"] != "split":
             form = form.replace("on the tcgen05 tensor cores", f"with gemm={chosen_opts['gemm']} instead of")
         if not args.no_learned and os.path.exists(snk.SCREEN_WEIGHTS):
             learned, thr, meta = snk.trained_screen()
@@ -583,11 +583,11 @@ def main():
             kern["integral_kernel"] = {"ms_per_step": ms64 / n, "bound": "alu", "achieved": a, "peak": FP64_PEAK,
                                        "unit": "TFLOP/s", "frac": a / FP64_PEAK}
     gms = acc["ms_fgemm"] + acc["ms_kgemm"]
-    if chosen_opts.get("gemm") == "tc" and gms > 0:
+    if chosen_opts.get("gemm") == "split" and gms > 0:
         # tensor-core products against the measured bf16 peak: flops of the slice
         # products issued (padded tiles), and the algorithmic FP64-equivalent rate
         sh = chosen_opts.get("tc_slices_hi", 5)
-        sl = chosen_opts.get("tc_slices_lo", 3)
+        sl = chosen_opts.get("tc_slices_lo", 4)
         fh = acc["gemm_flops_hi"]
         fl = acc["gemm_flops"] - fh
         for name, ms_k, f64, prods in (("tc_gemm_hi", acc["ms_gemm_hi"], fh, sh * (sh + 1) // 2),

@@ -21,7 +21,8 @@
  *   - plain: FP64 throughout (the default);
  *   - mixed precision: blocks with a small sn-LinK estimate in FP32, the rest
  *     in FP64 or double-FP32 (hi + lo float pairs), the two products in FP64,
- *     double-FP32 or split-TF32 tensor-core tiles; G and K accumulated in FP64;
+ *     double-FP32 or bf16 split products on the tcgen05 tensor cores; G and K
+ *     accumulated in FP64;
  *   - batched: many molecules in one handle (snk_create_batch), one launch per
  *     phase, optional CUDA-graph replay and autotuned tiles;
  *   - learned screen: a small MLP, trained by the library's own kernels,
@@ -94,7 +95,7 @@ typedef struct {
 
 typedef enum { SNK_PREC_FP64 = 0, SNK_PREC_MIXED = 1 } snk_precision;
 typedef enum { SNK_SCREEN_NONE = 0, SNK_SCREEN_LINK = 1, SNK_SCREEN_LEARNED = 2 } snk_screen_mode;
-typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1, SNK_GEMM_SPLIT = 2, SNK_GEMM_TC = 3 } snk_gemm_mode;
+typedef enum { SNK_GEMM_FP64 = 0, SNK_GEMM_DF32 = 1, SNK_GEMM_SPLIT = 2 } snk_gemm_mode;
 
 typedef struct {
   double eps_basis;        /* epsilon_B of Eq. (basis_screen); <= 0 keeps all   */
@@ -109,10 +110,6 @@ typedef struct {
   double fp32_bound;       /* mixed form: kept pairs whose sn-LinK estimate
                               epsilon^K is below this run their integrals in FP32 */
   int64_t workspace_bytes; /* device workspace cap for batch chunks (Alg. 1); 0 = auto */
-  int32_t tensor_gemms;    /* mixed form: bit 0 runs F = X P, bit 1 runs Kt = G^T X on
-                              the tensor cores (3xTF32, FP32 accumulation); default 0:
-                              both in FP64, because cancellation in X P amplifies the
-                              ~1e-7 split error to ~1e-5 in K on the 96-atom workload */
   int32_t graph;           /* 1: snk_build_K* capture the whole build in a CUDA graph
                               on first use (per density and output buffer) and
                               replay it; phase times are then not reported      */
@@ -122,38 +119,28 @@ typedef struct {
                               F = X P and Kt = G^T X in double-FP32 arithmetic on the
                               FP32 pipe (operands as hi + lo float pairs, error-free
                               TwoSum accumulation, ~2^-46 relative); SNK_GEMM_SPLIT,
-                              double-FP32 for the F columns and G rows of shells
-                              in a batch's FP64-tier pairs and split-TF32 tensor-core
-                              products (FP32 partial sums of 64 terms folded into
-                              double-FP32) for the shells only FP32-tier pairs use;
-                              SNK_GEMM_TC, both products on the tcgen05 tensor cores
-                              as sums of bf16 slice products: every operand cut into
-                              slices on a fixed-point grid per row and run of 256
-                              reduction indices, each run's low-order products
-                              accumulated exactly in FP32 and the runs summed in
-                              double-FP32 -- 5 slices (15 products, ~2^-40 of the
-                              run maxima) for the F columns and G rows of shells in
-                              a batch's FP64-tier pairs, 3 slices (6 products,
-                              ~2^-24) for the rest; single-molecule handles;
-                              not combined with tensor_gemms (SNK_ERR_INVALID_ARG) */
+                              both products on the tcgen05 tensor cores as sums of
+                              bf16 slice products: every operand cut into slices on
+                              a fixed-point grid per row and run of 256 reduction
+                              indices, each run's two leading levels of products
+                              accumulated exactly in FP32, the runs summed in
+                              double-FP32 -- tc_slices_hi slices for the F columns
+                              and G rows of shells in a batch's FP64-tier pairs,
+                              tc_slices_lo for the rest                         */
   int32_t ds_integrals;    /* mixed form: 1 runs the integrals of the pairs above
                               fp32_bound in double-FP32 arithmetic (hi + lo float
                               pairs on the FP32 pipe, ~1e-14 relative) instead of
                               FP64; default 0                                   */
-  int32_t fp32_g64;        /* mixed form: 1 adds the FP32 pairs' G contributions
-                              to the FP64 G with FP64 atomics (no FP32 partial
-                              sums); default 0, an FP32 copy of G merged once   */
-  int32_t fp32_hrr_ds;     /* mixed form: 1 runs the FP32 pairs' HRR (Eq. hrr, once per
-                              pair and point) in double-FP32 on the FP32 VRR result;
-                              measured to leave the FP32 tier's error unchanged (it
-                              comes from the FP32 seeds and VRR); default 0      */
   double learned_fp32;     /* learned screen, mixed form: a block of the FP64 (or
                               double-FP32) tier whose predicted log10 contribution
                               is below this moves to the FP32 tier; default -99
                               (off)                                             */
-  int32_t tc_slices_hi;    /* SNK_GEMM_TC: bf16 slices per operand for the high-tier
-                              columns / rows, 3..6 (default 5: 15 slice products)  */
-  int32_t tc_slices_lo;    /* SNK_GEMM_TC: the same for the rest, 3..6 (default 3) */
+  int32_t tc_slices_hi;    /* SNK_GEMM_SPLIT: bf16 slices per operand for the high-
+                              tier columns / rows, 3..6 (default 5: 15 slice
+                              products, ~2^-31 of the run maxima, set by the FP32
+                              sum of the products below the two leading levels)  */
+  int32_t tc_slices_lo;    /* SNK_GEMM_SPLIT: the same for the rest, 3..6 (default
+                              4: 10 products, ~2^-30)                           */
   double reserved[3];
 } snk_options;
 
@@ -188,7 +175,7 @@ typedef struct {
                                   (slicing, splitting, the FP32-tier G merge)       */
   double ms_gemm_hi;           /* last build: both products, high-tier columns / rows */
   double ms_gemm_lo;           /* last build: both products, the remaining ones      */
-  double gemm_tc_flops;        /* SNK_GEMM_TC: bf16 tensor-core flops issued per build
+  double gemm_tc_flops;        /* SNK_GEMM_SPLIT: bf16 tensor-core flops issued per build
                                   (2 M N K per slice product, padded tile sizes)     */
 } snk_stats;
 
@@ -351,7 +338,7 @@ int snk_debug_shell_A(snk_ctx *ctx, int32_t sa, int32_t sb, int64_t n, const dou
  * (sa, sb) (the A-tilde of Eq. exx_fmat_approx). */
 int snk_debug_pair_bound(snk_ctx *ctx, int32_t sa, int32_t sb, double *bound);
 
-/* The split-product tensor-core GEMM of SNK_GEMM_TC on plain matrices:
+/* The split-product tensor-core GEMM of SNK_GEMM_SPLIT on plain matrices:
  * C = A B^T with A (M x K) and B (N x K) row-major host doubles, C (M x N)
  * row-major host, each operand cut into `slices` (3..6) bf16 slices per row and
  * run of 256 columns (Sec. II.C, Eq. fmat, and Sec. II.D, Eq. usym_k, are

@@ -36,7 +36,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported input", -3: "density
           -4: "bad call order", -5: "out of memory", -6: "CUDA error", -7: "device wait timed out"}
 SCREEN = {"none": 0, "link": 1, "learned": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
-GEMM = {"fp64": 0, "df32": 1, "split": 2, "tc": 3}
+GEMM = {"fp64": 0, "df32": 1, "split": 2}
 LISTS = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
 # every entry point declared in include/snk.h
@@ -73,9 +73,8 @@ class SnkOptions(ctypes.Structure):
     _fields_ = [("eps_basis", ctypes.c_double), ("eps_E", ctypes.c_double), ("eps_K", ctypes.c_double),
                 ("batch_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("screen", ctypes.c_int32),
                 ("distance_bound", ctypes.c_int32), ("fp32_bound", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_int64), ("tensor_gemms", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64), ("graph", ctypes.c_int32),
                 ("learned_skip", ctypes.c_double), ("gemm", ctypes.c_int32), ("ds_integrals", ctypes.c_int32),
-                ("fp32_g64", ctypes.c_int32), ("fp32_hrr_ds", ctypes.c_int32),
                 ("learned_fp32", ctypes.c_double), ("tc_slices_hi", ctypes.c_int32),
                 ("tc_slices_lo", ctypes.c_int32), ("reserved", ctypes.c_double * 3)]
 
@@ -166,7 +165,7 @@ def options(**kw) -> SnkOptions:
     """snk_options from the library defaults and keyword overrides: any field
     of snk_options (include/snk.h), `eps` for eps_basis = eps_E = eps_K, and
     names for screen ("none", "link", "learned"), precision ("fp64", "mixed")
-    and gemm ("fp64", "df32", "split", "tc").  Unknown keys raise ValueError."""
+    and gemm ("fp64", "df32", "split").  Unknown keys raise ValueError."""
     o = SnkOptions()
     lib().snk_options_default(ctypes.byref(o))
     fields = {f[0] for f in SnkOptions._fields_} - {"reserved"}

@@ -3,9 +3,9 @@
 //   Eq. (exx_fmat_approx), F-tilde = |P| Phi-tilde (Eq. exx_fmat_approx) as
 //   a GEMM over batches, the sn-LinK pair screen with per-batch compaction
 //   (Eq. sp_set), the integral tiles, the products F_j = X_j P (Eq.
-//   batch_local_exx) and Kt += G_j^T X_j (Eq. usym_k) in FP64, double-FP32
-//   or split-TF32 tensor-core tiles (one F / G block per density), and the
-//   symmetrisation of Eq. (sn_k).
+//   batch_local_exx) and Kt += G_j^T X_j (Eq. usym_k) as FP64 or
+//   double-FP32 tiles (one F / G block per density; the tensor-core split
+//   products are in kernels_ozaki.cu), and the symmetrisation of Eq. (sn_k).
 //
 // Several molecules can share one handle: every batch knows its molecule, P
 // and K are packed per molecule (row-major N_b,m^2 blocks), and column lists
@@ -111,143 +111,6 @@ __device__ __forceinline__ void gemm_tile(int m0, int n0, int mdim, int ndim, in
       int m = m0 + ty + 16 * p, n = n0 + tx + 16 * q;
       if (m < mdim && n < ndim) st(m, n, acc[p][q]);
     }
-}
-
-// ---------------------------------------------------------------- split-TF32 tensor-core tile (mixed form)
-
-// 3xTF32: a = a_hi + a_lo with both parts rounded to TF32, and
-// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, each on the tensor cores with FP32
-// accumulation (the dropped A_lo B_lo is ~2^-22 relative).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int TC_THREADS = 128, TC_M = 64, TC_N = 64, TC_K = 16, TC_PAD = 4;
-
-// C[m][n] = sum_k A(m,k) B(k,n) over the 64 x 64 tile at (m0, n0); four warps
-// in 2 x 2, each 32 x 32 = 2 x 4 m16n8k8 tiles; st(m, n, c) stores.
-// With CHUNKED, the FP32 accumulators are folded into double-FP32 sums every
-// kTcChunk k (and cleared), so FP32 rounding acts on 64-term partial sums only.
-constexpr int kTcChunk = 64;
-
-template <bool CHUNKED = false, class LA, class LB, class ST>
-__device__ __forceinline__ void tf32x3_tile(int m0, int n0, int mdim, int ndim, int kdim, LA la, LB lb, ST st,
-                                            bool a_k_fast, bool b_k_fast) {
-  __shared__ uint32_t Ah[TC_M][TC_K + TC_PAD], Al[TC_M][TC_K + TC_PAD];
-  __shared__ uint32_t Bh[TC_K][TC_N + 2 * TC_PAD], Bl[TC_K][TC_N + 2 * TC_PAD];  // row stride = 8 banks
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
-  ds sum[CHUNKED ? 2 : 1][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        acc[i][j][r] = 0.f;
-        if (CHUNKED) sum[i % (CHUNKED ? 2 : 1)][j][r] = ds_make(0.f, 0.f);
-      }
-  for (int k0 = 0; k0 < kdim; k0 += TC_K) {
-    if (CHUNKED && k0 > 0 && k0 % kTcChunk == 0) {
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            sum[i % (CHUNKED ? 2 : 1)][j][r] += ds_make(acc[i][j][r], 0.f);
-            acc[i][j][r] = 0.f;
-          }
-    }
-#pragma unroll
-    for (int r = 0; r < (TC_M * TC_K) / TC_THREADS; ++r) {
-      const int e = tid + r * TC_THREADS;
-      int kk, mm;
-      if (a_k_fast) {
-        kk = e % TC_K;
-        mm = e / TC_K;
-      } else {
-        mm = e % TC_M;
-        kk = e / TC_M;
-      }
-      const int m = m0 + mm, k = k0 + kk;
-      const float v = (m < mdim && k < kdim) ? (float)la(m, k) : 0.f;
-      const uint32_t h = to_tf32(v);
-      Ah[mm][kk] = h;
-      Al[mm][kk] = to_tf32(v - __uint_as_float(h));
-      int nn;
-      if (b_k_fast) {
-        kk = e % TC_K;
-        nn = e / TC_K;
-      } else {
-        nn = e % TC_N;
-        kk = e / TC_N;
-      }
-      const int n = n0 + nn, k2 = k0 + kk;
-      const float u = (n < ndim && k2 < kdim) ? (float)lb(k2, n) : 0.f;
-      const uint32_t hb = to_tf32(u);
-      Bh[kk][nn] = hb;
-      Bl[kk][nn] = to_tf32(u - __uint_as_float(hb));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < TC_K; ks += 8) {
-      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r0 = wm + i * 16 + g;
-        ah[i][0] = Ah[r0][ks + t];
-        ah[i][1] = Ah[r0 + 8][ks + t];
-        ah[i][2] = Ah[r0][ks + t + 4];
-        ah[i][3] = Ah[r0 + 8][ks + t + 4];
-        al[i][0] = Al[r0][ks + t];
-        al[i][1] = Al[r0 + 8][ks + t];
-        al[i][2] = Al[r0][ks + t + 4];
-        al[i][3] = Al[r0 + 8][ks + t + 4];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c0 = wn + j * 8 + g;
-        bh[j][0] = Bh[ks + t][c0];
-        bh[j][1] = Bh[ks + t + 4][c0];
-        bl[j][0] = Bl[ks + t][c0];
-        bl[j][1] = Bl[ks + t + 4][c0];
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          mma_tf32(acc[i][j], al[i], bh[j]);
-          mma_tf32(acc[i][j], ah[i], bl[j]);
-          mma_tf32(acc[i][j], ah[i], bh[j]);
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + 2 * t + (r & 1);
-        double v = (double)acc[i][j][r];
-        if (CHUNKED) v += ds_to(sum[i % (CHUNKED ? 2 : 1)][j][r]);
-        if (m < mdim && n < ndim) st(m, n, v);
-      }
 }
 
 // ---------------------------------------------------------------- double-FP32 tile (mixed form)
@@ -616,26 +479,15 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, c
 // F-hat_{s i} = w_i f_s sum_{nu in B_j} X_{nu i} P_{nu s}: the quadrature weight
 // and the Cartesian component factor of the column are folded into F.  In the
 // mixed form an FP32 copy is written for the FP32 pairs.
-// Column ranges of a GEMM part: 0 all of S_j, 1 the high-tier columns
-// [0, nS_hi), 2 the low-tier columns [nS_hi, nS).
-__device__ __forceinline__ void part_range(const BatchDesc& bd, int part, int& lo, int& hi) {
-  lo = part == 2 ? bd.nS_hi : 0;
-  hi = part == 1 ? bd.nS_hi : bd.nS;
-}
-
-// MODE: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32 on (hi, lo) operands,
-// 3 split-TF32 on the hi floats of (hi, lo) operands with chunked ds accumulation
+// MODE: 0 FP64, 2 double-FP32 on (hi, lo) operands
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THREADS, MODE >= 2 ? 2 : 3)
+__global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
     fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P, const float2* __restrict__ P2,
                  const int* __restrict__ xfunc, const int* __restrict__ sfunc, const double* __restrict__ fcomp,
-                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32, int part,
-                 int dens) {
+                 const double* __restrict__ w, double* __restrict__ ws, float* __restrict__ ws32, int dens) {
   const BatchDesc bd = batches[blockIdx.z];
-  int c0, c1;
-  part_range(bd, part, c0, c1);
-  const int m0 = blockIdx.x * TM, n0 = c0 + blockIdx.y * TN;
-  if (m0 >= bd.ldq || n0 >= c1) return;
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= bd.ldq || n0 >= bd.nS) return;
   const int64_t dofs = (int64_t)dens * bd.ldq * bd.nS;  // density d's F / G block
   double* F = ws + bd.foff + dofs;
   float* F32 = ws32 ? ws32 + bd.foff32 + dofs : nullptr;
@@ -648,67 +500,47 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THR
     F[(int64_t)n * bd.ldq + m] = v;
     if (F32) F32[(int64_t)n * bd.ldq + m] = (float)v;
   };
-  if (MODE == 2 || MODE == 3) {
+  if (MODE == 2) {
     const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
     const float2* Pm2 = P2 + bd.pk_off;
     auto la = [&](int m, int k) { return X2[(int64_t)k * bd.ldq + m]; };
     auto lb = [&](int k, int n) { return Pm2[(int64_t)xf[k] * bd.nfm + sf[n]]; };
-    if (MODE == 2) {
-      df32_tile(m0, n0, bd.ldq, c1, bd.nB, la, lb, st, false, false);
-    } else {
-      auto la1 = [&](int m, int k) { return la(m, k).x; };
-      auto lb1 = [&](int k, int n) { return lb(k, n).x; };
-      tf32x3_tile<true>(m0, n0, bd.ldq, c1, bd.nB, la1, lb1, st, false, false);
-    }
+    df32_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
   } else {
     const double* X = ws + bd.xoff;
     const double* Pm = P + bd.pk_off;
     auto la = [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; };
     auto lb = [&](int k, int n) { return Pm[(int64_t)xf[k] * bd.nfm + sf[n]]; };
-    if (MODE == 1)
-      tf32x3_tile(m0, n0, bd.ldq, c1, bd.nB, la, lb, st, false, false);
-    else
-      gemm_tile(m0, n0, bd.ldq, c1, bd.nB, la, lb, st, false, false);
+    gemm_tile(m0, n0, bd.ldq, bd.nS, bd.nB, la, lb, st, false, false);
   }
 }
 
 // Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the molecule's block
 // of the packed accumulator (several batches add to the same entries).
 template <int MODE>
-__global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? TC_THREADS : GEMM_THREADS, MODE >= 2 ? 2 : 3)
+__global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
     kgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc, const int* __restrict__ sfunc,
-                 const double* __restrict__ ws, double* __restrict__ Khat, int part, int dens) {
+                 const double* __restrict__ ws, double* __restrict__ Khat, int dens) {
   const BatchDesc bd = batches[blockIdx.z];
-  int r0, r1;
-  part_range(bd, part, r0, r1);
-  const int m0 = r0 + blockIdx.x * TM, n0 = blockIdx.y * TN;
-  if (m0 >= r1 || n0 >= bd.nB) return;
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= bd.nS || n0 >= bd.nB) return;
   const int64_t dofs = (int64_t)dens * bd.ldq * bd.nS;  // density d's G block
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
   double* Km = Khat + bd.pk_off;
   auto st = [&](int m, int n, double c) { atomicAdd(&Km[(int64_t)sf[m] * bd.nfm + xf[n]], c); };
-  if (MODE == 2 || MODE == 3) {
+  if (MODE == 2) {
     const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
     const float2* G2 = reinterpret_cast<const float2*>(ws + bd.goff) + dofs;
     auto la = [&](int m, int k) { return G2[(int64_t)m * bd.ldq + k]; };
     auto lb = [&](int k, int n) { return X2[(int64_t)n * bd.ldq + k]; };
-    if (MODE == 2) {
-      df32_tile(m0, n0, r1, bd.nB, bd.q, la, lb, st, true, true);
-    } else {
-      auto la1 = [&](int m, int k) { return la(m, k).x; };
-      auto lb1 = [&](int k, int n) { return lb(k, n).x; };
-      tf32x3_tile<true>(m0, n0, r1, bd.nB, bd.q, la1, lb1, st, true, true);
-    }
+    df32_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
   } else {
     const double* X = ws + bd.xoff;
     const double* G = ws + bd.goff + dofs;
     auto la = [&](int m, int k) { return G[(int64_t)m * bd.ldq + k]; };
     auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
-    if (MODE == 1)
-      tf32x3_tile(m0, n0, r1, bd.nB, bd.q, la, lb, st, true, true);
-    else
-      gemm_tile(m0, n0, r1, bd.nB, bd.q, la, lb, st, true, true);
+    gemm_tile(m0, n0, bd.nS, bd.nB, bd.q, la, lb, st, true, true);
   }
 }
 
@@ -744,12 +576,6 @@ __global__ void abs_sum_kernel(const double* __restrict__ P, int n_dens, int64_t
     for (int d = 0; d < n_dens; ++d) v += fabs(P[d * n + e]);
     out[e] = v;
   }
-}
-
-// G += G32 over a chunk's contiguous G region (mixed form).
-__global__ void merge_g32_kernel(const float* __restrict__ g32, int64_t n, double* __restrict__ g64) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    g64[e] += (double)g32[e];
 }
 
 // K_{mu nu} = (f_mu Kt_{mu nu} + f_nu Kt_{nu mu}) / 2 in every molecule block,
@@ -847,29 +673,24 @@ cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc, const double* fcomp,
-                         const double* w, double* ws, float* ws32, int mode, int part, int dens) {
+                         const double* w, double* ws, float* ws32, int mode, int dens) {
   if (nbatch == 0 || max_ldq == 0 || max_nS == 0) return cudaSuccess;
   dim3 grid((max_ldq + TM - 1) / TM, (max_nS + TN - 1) / TN, nbatch);
-  switch (mode) {
-    case 1: fgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens); break;
-    case 2: fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens); break;
-    case 3: fgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens); break;
-    default: fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, part, dens);
-  }
+  if (mode == 2)
+    fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, dens);
+  else
+    fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, P2, xfunc, sfunc, fcomp, w, ws, ws32, dens);
   return cudaGetLastError();
 }
 
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part,
-                         int dens) {
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int dens) {
   if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
   dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
-  switch (mode) {
-    case 1: kgemm_kernel<1><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens); break;
-    case 2: kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens); break;
-    case 3: kgemm_kernel<3><<<grid, TC_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens); break;
-    default: kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, part, dens);
-  }
+  if (mode == 2)
+    kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, dens);
+  else
+    kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, dens);
   return cudaGetLastError();
 }
 
@@ -898,13 +719,6 @@ cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n
   if (n <= 0) return cudaSuccess;
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
   split_df32_copy_kernel<<<grid, 256, 0, st>>>(src, n, dst);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64) {
-  if (n == 0) return cudaSuccess;
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  merge_g32_kernel<<<blocks, 256, 0, st>>>(g32, n, g64);
   return cudaGetLastError();
 }
 

@@ -230,7 +230,7 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
 // shared memory once per tile (one barrier per tile); the next pair's F is
 // loaded while the current pair computes; for the light classes each warp
 // also stages the pair's records (below).
-template <int LA, int LB, bool HRR_DS, int ND>
+template <int LA, int LB, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
@@ -288,15 +288,10 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     }
     const int64_t ldq = bd.ldq, dstr = (int64_t)bd.ldq * bd.nS;  // density d's F / G: + d dstr
     const float* F = a.ws32 + bd.foff32 + i;
-    float* G = a.ws32 + bd.goff32 + i;
     double* G64 = a.ws + bd.goff + i;
-    const bool g64 = a.f32_g64 != 0;
-    auto gadd = [&](int d, int col, float v) {
-      if (g64)
-        atomicAdd(G64 + d * dstr + col * ldq, (double)v);
-      else
-        atomicAdd(G + d * dstr + col * ldq, v);
-    };
+    // the FP32 contributions are added to the FP64 G with FP64 atomics: their
+    // order changes K by ~1e-14 from run to run (FP32 atomics: ~1e-10)
+    auto gadd = [&](int d, int col, float v) { atomicAdd(G64 + d * dstr + col * ldq, (double)v); };
     if (STAGE) {  // the first pair's records
       const int n4 = min(s_ppn[0], kStage) * 4;
       const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 4;
@@ -370,17 +365,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
           for (int q = 0; q < ppn; ++q) prim(pp[4 * q], pp[4 * q + 1], pp[4 * q + 2], pp[4 * q + 3]);
         }
         float xi[NA * NB];
-        if (HRR_DS && LB > 0) {
-          ds accd[C::NACC], xid[NA * NB];
-#pragma unroll
-          for (int u = 0; u < C::NACC; ++u) accd[u] = ds_make(acc[u], 0.f);
-          C::hrr(accd, ds_make(s_ab[r][0].x, s_ab[r][0].y), ds_make(s_ab[r][1].x, s_ab[r][1].y),
-                 ds_make(s_ab[r][2].x, s_ab[r][2].y), xid);
-#pragma unroll
-          for (int u = 0; u < NA * NB; ++u) xi[u] = __fadd_rn(xid[u].hi, xid[u].lo);
-        } else {
-          C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
-        }
+        C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
 #pragma unroll
         for (int d = 0; d < ND; ++d)
 #pragma unroll
@@ -706,8 +691,7 @@ cudaError_t launch_kernel(K kernel, size_t smem, cudaStream_t st, const Integral
 
 template <int LA, int LB, int ND>
 cudaError_t launch_class_nd(cudaStream_t st, bool f32, const IntegralArgs& a, int grid) {
-  if (f32 && a.f32_hrr_ds) return launch_kernel(integral_kernel_f32<LA, LB, true, ND>, kSmem32, st, a, grid);
-  if (f32) return launch_kernel(integral_kernel_f32<LA, LB, false, ND>, kSmem32, st, a, grid);
+  if (f32) return launch_kernel(integral_kernel_f32<LA, LB, ND>, kSmem32, st, a, grid);
   if (a.hi_ds) return launch_kernel(integral_kernel_ds<LA, LB, ND>, kSmem64, st, a, grid);
   return launch_kernel(integral_kernel<LA, LB, ND>, kSmem64, st, a, grid);
 }
@@ -727,16 +711,15 @@ int ctas_for(K kernel, size_t smem, int num_sms) {
 }
 
 template <int LA, int LB, int ND>
-int max_ctas_nd(bool f32, bool ds, bool hrr_ds, int num_sms) {
-  if (f32 && hrr_ds) return ctas_for(integral_kernel_f32<LA, LB, true, ND>, kSmem32, num_sms);
-  return f32  ? ctas_for(integral_kernel_f32<LA, LB, false, ND>, kSmem32, num_sms)
+int max_ctas_nd(bool f32, bool ds, int num_sms) {
+  return f32  ? ctas_for(integral_kernel_f32<LA, LB, ND>, kSmem32, num_sms)
          : ds ? ctas_for(integral_kernel_ds<LA, LB, ND>, kSmem64, num_sms)
               : ctas_for(integral_kernel<LA, LB, ND>, kSmem64, num_sms);
 }
 
 template <int LA, int LB>
-int max_ctas(bool f32, bool ds, bool hrr_ds, int nd, int num_sms) {
-  return nd == 2 ? max_ctas_nd<LA, LB, 2>(f32, ds, hrr_ds, num_sms) : max_ctas_nd<LA, LB, 1>(f32, ds, hrr_ds, num_sms);
+int max_ctas(bool f32, bool ds, int nd, int num_sms) {
+  return nd == 2 ? max_ctas_nd<LA, LB, 2>(f32, ds, num_sms) : max_ctas_nd<LA, LB, 1>(f32, ds, num_sms);
 }
 
 }  // namespace
@@ -755,15 +738,15 @@ cudaError_t launch_integrals(cudaStream_t st, int list, const IntegralArgs& a, i
   return cudaErrorInvalidValue;
 }
 
-int integral_max_ctas(int list, int num_sms, bool ds, bool hrr_ds, int n_dens) {
+int integral_max_ctas(int list, int num_sms, bool ds, int n_dens) {
   const bool f32 = list >= kNumClasses;
   switch (list % kNumClasses) {
-    case 0: return max_ctas<0, 0>(f32, ds, hrr_ds, n_dens, num_sms);
-    case 1: return max_ctas<1, 0>(f32, ds, hrr_ds, n_dens, num_sms);
-    case 2: return max_ctas<1, 1>(f32, ds, hrr_ds, n_dens, num_sms);
-    case 3: return max_ctas<2, 0>(f32, ds, hrr_ds, n_dens, num_sms);
-    case 4: return max_ctas<2, 1>(f32, ds, hrr_ds, n_dens, num_sms);
-    case 5: return max_ctas<2, 2>(f32, ds, hrr_ds, n_dens, num_sms);
+    case 0: return max_ctas<0, 0>(f32, ds, n_dens, num_sms);
+    case 1: return max_ctas<1, 0>(f32, ds, n_dens, num_sms);
+    case 2: return max_ctas<1, 1>(f32, ds, n_dens, num_sms);
+    case 3: return max_ctas<2, 0>(f32, ds, n_dens, num_sms);
+    case 4: return max_ctas<2, 1>(f32, ds, n_dens, num_sms);
+    case 5: return max_ctas<2, 2>(f32, ds, n_dens, num_sms);
   }
   return num_sms;
 }

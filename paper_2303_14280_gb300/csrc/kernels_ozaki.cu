@@ -1,4 +1,4 @@
-// Split-product tensor-core GEMMs of the mixed form on sm_103a (tcgen05):
+// Split-product tensor-core GEMMs of the mixed form (SNK_GEMM_SPLIT) on sm_103a (tcgen05):
 // F_j = X_j P (Eq. batch_local_exx) and Kt += G_j^T X_j (Eq. usym_k).
 //
 // Every FP64 operand is cut into bf16 slices on a fixed-point grid (an

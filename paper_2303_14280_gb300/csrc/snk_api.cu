@@ -141,7 +141,7 @@ struct snk_ctx {
   DevBuf<Tile> tiles;
   DevBuf<double> ws;
   DevBuf<float> ws32;
-  // tensor-core products (SNK_GEMM_TC): bf16 slice arena, split and product jobs, error flag
+  // tensor-core split products (SNK_GEMM_SPLIT): bf16 slice arena, split and product jobs, error flag
   DevBuf<uint8_t> arena;
   DevBuf<OzSplitJob> ozsplit;
   DevBuf<OzGemmJob> ozjobs;
@@ -153,10 +153,10 @@ struct snk_ctx {
 
   struct Chunk {
     int b0 = 0, b1 = 0;
-    int64_t bytes = 0, xn = 0, goff = 0, gbytes = 0, g32off = 0, g32n = 0;
+    int64_t bytes = 0, xn = 0, goff = 0, gbytes = 0;
     int max_ldq = 0, max_nS = 0, max_nB = 0, max_nBshell = 0;
     int64_t tile_off[kNumLists] = {0}, tile_n[kNumLists] = {0};
-    // SNK_GEMM_TC: split jobs of the F and K phases, product jobs of F hi, F lo, K hi, K lo
+    // SNK_GEMM_SPLIT: split jobs of the F and K phases, product jobs of F hi, F lo, K hi, K lo
     int ozs_off[2] = {0, 0}, ozs_n[2] = {0, 0}, ozs_rows[2] = {0, 0}, ozs_k[2] = {0, 0};
     int ozg_off[4] = {0, 0, 0, 0}, ozg_n[4] = {0, 0, 0, 0}, ozg_tiles[4] = {0, 0, 0, 0};
     int64_t arena_bytes = 0;
@@ -354,13 +354,13 @@ int make_tiles(snk_ctx* c, cudaStream_t st) {
 void set_max_ctas(snk_ctx* c) {
   const bool ds = c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals;
   for (int k = 0; k < kNumLists; ++k)
-    c->max_ctas[k] = integral_max_ctas(k, c->num_sms, ds, c->opt.fp32_hrr_ds != 0, c->n_dens);
+    c->max_ctas[k] = integral_max_ctas(k, c->num_sms, ds, c->n_dens);
   c->ctas_nd = c->n_dens;
 }
 
 int check_device_flags(snk_ctx* c);
 
-// Split and product jobs of the tensor-core GEMMs (SNK_GEMM_TC) for every
+// Split and product jobs of the tensor-core GEMMs (SNK_GEMM_SPLIT) for every
 // chunk: where each operand's slices go in the chunk's arena (the F phase and
 // the K phase reuse the same arena), and the (batch, tier, density) products
 // with their tile numbering.  Operands of a tier with no rows are left out.
@@ -599,10 +599,8 @@ int screen_and_plan(snk_ctx* c) {
 
   // shells of V_j -> F / G columns (molecule-local function indices); with
   // the split GEMMs the shells of high-tier pairs come first, [0, nS_hi)
-  const bool tc = mixed && c->opt.gemm == SNK_GEMM_TC;
-  const bool split = mixed && (c->opt.gemm == SNK_GEMM_SPLIT || tc);
-  if (tc && s.n_mol != 1)
-    return fail(c, SNK_ERR_UNSUPPORTED, "gemm = SNK_GEMM_TC needs a single-molecule handle");
+  const bool split = mixed && c->opt.gemm == SNK_GEMM_SPLIT;
+  const bool tc = split;
   std::vector<int> hcolmap(cmn, -1), hsfunc;
   auto& bd = c->hbatch;
   c->chunks.clear();
@@ -672,7 +670,7 @@ int screen_and_plan(snk_ctx* c) {
     while (j < nb) {
       // F and G of density d at foff / goff + d ldq nS
       int64_t xs = (int64_t)bd[j].ldq * bd[j].nB, fs = (int64_t)nd * bd[j].ldq * bd[j].nS;
-      int64_t bytes = (xo + xs + 2 * (fo + fs)) * 8 + (mixed ? 2 * (fo + fs) * 4 : 0);
+      int64_t bytes = (xo + xs + 2 * (fo + fs)) * 8 + (mixed ? (fo + fs) * 4 : 0);
       const int64_t ozf = tc ? oz_bytes(bd[j], 0) : 0, ozk = tc ? oz_bytes(bd[j], 1) : 0;
       bytes += std::max(af + ozf, ak + ozk);
       if (j > ch.b0 && bytes > c->ws_budget) break;
@@ -685,12 +683,10 @@ int screen_and_plan(snk_ctx* c) {
     ch.arena_bytes = std::max(af, ak);
     need_arena = std::max(need_arena, ch.arena_bytes);
     ch.b1 = j;
-    int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0, g32cur = fo;
+    int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0;
     ch.xn = xo;
     ch.goff = gcur;
     ch.gbytes = fo * 8;
-    ch.g32off = g32cur;
-    ch.g32n = mixed ? fo : 0;
     for (int t = ch.b0; t < ch.b1; ++t) {
       const int64_t fs = (int64_t)nd * bd[t].ldq * bd[t].nS;
       bd[t].xoff = xcur;
@@ -698,11 +694,9 @@ int screen_and_plan(snk_ctx* c) {
       bd[t].foff = fcur;
       bd[t].goff = gcur;
       bd[t].foff32 = f32cur;
-      bd[t].goff32 = g32cur;
       fcur += fs;
       gcur += fs;
       f32cur += fs;
-      g32cur += fs;
       ch.max_ldq = std::max(ch.max_ldq, bd[t].ldq);
       ch.max_nS = std::max(ch.max_nS, bd[t].nS);
       ch.max_nB = std::max(ch.max_nB, bd[t].nB);
@@ -710,7 +704,7 @@ int screen_and_plan(snk_ctx* c) {
     }
     ch.bytes = (xo + 2 * fo) * 8;
     need = std::max(need, xo + 2 * fo);
-    if (mixed) need32 = std::max(need32, 2 * fo);
+    if (mixed) need32 = std::max(need32, fo);
     c->chunks.push_back(ch);
   }
   SNK_CK(c, c->ws.ensure((size_t)need));
@@ -796,8 +790,6 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.pair_ab = reinterpret_cast<const float2*>(c->pair_ab.p);
   a.prims_f32 = reinterpret_cast<const float4*>(c->prims_f32.p);
   a.hi_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals) ? 1 : 0;
-  a.f32_g64 = c->opt.fp32_g64 ? 1 : 0;
-  a.f32_hrr_ds = c->opt.fp32_hrr_ds ? 1 : 0;
   a.n_dens = c->n_dens;
   return a;
 }
@@ -807,12 +799,9 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
 int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   Setup& s = c->s;
   const bool mixed = c->opt.precision == SNK_PREC_MIXED;
-  const bool tc = mixed && c->opt.gemm == SNK_GEMM_TC;
-  const bool split = mixed && c->opt.gemm == SNK_GEMM_SPLIT;
-  const bool df32 = mixed && (c->opt.gemm == SNK_GEMM_DF32 || split);
-  const int fmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 1)) ? 1 : 0;
-  const int kmode = df32 ? 2 : (mixed && (c->opt.tensor_gemms & 2)) ? 1 : 0;
-  const int gpart = split ? 1 : 0;  // with split: df32 on the high-tier columns, then mode 3 on the rest
+  const bool tc = mixed && c->opt.gemm == SNK_GEMM_SPLIT;  // the tensor-core split products
+  const bool df32 = mixed && c->opt.gemm == SNK_GEMM_DF32;
+  const int gmode = df32 ? 2 : 0;
   const int nd = c->n_dens;
   const int64_t pk = s.packed;
   int ev = 0;
@@ -876,23 +865,13 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     } else {
       for (int d = 0; d < nd; ++d) {
         SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
-                               c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, fmode, gpart,
-                               d));
+                               c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, mixed ? c->ws32.p : nullptr, gmode, d));
         ++c->launches_build;
       }
     }
     SNK_CK(c, mark());
-    if (tc) {
-      SNK_CK(c, oz_gemm(ch, 1));
-    } else if (split) {
-      for (int d = 0; d < nd; ++d) {
-        SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p + d * pk, c->P2.p + d * pk, c->xfunc.p,
-                               c->sfunc.p, c->fcomp.p, c->w.p, c->ws.p, c->ws32.p, 3, 2, d));
-        ++c->launches_build;
-      }
-    }
+    if (tc) SNK_CK(c, oz_gemm(ch, 1));
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
-    if (mixed && !c->opt.fp32_g64) SNK_CK(c, cudaMemsetAsync(c->ws32.p + ch.g32off, 0, sizeof(float) * ch.g32n, st));
     SNK_CK(c, mark());
     // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, list by list
     for (int k = 0; k < kNumLists; ++k) {
@@ -904,11 +883,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
       }
       SNK_CK(c, mark());
     }
-    // the FP32 pairs' G into the FP64 G, then the operands of Kt_d += G_dj^T X_j, Eq. (usym_k)
-    if (mixed && ch.g32n > 0 && !c->opt.fp32_g64) {
-      SNK_CK(c, launch_merge_g32(st, c->ws32.p + ch.g32off, ch.g32n, c->ws.p + ch.goff));
-      ++c->launches_build;
-    }
+    // the operands of Kt_d += G_dj^T X_j, Eq. (usym_k)
     if (tc) {
       SNK_CK(c, oz_split(ch, 1));
     } else if (df32) {
@@ -921,20 +896,12 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     } else {
       for (int d = 0; d < nd; ++d) {
         SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p,
-                               c->Khat.p + d * pk, kmode, gpart, d));
+                               c->Khat.p + d * pk, gmode, d));
         ++c->launches_build;
       }
     }
     SNK_CK(c, mark());
-    if (tc) {
-      SNK_CK(c, oz_gemm(ch, 3));
-    } else if (split) {
-      for (int d = 0; d < nd; ++d) {
-        SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p,
-                               c->Khat.p + d * pk, 3, 2, d));
-        ++c->launches_build;
-      }
-    }
+    if (tc) SNK_CK(c, oz_gemm(ch, 3));
     SNK_CK(c, mark());
   }
   // K_d = (Kt_d + Kt_d^T) / 2 in every molecule block, Eq. (sn_k)
@@ -1116,10 +1083,8 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   else
     snk_options_default(&c->opt);
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
-  if (c->opt.gemm < 0 || c->opt.gemm > 3 || c->opt.tensor_gemms < 0 || c->opt.tensor_gemms > 3 ||
-      (c->opt.gemm != SNK_GEMM_FP64 && c->opt.tensor_gemms != 0) || c->opt.ds_integrals < 0 ||
-      c->opt.ds_integrals > 1 || c->opt.fp32_g64 < 0 || c->opt.fp32_g64 > 1 ||
-      c->opt.fp32_hrr_ds < 0 || c->opt.fp32_hrr_ds > 1 || c->opt.tc_slices_hi < 3 || c->opt.tc_slices_hi > 6 ||
+  if (c->opt.gemm < 0 || c->opt.gemm > 2 || c->opt.ds_integrals < 0 || c->opt.ds_integrals > 1 ||
+      c->opt.tc_slices_hi < 3 || c->opt.tc_slices_hi > 6 ||
       c->opt.tc_slices_lo < 3 || c->opt.tc_slices_lo > 6)
     return SNK_ERR_INVALID_ARG;
   for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
@@ -1275,16 +1240,13 @@ void snk_options_default(snk_options* o) {
   o->fp32_bound = 1e-6;
   o->workspace_bytes = 0;
   o->distance_bound = 1;
-  o->tensor_gemms = 0;
   o->gemm = SNK_GEMM_FP64;
   o->ds_integrals = 0;
-  o->fp32_g64 = 0;
-  o->fp32_hrr_ds = 0;
   o->learned_fp32 = -99.0;
   o->graph = 0;
   o->learned_skip = -11.0;
   o->tc_slices_hi = 5;
-  o->tc_slices_lo = 3;
+  o->tc_slices_lo = 4;
 }
 
 const char* snk_status_string(int status) {
@@ -1814,7 +1776,7 @@ int learn_collect(snk_ctx* c, int stride, int64_t cap, float* feat, float* lab, 
     SNK_CK(c, launch_collocation(st, db, nbc, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                  dev_basis(c), c->ws.p));
     SNK_CK(c, launch_fgemm(st, db, nbc, ch.max_ldq, ch.max_nS, c->P.p, nullptr, c->xfunc.p, c->sfunc.p, c->fcomp.p,
-                           c->w.p, c->ws.p, nullptr, 0, 0, 0));
+                           c->w.p, c->ws.p, nullptr, 0, 0));
     SNK_CK(c, launch_xmax(st, db, nbc, c->ws.p, dxmax.p));
     for (int k = 0; k < kNumLists; ++k) {
       std::vector<Tile> ht;

@@ -87,8 +87,8 @@ struct BatchDesc {
   int32_t sfunc_off;
   int32_t bshell_off;
   int32_t nBshell;
-  int64_t foff32;    // mixed form: offsets (floats) of the FP32 copies of F and G
-  int64_t goff32;
+  int64_t foff32;    // mixed form: offset (floats) of the FP32 copy of F
+  int64_t pad64_;
   int32_t mol;       // molecule of the batch, its first shell and function, N_b,m
   int32_t ms0;
   int32_t mf0;
@@ -222,19 +222,14 @@ cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, 
 cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list);
 // P, Khat and K below are the packed molecule blocks (BatchDesc::pk_off,
 // MolDesc::pk_off); xfunc / sfunc hold molecule-local function indices.
-// mode: 0 FP64, 1 split-TF32 tensor cores, 2 double-FP32 (X, G and P2 then
-// hold (hi, lo) float pairs in place of the doubles, see launch_split_df32).
-// mode 3: split-TF32 on the hi floats of (hi, lo) operands, FP32 partial sums
-// of 64 terms folded into double-FP32.  part: 0 all F / G columns, 1 the
-// high-tier columns [0, nS_hi), 2 the rest.  dens: which density's F / G
+// mode: 0 FP64, 2 double-FP32 (X, G and P2 then hold (hi, lo) float pairs in
+// place of the doubles, see launch_split_df32).  dens: which density's F / G
 // block of each batch (at foff / goff + dens ldq nS).
 cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nS,
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc,
-                         const double* fcomp, const double* w, double* ws, float* ws32, int mode, int part,
-                         int dens);
+                         const double* fcomp, const double* w, double* ws, float* ws32, int mode, int dens);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int part,
-                         int dens);
+                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int dens);
 // In place, each double of buf[0, n) becomes the float pair (fl32(v), fl32(v - fl32(v))).
 cudaError_t launch_split_df32(cudaStream_t st, double* buf, int64_t n);
 cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n, float2* dst);
@@ -270,13 +265,11 @@ struct IntegralArgs {
   // Pz_lo, pref}, {PAx, PAy, PAz, pref_far}, {k1, k2, k3, 0}
   const float4* prims_f32;
   int hi_ds;
-  int f32_g64;  // FP32 lists add into the FP64 G (ws + goff) instead of the FP32 copy
-  int f32_hrr_ds;  // FP32 lists run the HRR in double-FP32
-  int n_dens;      // densities: F and G of density d at foff / goff (+32) + d ldq nS
+  int n_dens;      // densities: F and G of density d at foff / goff (F32: foff32) + d ldq nS
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
-int integral_max_ctas(int cls, int num_sms, bool ds, bool hrr_ds, int n_dens);
+int integral_max_ctas(int cls, int num_sms, bool ds, int n_dens);
 cudaError_t launch_debug_A(cudaStream_t st, int cls, const PairHdr* pair, const PrimPair* prims,
                            const double* boys, int64_t n, const double* xyz, double* xi);
 cudaError_t launch_debug_boys(cudaStream_t st, const double* boys, int64_t n, const double* T,
@@ -290,7 +283,6 @@ void class_flops(int cls, double* per_prim, double* per_pair);
 // the (batch, list)'s tiles from tiles[tstart[batch * kNumLists + list]] on.
 cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batches, const int* counts,
                              const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles);
-cudaError_t launch_merge_g32(cudaStream_t st, const float* g32, int64_t n, double* g64);
 
 // ---------------------------------------------------------------- split-product tensor-core GEMMs
 

@@ -38,8 +38,8 @@ def test_options_defaults():
     o = snk.options()
     assert o.batch_max == 4096 and o.eps_E == 1e-12 and o.screen == 1 and o.precision == 0
     # the plain FP64 form unless a form is asked for
-    assert o.gemm == 0 and o.ds_integrals == 0 and o.tensor_gemms == 0 and o.graph == 0
-    assert o.fp32_g64 == 0 and o.fp32_hrr_ds == 0 and o.distance_bound == 1
+    assert o.gemm == 0 and o.ds_integrals == 0 and o.graph == 0 and o.distance_bound == 1
+    assert o.tc_slices_hi == 5 and o.tc_slices_lo == 4
     assert o.learned_skip == -11.0 and o.learned_fp32 == -99.0 and o.fp32_bound == 1e-6
     assert snk.options(gemm="split").gemm == 2 and snk.options(precision="mixed").precision == 1
     with pytest.raises(ValueError):

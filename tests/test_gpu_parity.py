@@ -203,9 +203,9 @@ def test_mixed_precision_form(snk):
     Kf, sf = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e300)
     assert sf["pairs_kept_fp32"] == sf["pairs_kept"]
     assert 1e-12 < np.max(np.abs(Kf - Kref)) <= 1e-5
-    # split-TF32 tensor-core products (FP32 accumulation): FP32-level K
-    Kt, st = _gpu_K(snk, p, batch_max=300, precision="mixed", tensor_gemms=3)
-    assert np.max(np.abs(Kt - Kref)) <= 1e-4
+    # tensor-core split products at their fewest slices (3 per operand, ~2^-22 of the run maxima)
+    Kt, st = _gpu_K(snk, p, batch_max=300, precision="mixed", gemm="split", tc_slices_hi=3, tc_slices_lo=3)
+    assert np.max(np.abs(Kt - Kref)) <= 1e-6
     assert np.max(np.abs(Kt - Kt.T)) == 0.0
 
 
@@ -229,20 +229,21 @@ def test_double_fp32_gemms(snk):
     Km, sm = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=1e-3, gemm="df32")
     assert sm["pairs_kept_fp32"] > 0
     assert np.max(np.abs(Km - Kref)) <= 1e-8
-    # plain precision ignores the GEMM mode; combining it with tensor_gemms is rejected
+    # plain precision ignores the GEMM mode; out-of-range GEMM options are rejected
     Kp, _ = _gpu_K(snk, p, batch_max=300, gemm="df32")
     assert np.max(np.abs(Kp - K64)) <= 1e-15       # FP64 atomics: summation order only
-    with pytest.raises(snk.SnkError) as e:
-        snk.Engine(p.basis, p.grid, precision="mixed", gemm="df32", tensor_gemms=1)
-    assert e.value.status == -1
+    for bad in (dict(gemm=3), dict(gemm="split", tc_slices_hi=7), dict(gemm="split", tc_slices_lo=2)):
+        with pytest.raises(snk.SnkError) as e:
+            snk.Engine(p.basis, p.grid, precision="mixed", **bad)
+        assert e.value.status == -1
     # captured in a CUDA graph and replayed
     eng = snk.Engine(p.basis, p.grid, batch_max=300, precision="mixed", fp32_bound=1e-3, gemm="df32", graph=1)
     eng.set_density(p.P)
     Kg1 = eng.build_K()
     Kg2 = eng.build_K()
     eng.close()
-    # FP32 atomics into G32 make the FP32 pairs' sums order-dependent: ~1e-11 run to run
-    assert np.max(np.abs(Kg1 - Km)) <= 1e-10 and np.max(np.abs(Kg2 - Km)) <= 1e-10
+    # the FP32 pairs' G goes through FP64 atomics: summation order only, ~1e-14 run to run
+    assert np.max(np.abs(Kg1 - Km)) <= 1e-12 and np.max(np.abs(Kg2 - Km)) <= 1e-12
 
 
 def test_double_fp32_integrals(snk, chain4):
@@ -275,8 +276,8 @@ def test_double_fp32_integrals(snk, chain4):
 
 
 def test_split_gemms(snk):
-    """SNK_GEMM_SPLIT: double-FP32 products for the F columns / G rows of
-    shells in FP64-tier pairs, chunked split-TF32 for the shells only FP32-tier
+    """SNK_GEMM_SPLIT: the tcgen05 split products, 5 slices for the F columns
+    / G rows of shells in FP64-tier pairs and 4 for the shells only FP32-tier
     pairs touch; the FP32 tier's own accuracy bounds the result."""
     p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
     Kref = oracle.snk_K(p.basis, p.grid, p.P)
@@ -296,22 +297,16 @@ def test_split_gemms(snk):
     assert np.max(np.abs(K0 - Kref)) <= TOL_K
 
 
-def test_fp32_tier_accumulation_and_hrr_variants(snk):
-    """FP32 pairs added straight into the FP64 G (fp32_g64) and their HRR run in
-    double-FP32 (fp32_hrr_ds): both keep the mixed form's parity; neither
-    changes its accuracy measurably (the FP32 tier's error is in the FP32
-    Boys seeds and recursions), so both are off by default."""
+def test_fp32_tier_run_to_run(snk):
+    """The FP32 pairs add into the FP64 G with FP64 atomics, so repeated
+    builds of the mixed form differ only by FP64 summation order."""
     p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
-    Kref = oracle.snk_K(p.basis, p.grid, p.P)
-    form = dict(batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="split")
-    K0, s0 = _gpu_K(snk, p, **form)
-    K1, _ = _gpu_K(snk, p, fp32_g64=1, **form)
-    K2, _ = _gpu_K(snk, p, fp32_hrr_ds=1, **form)
-    assert s0["pairs_kept_fp32"] > 0
-    for K in (K0, K1, K2):
-        assert np.max(np.abs(K - Kref)) <= 1e-8
-        assert np.max(np.abs(K - K.T)) == 0.0
-    assert np.max(np.abs(K1 - K0)) <= 1e-9 and np.max(np.abs(K2 - K0)) <= 1e-9
+    eng = snk.Engine(p.basis, p.grid, batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1,
+                     gemm="split")
+    eng.set_density(p.P)
+    Ks = [eng.build_K() for _ in range(3)]
+    eng.close()
+    assert max(np.max(np.abs(K - Ks[0])) for K in Ks[1:]) <= 1e-13
 
 
 def test_two_densities_in_one_build(snk, chain4):

@@ -1,4 +1,4 @@
-"""The split-product tensor-core GEMM (SNK_GEMM_TC) through the C ABI.
+"""The split-product tensor-core GEMM (gemm = SNK_GEMM_SPLIT) through the C ABI.
 
 Unit level (snk_debug_tc_gemm, C = A B^T): integer matrices whose slices are
 exact must come out exact, which pins the shared-memory layout, the tcgen05
@@ -112,21 +112,21 @@ def _gpu_K(snk, p, **opt):
 
 def test_tensor_core_products_in_the_mixed_form(snk):
     """F = X P and Kt = G^T X on the tensor cores (5 slices on the high-tier
-    columns and rows, 3 on the rest) against the oracle and the double-FP32
+    columns and rows, 4 on the rest) against the oracle and the double-FP32
     products, on ragged batches, one chunk and several."""
     p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
     Kref = oracle.snk_K(p.basis, p.grid, p.P)
     form = dict(batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1)
     Kd, sd = _gpu_K(snk, p, gemm="df32", **form)
-    Kt, st = _gpu_K(snk, p, gemm="tc", **form)
+    Kt, st = _gpu_K(snk, p, gemm="split", **form)
     assert 0 < st["gemm_flops_hi"] < st["gemm_flops"] and st["gemm_tc_flops"] > 0
     assert np.max(np.abs(Kt - Kref)) <= 1e-8
     assert np.max(np.abs(Kt - Kd)) <= 1e-8
     assert np.max(np.abs(Kt - Kt.T)) == 0.0 and np.all(np.isfinite(Kt))
-    Kc, sc = _gpu_K(snk, p, gemm="tc", workspace_bytes=1 << 20, **form)
+    Kc, sc = _gpu_K(snk, p, gemm="split", workspace_bytes=1 << 20, **form)
     assert sc["n_chunks"] > 1 and np.max(np.abs(Kc - Kref)) <= 1e-8
     # every pair in the high tier: FP64-grade products (6 slices) keep the plain form's 1e-10
-    K0, s0 = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=0.0, ds_integrals=1, gemm="tc",
+    K0, s0 = _gpu_K(snk, p, batch_max=300, precision="mixed", fp32_bound=0.0, ds_integrals=1, gemm="split",
                     tc_slices_hi=6)
     assert s0["gemm_flops_hi"] == s0["gemm_flops"]
     assert np.max(np.abs(K0 - Kref)) <= 1e-10
