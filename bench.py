@@ -364,7 +364,7 @@ def timed(runner, steps, warmup, stream, barrier):
             for k in ("ms_integrals", "ms_integrals_fp32", "ms_fgemm", "ms_kgemm", "ms_screen", "ms_collocation",
                       "ms_finish", "integral_flops", "flops_fp32", "gemm_flops", "kernel_launches", "integrals",
                       "colloc_bytes", "ms_gemm_split", "ms_gemm_hi", "ms_gemm_lo", "gemm_tc_flops",
-                      "gemm_flops_hi"):
+                      "gemm_flops_hi", "pair_points_fp32", "pair_points_fp32_listed"):
                 acc[k] = acc.get(k, 0.0) + float(s[k])
     e1.record(stream)
     torch.cuda.synchronize()
@@ -444,6 +444,7 @@ def main():
     ap.add_argument("--gemm", default=None, choices=["split", "df32"],
                     help="products of the chosen form (default: its own)")
     ap.add_argument("--slices", default=None, help="split: slices of the high and low tier, e.g. 5,4")
+    ap.add_argument("--eps-tile", type=float, default=None, help="tile screen of the FP32 lists (0 = off)")
     ap.add_argument("--workload", default=WORKLOAD,  # cluster24: a small case of cluster96's shape for profiles
                     choices=["cluster24", "cluster96", "cluster256", "cluster512", "batch64", "batch64_small"])
     args = ap.parse_args()
@@ -488,6 +489,8 @@ def main():
         if args.slices:
             hi, lo = (int(x) for x in args.slices.split(","))
             chosen_opts.update(tc_slices_hi=hi, tc_slices_lo=lo)
+        if args.eps_tile is not None:
+            chosen_opts["eps_tile"] = args.eps_tile
         form = ("mixed: rigorous sn-LinK at 1e-10, FP32 integrals for pairs with estimate < 3e-4, double-FP32 "
                 "integrals otherwise; F = X P and Kt = G^T X on the tcgen05 tensor cores as sums of bf16 "
                 "fixed-point slice products (5 slices for the columns / rows of shells in double-FP32 pairs, 4 "
@@ -669,6 +672,8 @@ def main():
         "pairs_kept": sum(s["pairs_kept"] for s in st_ch),
         "pairs_kept_fp32": sum(s["pairs_kept_fp32"] for s in st_ch),
         "pairs_learned_skipped": sum(s["pairs_learned_skipped"] for s in st_ch),
+        "fp32_pair_points_computed_fraction": (acc["pair_points_fp32"] / acc["pair_points_fp32_listed"]
+                                               if acc.get("pair_points_fp32_listed") else None),
         "create_s": ch_create,
         "roofline": roof,
         "clocks": clocks,

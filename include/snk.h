@@ -141,6 +141,15 @@ typedef struct {
                               sum of the products below the two leading levels)  */
   int32_t tc_slices_lo;    /* SNK_GEMM_SPLIT: the same for the rest, 3..6 (default
                               4: 10 products, ~2^-30)                           */
+  double eps_tile;         /* mixed form, FP32 pairs, gemm FP64 or SPLIT: a kept
+                              (batch, pair) block is also screened per 128-point
+                              tile of the batch (points ordered by a finer
+                              octree), skipping the tile when A-tilde_ab x
+                              max(sum_i |F_b(i)| max|Phi(i)|, the same with a)
+                              over the tile's points -- a bound of what the
+                              tile adds to any K-tilde entry, up to the
+                              component factors -- is below eps_tile; 0 = off
+                              (default)                                         */
   double reserved[3];
 } snk_options;
 
@@ -177,6 +186,10 @@ typedef struct {
   double ms_gemm_lo;           /* last build: both products, the remaining ones      */
   double gemm_tc_flops;        /* SNK_GEMM_SPLIT: bf16 tensor-core flops issued per build
                                   (2 M N K per slice product, padded tile sizes)     */
+  double pair_points_fp32;     /* last build: FP32-tier (pair, point) evaluations made
+                                  (after the tile screen; integrals_fp32 and
+                                  flops_fp32 count the same work)                  */
+  double pair_points_fp32_listed; /* the same before the tile screen               */
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,

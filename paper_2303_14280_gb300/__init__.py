@@ -76,7 +76,7 @@ class SnkOptions(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("graph", ctypes.c_int32),
                 ("learned_skip", ctypes.c_double), ("gemm", ctypes.c_int32), ("ds_integrals", ctypes.c_int32),
                 ("learned_fp32", ctypes.c_double), ("tc_slices_hi", ctypes.c_int32),
-                ("tc_slices_lo", ctypes.c_int32), ("reserved", ctypes.c_double * 3)]
+                ("tc_slices_lo", ctypes.c_int32), ("eps_tile", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
 
 
 class SnkStats(ctypes.Structure):
@@ -92,7 +92,8 @@ class SnkStats(ctypes.Structure):
                 ("ms_integrals_fp32", ctypes.c_double), ("pairs_learned_skipped", ctypes.c_int64),
                 ("gemm_flops_hi", ctypes.c_double), ("ms_integrals_class_fp32", ctypes.c_double * 6),
                 ("colloc_bytes", ctypes.c_double), ("ms_gemm_split", ctypes.c_double),
-                ("ms_gemm_hi", ctypes.c_double), ("ms_gemm_lo", ctypes.c_double), ("gemm_tc_flops", ctypes.c_double)]
+                ("ms_gemm_hi", ctypes.c_double), ("ms_gemm_lo", ctypes.c_double), ("gemm_tc_flops", ctypes.c_double),
+                ("pair_points_fp32", ctypes.c_double), ("pair_points_fp32_listed", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -396,6 +396,13 @@ int build_setup_one(const snk_basis* basis, const snk_grid* grid, const snk_opti
     octree(idx, lo, hi, grid->xyz, opt->batch_max, 0, leaves);
     lo = hi;
   }
+  // inside each batch, the points in the order of a finer octree (leaves of at
+  // most kPointTile points): the 128-point tiles of the integral kernels are
+  // then spatially compact, which the per-tile screen exploits
+  for (const auto& lf : leaves) {
+    std::vector<std::pair<size_t, size_t>> sub;
+    octree(idx, lf.first, lf.second, grid->xyz, kPointTile, 0, sub);
+  }
   s->perm = idx;
   s->xyz.resize(3 * npts);
   s->w.resize(npts);

@@ -323,6 +323,44 @@ __global__ void xmax_kernel(const BatchDesc* __restrict__ batches, const double*
   }
 }
 
+// Tile screen sums: one block per (tile of 128 points, batch).  The points'
+// max |X| first (integer max of the IEEE bit patterns: no FP64 arithmetic),
+// then per F column the warp-reduced sum over the tile of |F32| max |X|.
+__global__ void __launch_bounds__(256) tile_sums_kernel(const BatchDesc* __restrict__ batches,
+                                                        const double* __restrict__ ws, const float* __restrict__ ws32,
+                                                        int n_dens, float* __restrict__ tsum) {
+  const BatchDesc bd = batches[blockIdx.y];
+  const int tile = blockIdx.x, i0 = tile * kPointTile;
+  if (i0 >= bd.q) return;
+  __shared__ float xt[kPointTile];
+  const double* X = ws + bd.xoff;
+  for (int t = threadIdx.x; t < kPointTile; t += blockDim.x) {
+    unsigned long long m = 0;
+    if (i0 + t < bd.q)
+      for (int c = 0; c < bd.nB; ++c) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(X[(int64_t)c * bd.ldq + i0 + t]) &
+                                     0x7FFFFFFFFFFFFFFFull;
+        m = b > m ? b : m;
+      }
+    xt[t] = (float)__longlong_as_double((long long)m);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* out = tsum + bd.ssoff + (int64_t)tile * bd.nS;
+  const int64_t dstr = (int64_t)bd.ldq * bd.nS;
+  for (int c = warp; c < bd.nS; c += blockDim.x / 32) {
+    float s = 0.f;
+    for (int d = 0; d < n_dens; ++d) {
+      const float* F = ws32 + bd.foff32 + d * dstr + (int64_t)c * bd.ldq + i0;
+#pragma unroll
+      for (int q = 0; q < kPointTile / 32; ++q) s += fabsf(F[lane + 32 * q]) * xt[lane + 32 * q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[c] = s;
+  }
+}
+
 // ---------------------------------------------------------------- F-tilde
 
 // For molecule blockIdx.z: F-tilde_a^(j) = max_{mu in a} sum_nu |P_{mu nu}|
@@ -640,6 +678,13 @@ cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nba
     phit_f_kernel<<<grid, 128, 0, st>>>(dbatch, ws, w, xfunc, phit_f);
   }
   phit_b_kernel<<<nbatch, 256, 0, st>>>(dbatch, ws, w, phit_b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sums(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_tiles, const double* ws,
+                             const float* ws32, int n_dens, float* tsum) {
+  if (nbatch == 0 || max_tiles == 0) return cudaSuccess;
+  tile_sums_kernel<<<dim3(max_tiles, nbatch), 256, 0, st>>>(dbatch, ws, ws32, n_dens, tsum);
   return cudaGetLastError();
 }
 

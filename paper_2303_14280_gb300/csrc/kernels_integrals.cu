@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kIntThreads = kPointTile;
 constexpr int kMaxRun = 128;  // longest pair run of a tile (the autotuner's largest candidate)
+static_assert(kMaxRun == kIntThreads, "the FP32 kernel stages a tile's pairs one per thread");
 constexpr long long kBoysTMaxBits = 0x4049000000000000LL;  // bit pattern of 50.0
 static_assert(kBoysTMax == 50.0, "kBoysTMaxBits encodes 50.0");
 
@@ -182,9 +183,11 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
 
 // ---------------------------------------------------------------- FP32 pairs (mixed form)
 
-// FP32 seeds S_n = pref F_n(T): 6-term Taylor about the nearest node of a
-// 0.1-spaced float table below T = 30 (truncation < 3e-11), the asymptotic
-// form above (e^{-T} < 1e-13 is below FP32 resolution).
+// FP32 seeds S_n = pref F_n(T): 5-term Taylor about the nearest node of a
+// 0.1-spaced float table below T = 30 (|T - T_k| <= 0.05: truncation below
+// 3e-9 relative), the asymptotic form above (e^{-T} < 1e-13 is below FP32
+// resolution).  e^{-T} of the downward recursion comes from the hardware
+// exponential (__expf, ~2^-21 relative).
 template <int L>
 __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_far, const float* tab, float* S) {
   if (T < kBoysTMaxF) {
@@ -192,20 +195,14 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
     const int k = __float2int_rn(T * (float)(1.0 / kBoysH));
     const float4 lo = reinterpret_cast<const float4*>(tab)[2 * k];      // F_{L+m}/m!, m = 0..3
     const float4 hi = reinterpret_cast<const float4*>(tab)[2 * k + 1];  // m = 4, 5; e^{-T_k}; T_k
-    const float row[kBoysColsF] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-    const float x = row[kBoysColsF - 1] - T;
-    float f = row[kBoysTermsF - 1];
-#pragma unroll
-    for (int m = kBoysTermsF - 2; m >= 0; --m) f = fmaf(f, x, row[m]);
+    const float x = hi.w - T;
+    float f = fmaf(hi.x, x, lo.w);
+    f = fmaf(f, x, lo.z);
+    f = fmaf(f, x, lo.y);
+    f = fmaf(f, x, lo.x);
     S[L] = pref * f;
     if (L > 0) {
-      float e = 1.0f / 120.0f;
-      e = fmaf(e, x, 1.0f / 24.0f);
-      e = fmaf(e, x, 1.0f / 6.0f);
-      e = fmaf(e, x, 0.5f);
-      e = fmaf(e, x, 1.0f);
-      e = fmaf(e, x, 1.0f);
-      const float pe = (pref * row[kBoysTermsF]) * e;
+      const float pe = pref * __expf(-T);
       const float T2 = T + T;
 #pragma unroll
       for (int n = L - 1; n >= 0; --n) S[n] = fmaf(T2, S[n + 1], pe) * (1.0f / (2 * n + 1));
@@ -221,20 +218,21 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
   }
 }
 
-// Primitive pair in FP32, its product centre relative to the batch centre.
-// The FP32 lists of the mixed form.  Primitive-pair data come as one 64-byte
-// FP32 record per primitive pair with the product centre split into hi + lo
-// floats, and P - r_i is formed as (P_hi - r_hi) + (P_lo - r_lo) so that it is
-// accurate to FP32 relative to |P - r_i| however far the molecule sits from
-// the origin.  A tile's pair headers, columns and R_a - R_b are staged in
-// shared memory once per tile (one barrier per tile); the next pair's F is
-// loaded while the current pair computes; for the light classes each warp
-// also stages the pair's records (below).
+// The FP32 lists of the mixed form.  Each primitive pair is a 32-byte FP32
+// record {zeta, P - A, pref, pref_far, 1/(2 zeta)}; per (pair, point) the
+// kernel forms A - r_i once from the (hi, lo) float splits of A and r_i, and
+// P - r_i = (P - A) + (A - r_i) per primitive: accurate to FP32 relative to
+// the larger of |P - A| and |A - r_i| wherever the molecule sits, which is
+// what the VRR terms PA_x Theta and PC_x Theta need.  A tile's pair headers,
+// columns, R_a - R_b and R_a are staged in shared memory once per tile (one
+// barrier per tile); the next pair's F is loaded while the current pair
+// computes; for the light classes each warp also stages the pair's records
+// (below).
 template <int LA, int LB, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
-  constexpr int kStage = 16;  // primitive records per pair staged per warp (64 float4)
+  constexpr int kStage = 16;  // primitive records per pair staged per warp (32 float4)
   // staging pays for the light classes, whose few FP32 operations per
   // primitive cannot cover the record loads; heavier classes read the records
   // directly (fewer registers, more resident warps)
@@ -243,13 +241,14 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
   for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
   // the tile's pairs, staged once per tile: primitive range, shells, F / G
-  // columns and R_a - R_b
+  // columns, R_a - R_b and R_a
   __shared__ int s_ppo[kMaxRun], s_ppn[kMaxRun], s_sa[kMaxRun], s_sb[kMaxRun], s_ca[kMaxRun], s_cb[kMaxRun];
   __shared__ float2 s_ab[kMaxRun][3];  // (hi, lo)
+  __shared__ float2 s_A[kMaxRun][3];   // (hi, lo)
   // per warp, double-buffered: the current pair's primitive records; the next
   // pair's are loaded (coalesced, one request per 128 B) while this one computes
-  __shared__ float4 s_pr[STAGE ? kIntThreads / 32 : 1][2][STAGE ? kStage * 4 : 1];
-  __shared__ int s_tile;
+  __shared__ float4 s_pr[STAGE ? kIntThreads / 32 : 1][2][STAGE ? kStage * 2 : 1];
+  __shared__ int s_tile, s_wcnt[kIntThreads / 32];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (;;) {
@@ -261,22 +260,64 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     const Tile tile = a.tiles[t];
     const BatchDesc bd = a.batches[tile.batch];
     const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
-    const int nrun = tile.k1 - tile.k0;                // <= kMaxRun
-    for (int r = threadIdx.x; r < nrun; r += blockDim.x) {
-      const int p = a.pairlist[tile.k0 + r];
-      const PairHdr h = a.pairs[p];
-      s_ppo[r] = h.pp_off;
-      s_ppn[r] = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
-      s_sa[r] = h.sa;
-      s_sb[r] = h.sb;
-      s_ca[r] = cmap[h.sa];
-      s_cb[r] = cmap[h.sb];
-      const float2* ab = a.pair_ab + 4 * (size_t)p;
-      s_ab[r][0] = ab[0];
-      s_ab[r][1] = ab[1];
-      s_ab[r][2] = ab[2];
+    // stage the tile's pairs (one per thread, order kept); with the tile screen
+    // only those whose bound on this tile's points reaches eps_tile
+    int nrun;
+    {
+      const int r = threadIdx.x, n = tile.k1 - tile.k0;  // n <= kMaxRun = blockDim
+      int p = 0, ca = 0, cb = 0;
+      PairHdr h{};
+      bool keep = r < n;
+      if (keep) {
+        p = a.pairlist[tile.k0 + r];
+        h = a.pairs[p];
+        ca = cmap[h.sa];
+        cb = cmap[h.sb];
+        if (a.eps_tile > 0.f) {
+          const float* ts = a.tsum + bd.ssoff + (int64_t)(tile.i0 / kPointTile) * bd.nS;
+          float sa = 0.f, sb = 0.f;
+#pragma unroll
+          for (int u = 0; u < NA; ++u) sa += ts[ca + u];
+#pragma unroll
+          for (int v = 0; v < NB; ++v) sb += ts[cb + v];
+          keep = (float)a.pbound[p] * fmaxf(sa, sb) >= a.eps_tile;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) s_wcnt[wid] = __popc(bal);
+      __syncthreads();
+      int before = 0;
+      nrun = 0;
+#pragma unroll
+      for (int w = 0; w < kIntThreads / 32; ++w) {
+        before += w < wid ? s_wcnt[w] : 0;
+        nrun += s_wcnt[w];
+      }
+      if (keep) {
+        const int q = before + __popc(bal & ((1u << lane) - 1u));
+        s_ppo[q] = h.pp_off;
+        s_ppn[q] = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
+        s_sa[q] = h.sa;
+        s_sb[q] = h.sb;
+        s_ca[q] = ca;
+        s_cb[q] = cb;
+        const float2* ab = a.pair_ab + 4 * (size_t)p;
+        const float2* pa = a.pair_a + 4 * (size_t)p;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          s_ab[q][m] = ab[m];
+          s_A[q][m] = pa[m];
+        }
+      }
     }
     __syncthreads();
+    if (threadIdx.x == 0 && nrun > 0) {  // the work this tile computes, for the flop counts
+      unsigned long long npp = 0;
+      for (int r = 0; r < nrun; ++r) npp += (unsigned long long)s_ppn[r];
+      const unsigned long long pts = (unsigned long long)min(kPointTile, bd.q - tile.i0);
+      atomicAdd(&a.exec[0], npp * pts);
+      atomicAdd(&a.exec[1], (unsigned long long)nrun * pts);
+    }
     const int i = tile.i0 + threadIdx.x;
     const bool active = i < bd.q;  // inactive lanes still stage records for their warp
     if (nrun <= 0 || __all_sync(0xffffffffu, !active)) continue;
@@ -293,9 +334,9 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     // order changes K by ~1e-14 from run to run (FP32 atomics: ~1e-10)
     auto gadd = [&](int d, int col, float v) { atomicAdd(G64 + d * dstr + col * ldq, (double)v); };
     if (STAGE) {  // the first pair's records
-      const int n4 = min(s_ppn[0], kStage) * 4;
-      const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 4;
-      for (int e = lane; e < n4; e += 32) s_pr[wid][0][e] = src[e];
+      const int n2 = min(s_ppn[0], kStage) * 2;
+      const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 2;
+      if (lane < n2) s_pr[wid][0][lane] = src[lane];
       __syncwarp();
     }
     float ga[ND][NA], fa[ND][NA], fn[ND][NB];
@@ -306,13 +347,12 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       for (int v = 0; v < NB; ++v) fn[d][v] = active ? F[d * dstr + (s_cb[0] + v) * ldq] : 0.f;
     for (int r = 0; r < nrun; ++r) {
       const float4* rec = s_pr[STAGE ? wid : 0][r & 1];
-      float4 pre0 = make_float4(0.f, 0.f, 0.f, 0.f), pre1 = pre0;
-      int n4n = 0;
+      float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+      int n2n = 0;
       if (STAGE && r + 1 < nrun) {  // the next pair's records are in flight while this pair computes
-        n4n = min(s_ppn[r + 1], kStage) * 4;
-        const float4* src = a.prims_f32 + (size_t)s_ppo[r + 1] * 4;
-        if (lane < n4n) pre0 = src[lane];
-        if (lane + 32 < n4n) pre1 = src[lane + 32];
+        n2n = min(s_ppn[r + 1], kStage) * 2;
+        const float4* src = a.prims_f32 + (size_t)s_ppo[r + 1] * 2;
+        if (lane < n2n) pre = src[lane];
       }
       float fb[ND][NB];
 #pragma unroll
@@ -345,24 +385,26 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
               fa[d][u] = F[d * dstr + (cola + u) * ldq];
             }
         }
+        // A - r_i, once per pair and point
+        const float ACx = (s_A[r][0].x - cx.hi) + (s_A[r][0].y - cx.lo);
+        const float ACy = (s_A[r][1].x - cy.hi) + (s_A[r][1].y - cy.lo);
+        const float ACz = (s_A[r][2].x - cz.hi) + (s_A[r][2].y - cz.lo);
         float acc[C::NACC];
 #pragma unroll
         for (int u = 0; u < C::NACC; ++u) acc[u] = 0.f;
-        auto prim = [&](float4 r0, float4 r1, float4 r2, float4 r3) {
-          const float PCx = (r0.y - cx.hi) + (r1.x - cx.lo);
-          const float PCy = (r0.z - cy.hi) + (r1.y - cy.lo);
-          const float PCz = (r0.w - cz.hi) + (r1.z - cz.lo);
+        auto prim = [&](float4 r0, float4 r1) {
+          const float PCx = r0.y + ACx, PCy = r0.z + ACy, PCz = r0.w + ACz;
           const float T = r0.x * fmaf(PCx, PCx, fmaf(PCy, PCy, PCz * PCz));
           float S[C::L + 1];
-          boys_seeds_f32<C::L>(T, r1.w, r2.w, s_tabf, S);
-          C::vrr(S, r2.x, r2.y, r2.z, PCx, PCy, PCz, r3.x, r3.y, r3.z, acc);
+          boys_seeds_f32<C::L>(T, r1.x, r1.y, s_tabf, S);
+          C::vrr(S, r0.y, r0.z, r0.w, PCx, PCy, PCz, r1.z, 2.0f * r1.z, 3.0f * r1.z, acc);
         };
         const int ppn = s_ppn[r];
         if (STAGE && ppn <= kStage) {
-          for (int q = 0; q < ppn; ++q) prim(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
+          for (int q = 0; q < ppn; ++q) prim(rec[2 * q], rec[2 * q + 1]);
         } else {  // heavier classes, or more primitive pairs than staged: global memory
-          const float4* pp = a.prims_f32 + (size_t)s_ppo[r] * 4;
-          for (int q = 0; q < ppn; ++q) prim(pp[4 * q], pp[4 * q + 1], pp[4 * q + 2], pp[4 * q + 3]);
+          const float4* pp = a.prims_f32 + (size_t)s_ppo[r] * 2;
+          for (int q = 0; q < ppn; ++q) prim(pp[2 * q], pp[2 * q + 1]);
         }
         float xi[NA * NB];
         C::hrr(acc, s_ab[r][0].x, s_ab[r][1].x, s_ab[r][2].x, xi);
@@ -388,9 +430,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       // every lane is past its reads of the other buffer (the previous
       // iteration's closing __syncwarp), so it can take the next records
       if (STAGE) {
-        float4* nxt = s_pr[wid][(r + 1) & 1];
-        if (lane < n4n) nxt[lane] = pre0;
-        if (lane + 32 < n4n) nxt[lane + 32] = pre1;
+        if (lane < n2n) s_pr[wid][(r + 1) & 1][lane] = pre;
         __syncwarp();
       }
     }

@@ -115,7 +115,7 @@ struct snk_ctx {
   // geometry (device)
   DevBuf<int> l, poff, nprim, foff, fshell, bshell, bshell_col, xfunc;
   DevBuf<double> center, exps, d, fcomp, xyz, w, boys, bound, qbound, bcenter, bradius, phit_f, phit_b;
-  DevBuf<float> boys_f, boys_ds, prims_ds, pair_ab, prims_f32;  // mixed form: FP32 and (hi, lo) copies
+  DevBuf<float> boys_f, boys_ds, prims_ds, pair_ab, pair_a, prims_f32;  // mixed form: FP32 and (hi, lo) copies
   DevBuf<PairHdr> pairs;
   DevBuf<PrimPair> prims;
   DevBuf<MolDesc> mols;
@@ -146,6 +146,9 @@ struct snk_ctx {
   DevBuf<OzSplitJob> ozsplit;
   DevBuf<OzGemmJob> ozjobs;
   DevBuf<int> ozerr;
+  // tile screen of the FP32 lists: per-tile column sums, per-list executed work
+  DevBuf<float> tsum;
+  DevBuf<unsigned long long> exec;
   std::vector<int> hcounts;
   std::vector<long long> hpp;
   std::vector<int64_t> hlist_off;
@@ -160,6 +163,7 @@ struct snk_ctx {
     int ozs_off[2] = {0, 0}, ozs_n[2] = {0, 0}, ozs_rows[2] = {0, 0}, ozs_k[2] = {0, 0};
     int ozg_off[4] = {0, 0, 0, 0}, ozg_n[4] = {0, 0, 0, 0}, ozg_tiles[4] = {0, 0, 0, 0};
     int64_t arena_bytes = 0;
+    int max_tiles = 0;  // 128-point tiles of the chunk's largest batch (tile screen)
   };
   std::vector<Chunk> chunks;
   int max_ctas[kNumLists] = {0};
@@ -184,11 +188,11 @@ struct snk_ctx {
     f(l), f(poff), f(nprim), f(foff), f(fshell), f(bshell), f(bshell_col), f(xfunc);
     f(center), f(exps), f(d), f(fcomp), f(xyz), f(w), f(boys), f(bound), f(qbound), f(bcenter), f(bradius);
     f(phit_f), f(phit_b);
-    f(boys_f), f(boys_ds), f(prims_ds), f(pair_ab), f(prims_f32);
+    f(boys_f), f(boys_ds), f(prims_ds), f(pair_ab), f(pair_a), f(prims_f32);
     f(pairs), f(prims), f(mols), f(mlp_w), f(shell_feat), f(keep);
     f(P), f(Pscr), f(ft), f(sym), f(Khat), f(K), f(P2);
     f(counts), f(list), f(list2), f(sfunc), f(colmap), f(tickets), f(ppcounts), f(sflag), f(list_off), f(tstart);
-    f(batch), f(tiles), f(ws), f(ws32), f(arena), f(ozsplit), f(ozjobs), f(ozerr);
+    f(batch), f(tiles), f(ws), f(ws32), f(arena), f(ozsplit), f(ozjobs), f(ozerr), f(tsum), f(exec);
   }
   snk_ctx() {
     alloc.stream = &stream;
@@ -359,6 +363,12 @@ void set_max_ctas(snk_ctx* c) {
 }
 
 int check_device_flags(snk_ctx* c);
+
+// The tile screen runs for the FP32 lists of the mixed form when the products
+// leave X and the FP32 copy of F in place (gemm FP64 or SPLIT).
+bool tile_screen(const snk_ctx* c) {
+  return c->opt.precision == SNK_PREC_MIXED && c->opt.eps_tile > 0.0 && c->opt.gemm != SNK_GEMM_DF32;
+}
 
 // Split and product jobs of the tensor-core GEMMs (SNK_GEMM_SPLIT) for every
 // chunk: where each operand's slices go in the chunk's arena (the F phase and
@@ -629,6 +639,7 @@ int screen_and_plan(snk_ctx* c) {
   for (int k = 0; k < kNumClasses; ++k) class_flops(k, &per_prim[k], &per_pair[k]);
   double lint[kNumLists] = {0}, lflops[kNumLists] = {0}, gflops = 0.0, gflops_hi = 0.0, xbytes = 0.0;
   int64_t kept[2] = {0, 0}, pair_points = 0;
+  double listed32 = 0.0;
   for (int j = 0; j < nb; ++j) {
     gflops += 4.0 * c->n_dens * bd[j].q * (double)bd[j].nB * bd[j].nS;
     gflops_hi += 4.0 * c->n_dens * bd[j].q * (double)bd[j].nB * bd[j].nS_hi;
@@ -641,6 +652,7 @@ int screen_and_plan(snk_ctx* c) {
       lflops[k] += (npp * per_prim[cls] + n * per_pair[cls]) * bd[j].q;
       kept[k >= kNumClasses] += (int64_t)n;
       pair_points += (int64_t)n * bd[j].q;
+      if (k >= kNumClasses) listed32 += n * bd[j].q;
     }
   }
   SNK_CK(c, upload(c->colmap, hcolmap, st));
@@ -650,7 +662,7 @@ int screen_and_plan(snk_ctx* c) {
   // chunks under the workspace budget (Alg. 1): X, F, G in doubles, plus the
   // FP32 copies of F and G in the mixed form
   int j = 0;
-  int64_t need = 1, need32 = 1, need_arena = 0;
+  int64_t need = 1, need32 = 1, need_arena = 0, need_tsum = 1;
   const int nd = c->n_dens;
   // slice-arena bytes of one batch for the F phase (X_j and P[S_j, B_j] per
   // density, split by tier) and the K phase (X_j and G_j rows per density)
@@ -683,7 +695,7 @@ int screen_and_plan(snk_ctx* c) {
     ch.arena_bytes = std::max(af, ak);
     need_arena = std::max(need_arena, ch.arena_bytes);
     ch.b1 = j;
-    int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0;
+    int64_t xcur = 0, fcur = xo, gcur = xo + fo, f32cur = 0, scur = 0;
     ch.xn = xo;
     ch.goff = gcur;
     ch.gbytes = fo * 8;
@@ -694,6 +706,9 @@ int screen_and_plan(snk_ctx* c) {
       bd[t].foff = fcur;
       bd[t].goff = gcur;
       bd[t].foff32 = f32cur;
+      bd[t].ssoff = scur;
+      scur += (int64_t)(bd[t].ldq / kPointTile) * bd[t].nS;
+      ch.max_tiles = std::max(ch.max_tiles, bd[t].ldq / kPointTile);
       fcur += fs;
       gcur += fs;
       f32cur += fs;
@@ -704,12 +719,15 @@ int screen_and_plan(snk_ctx* c) {
     }
     ch.bytes = (xo + 2 * fo) * 8;
     need = std::max(need, xo + 2 * fo);
+    need_tsum = std::max(need_tsum, scur);
     if (mixed) need32 = std::max(need32, fo);
     c->chunks.push_back(ch);
   }
   SNK_CK(c, c->ws.ensure((size_t)need));
   if (mixed) SNK_CK(c, c->ws32.ensure((size_t)need32));
   SNK_CK(c, upload(c->batch, bd, st));
+  if (tile_screen(c)) SNK_CK(c, c->tsum.ensure((size_t)need_tsum));
+  SNK_CK(c, c->exec.ensure(2 * kNumLists));
   double tc_flops = 0.0;
   if (tc) {
     if (int rc = plan_tc(c, &tc_flops)) return rc;
@@ -743,6 +761,8 @@ int screen_and_plan(snk_ctx* c) {
   S.gemm_flops_hi = gflops_hi;
   S.colloc_bytes = xbytes;
   S.gemm_tc_flops = tc_flops;
+  S.pair_points_fp32_listed = listed32;
+  S.pair_points_fp32 = listed32;
   S.n_chunks = (int64_t)c->chunks.size();
   S.workspace_bytes = (int64_t)(c->ws.n * 8 + c->ws32.n * 4);
   float ms = 0.f;
@@ -789,7 +809,12 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.prims_ds = reinterpret_cast<const float2*>(c->prims_ds.p);
   a.pair_ab = reinterpret_cast<const float2*>(c->pair_ab.p);
   a.prims_f32 = reinterpret_cast<const float4*>(c->prims_f32.p);
+  a.pair_a = reinterpret_cast<const float2*>(c->pair_a.p);
   a.hi_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals) ? 1 : 0;
+  a.tsum = c->tsum.p;
+  a.pbound = c->bound.p;
+  a.eps_tile = (k >= kNumClasses && tile_screen(c)) ? (float)c->opt.eps_tile : 0.f;
+  a.exec = c->exec.p + 2 * k;
   a.n_dens = c->n_dens;
   return a;
 }
@@ -842,6 +867,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     ++c->launches_build;
   }
   SNK_CK(c, cudaMemsetAsync(c->tickets.p, 0, sizeof(int) * c->tickets.n, st));
+  SNK_CK(c, cudaMemsetAsync(c->exec.p, 0, sizeof(unsigned long long) * c->exec.n, st));
   for (size_t ci = 0; ci < c->chunks.size(); ++ci) {
     const auto& ch = c->chunks[ci];
     const int nbc = ch.b1 - ch.b0;
@@ -871,6 +897,10 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     }
     SNK_CK(c, mark());
     if (tc) SNK_CK(c, oz_gemm(ch, 1));
+    if (tile_screen(c)) {  // per-tile column sums of the tile screen, from X and the FP32 F
+      SNK_CK(c, launch_tile_sums(st, db, nbc, ch.max_tiles, c->ws.p, c->ws32.p, nd, c->tsum.p));
+      ++c->launches_build;
+    }
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
     SNK_CK(c, mark());
     // G_j, Eq. (gmat) with the 3c-CP integrals of App. A, list by list
@@ -1007,6 +1037,24 @@ void collect_times(snk_ctx* c) {
   }
   st.ms_finish = el(ev, ev + 1);
   st.ms_build = el(0, ev + 1);
+  // the FP32 lists' work as computed (after the tile screen)
+  unsigned long long hx[2 * kNumLists];
+  if (c->exec.p && cudaMemcpy(hx, c->exec.p, sizeof(hx), cudaMemcpyDeviceToHost) == cudaSuccess) {
+    double pp = 0.0, fl = 0.0, in = 0.0;
+    for (int k = kNumClasses; k < kNumLists; ++k) {
+      double per_prim, per_pair;
+      const int cls = k - kNumClasses;
+      class_flops(cls, &per_prim, &per_pair);
+      const int la = cls >= 3 ? 2 : (cls >= 1 ? 1 : 0), lb = cls - la * (la + 1) / 2;
+      fl += (double)hx[2 * k] * per_prim + (double)hx[2 * k + 1] * per_pair;
+      in += (double)hx[2 * k + 1] * ncart(la) * ncart(lb);
+      pp += (double)hx[2 * k + 1];
+    }
+    st.pair_points_fp32 = pp;
+    st.flops_fp32 = fl;
+    st.integrals += in - st.integrals_fp32;
+    st.integrals_fp32 = in;
+  }
 }
 
 // Autotuner: for every integral list, time the list's kernel on the last
@@ -1085,7 +1133,7 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   if (c->opt.screen < 0 || c->opt.screen > 2 || c->opt.precision < 0 || c->opt.precision > 1) return SNK_ERR_INVALID_ARG;
   if (c->opt.gemm < 0 || c->opt.gemm > 2 || c->opt.ds_integrals < 0 || c->opt.ds_integrals > 1 ||
       c->opt.tc_slices_hi < 3 || c->opt.tc_slices_hi > 6 ||
-      c->opt.tc_slices_lo < 3 || c->opt.tc_slices_lo > 6)
+      c->opt.tc_slices_lo < 3 || c->opt.tc_slices_lo > 6 || !(c->opt.eps_tile >= 0.0))
     return SNK_ERR_INVALID_ARG;
   for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
   int rc = build_setup(n_mol, bases, grids, &c->opt, &c->s, &c->err);
@@ -1159,16 +1207,21 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
          SNK_CK(cp, upload(cp->bradius, s.bradius, st));
          SNK_CK(cp, upload(cp->boys_f, s.boys_f, st));
          if (cp->opt.precision == SNK_PREC_MIXED) {
-           std::vector<float> pab(s.pairs.size() * 8, 0.0f);
+           std::vector<float> pab(s.pairs.size() * 8, 0.0f), pa(s.pairs.size() * 8, 0.0f);
            for (size_t q = 0; q < s.pairs.size(); ++q) {
              const double v[3] = {s.pairs[q].ABx, s.pairs[q].ABy, s.pairs[q].ABz};
+             const double* A = &s.center[3 * (size_t)s.pairs[q].sa];
              for (int m = 0; m < 3; ++m) {
                const float hh = (float)v[m];
                pab[q * 8 + 2 * m] = hh;
                pab[q * 8 + 2 * m + 1] = (float)(v[m] - (double)hh);
+               const float ah = (float)A[m];
+               pa[q * 8 + 2 * m] = ah;
+               pa[q * 8 + 2 * m + 1] = (float)(A[m] - (double)ah);
              }
            }
            SNK_CK(cp, upload(cp->pair_ab, pab, st));
+           SNK_CK(cp, upload(cp->pair_a, pa, st));
            std::vector<float> pds(s.prims.size() * 24);
            for (size_t q = 0; q < s.prims.size(); ++q) {
              const double* v = reinterpret_cast<const double*>(&s.prims[q]);
@@ -1179,24 +1232,17 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
              }
            }
            SNK_CK(cp, upload(cp->prims_ds, pds, st));
-           std::vector<float> pf(s.prims.size() * 16, 0.0f);
+           std::vector<float> pf(s.prims.size() * 8, 0.0f);
            for (size_t q = 0; q < s.prims.size(); ++q) {
              const PrimPair& P = s.prims[q];
-             float* r = &pf[q * 16];
-             const double c3[3] = {P.Px, P.Py, P.Pz};
+             float* r = &pf[q * 8];
              r[0] = (float)P.zeta;
-             for (int m = 0; m < 3; ++m) {
-               r[1 + m] = (float)c3[m];
-               r[4 + m] = (float)(c3[m] - (double)r[1 + m]);
-             }
-             r[7] = (float)P.pref;
-             r[8] = (float)P.PAx;
-             r[9] = (float)P.PAy;
-             r[10] = (float)P.PAz;
-             r[11] = (float)P.pref_far;
-             r[12] = (float)P.k1;
-             r[13] = (float)P.k2;
-             r[14] = (float)P.k3;
+             r[1] = (float)P.PAx;
+             r[2] = (float)P.PAy;
+             r[3] = (float)P.PAz;
+             r[4] = (float)P.pref;
+             r[5] = (float)P.pref_far;
+             r[6] = (float)P.k1;
            }
            SNK_CK(cp, upload(cp->prims_f32, pf, st));
            SNK_CK(cp, upload(cp->boys_ds, s.boys_ds, st));
@@ -1247,6 +1293,7 @@ void snk_options_default(snk_options* o) {
   o->learned_skip = -11.0;
   o->tc_slices_hi = 5;
   o->tc_slices_lo = 4;
+  o->eps_tile = 0.0;
 }
 
 const char* snk_status_string(int status) {

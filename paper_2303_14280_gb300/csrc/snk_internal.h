@@ -88,7 +88,7 @@ struct BatchDesc {
   int32_t bshell_off;
   int32_t nBshell;
   int64_t foff32;    // mixed form: offset (floats) of the FP32 copy of F
-  int64_t pad64_;
+  int64_t ssoff;     // tile screen: offset (floats) of the batch's per-tile column sums
   int32_t mol;       // molecule of the batch, its first shell and function, N_b,m
   int32_t ms0;
   int32_t mf0;
@@ -261,11 +261,19 @@ struct IntegralArgs {
   const float2* boys_ds;   // (hi, lo) Boys table, nodes rounded to ds values
   const float2* prims_ds;  // 12 (hi, lo) pairs per primitive pair, PrimPair order
   const float2* pair_ab;   // 4 per shell pair: R_a - R_b as 3 (hi, lo) pairs, padding
-  // FP32 record per primitive pair: {zeta, Px_hi, Py_hi, Pz_hi}, {Px_lo, Py_lo,
-  // Pz_lo, pref}, {PAx, PAy, PAz, pref_far}, {k1, k2, k3, 0}
+  // FP32 record per primitive pair (32 bytes): {zeta, PAx, PAy, PAz}, {pref, pref_far, 1/(2 zeta), 0}
   const float4* prims_f32;
+  const float2* pair_a;    // 4 per shell pair: R_a as 3 (hi, lo) pairs, padding
   int hi_ds;
   int n_dens;      // densities: F and G of density d at foff / goff (F32: foff32) + d ldq nS
+  // tile screen of the FP32 lists (eps_tile > 0): a pair is skipped on a
+  // 128-point tile when bound_ab x max(sum over b's columns, sum over a's
+  // columns) of tsum is below eps_tile; tsum[ssoff + tile nS + col] =
+  // sum_{i in tile} |F_col(i)| max_nu |X_nu(i)|
+  const float* tsum;
+  const double* pbound;  // rigorous max_r |A_ab(r)| per shell pair
+  float eps_tile;
+  unsigned long long* exec;  // FP32 lists: += (primitive pairs x points, pairs x points) computed
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
@@ -352,5 +360,9 @@ cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbat
                                   long long* ppcounts, const float* shell_feat, float skip_log10, float fp32_log10,
                                   unsigned char* keep, unsigned char* hflag);
 cudaError_t launch_xmax(cudaStream_t st, const BatchDesc* dbatch, int nbatch, const double* ws, double* xm);
+// Per-tile column sums of the tile screen: for every batch, 128-point tile and
+// F column, sum_i |F32_col(i)| max_nu |X_nu(i)| (summed over the densities).
+cudaError_t launch_tile_sums(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_tiles, const double* ws,
+                             const float* ws32, int n_dens, float* tsum);
 
 }  // namespace snk

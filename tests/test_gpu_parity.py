@@ -297,6 +297,27 @@ def test_split_gemms(snk):
     assert np.max(np.abs(K0 - Kref)) <= TOL_K
 
 
+def test_tile_screen(snk):
+    """The per-tile screen of the FP32 lists skips (tile, pair) blocks whose
+    bound on the tile's points is below eps_tile; at 1e-13 the mixed form
+    stays within its 1e-8 target, with fewer (pair, point) evaluations."""
+    p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
+    Kref = oracle.snk_K(p.basis, p.grid, p.P)
+    form = dict(batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="split")
+    K0, s0 = _gpu_K(snk, p, **form)
+    K1, s1 = _gpu_K(snk, p, eps_tile=1e-13, **form)
+    assert s0["pair_points_fp32"] == s0["pair_points_fp32_listed"] > 0
+    assert 0 < s1["pair_points_fp32"] < s1["pair_points_fp32_listed"] == s0["pair_points_fp32_listed"]
+    assert s1["flops_fp32"] < s0["flops_fp32"]
+    assert np.max(np.abs(K1 - Kref)) <= 1e-8 and np.max(np.abs(K1 - K0)) <= 1e-9
+    assert np.max(np.abs(K1 - K1.T)) == 0.0
+    # an enormous threshold skips every FP32 block: only the high tier remains
+    K2, s2 = _gpu_K(snk, p, eps_tile=1e300, **form)
+    assert s2["pair_points_fp32"] == 0 and np.all(np.isfinite(K2))
+    with pytest.raises(snk.SnkError):
+        snk.Engine(p.basis, p.grid, eps_tile=-1.0, **form)
+
+
 def test_fp32_tier_run_to_run(snk):
     """The FP32 pairs add into the FP64 G with FP64 atomics, so repeated
     builds of the mixed form differ only by FP64 summation order."""
