@@ -79,7 +79,7 @@ BF16_MEASURED = _measured_peaks().get("bf16_tflops")
 BF16_PEAK = float(BF16_MEASURED or 1900.0)
 PLAIN = dict()
 CHOSEN = dict(eps=1e-10, precision="mixed", fp32_bound=3e-4, gemm="split", tc_slices_hi=5, tc_slices_lo=4,
-              ds_integrals=1)
+              ds_integrals=1, eps_tile=1e-11)
 GOLDEN = {n: os.path.join(ROOT, "tests", "golden", f"{n}_K_entries.txt")
           for n in ("cluster96", "cluster256", "cluster512")}
 # workloads whose plain FP64 build is too slow to repeat beside the chosen
@@ -494,8 +494,9 @@ def main():
         form = ("mixed: rigorous sn-LinK at 1e-10, FP32 integrals for pairs with estimate < 3e-4, double-FP32 "
                 "integrals otherwise; F = X P and Kt = G^T X on the tcgen05 tensor cores as sums of bf16 "
                 "fixed-point slice products (5 slices for the columns / rows of shells in double-FP32 pairs, 4 "
-                "for the rest, exact FP32 accumulation per 256-term run, double-FP32 run sums); FP64 G and K "
-                "accumulation")
+                "for the rest, exact FP32 accumulation per 256-term run, double-FP32 run sums); FP32 blocks "
+                "screened again per 128-point tile at 1e-11 (tile skipped, or its primitive-pair tail trimmed); "
+                "FP64 G and K accumulation")
         if chosen_opts["gemm"] != "split":
             form = form.replace("on the tcgen05 tensor cores", f"with gemm={chosen_opts['gemm']} instead of")
         if not args.no_learned and os.path.exists(snk.SCREEN_WEIGHTS):

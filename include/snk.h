@@ -148,8 +148,11 @@ typedef struct {
                               max(sum_i |F_b(i)| max|Phi(i)|, the same with a)
                               over the tile's points -- a bound of what the
                               tile adds to any K-tilde entry, up to the
-                              component factors -- is below eps_tile; 0 = off
-                              (default)                                         */
+                              component factors -- is below eps_tile; on the
+                              tiles kept, the pair's primitive pairs (stored
+                              largest bound first) whose bounds on the tile
+                              add up to less than eps_tile are left out;
+                              0 = off (default)                                 */
   double reserved[3];
 } snk_options;
 

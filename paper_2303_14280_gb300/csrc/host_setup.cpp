@@ -326,6 +326,7 @@ int build_setup_one(const snk_basis* basis, const snk_grid* grid, const snk_opti
       for (int q : ord) {
         sorted_keep.push_back(keep[q]);
         if (kb[q] >= kPrimPairRelTolF32 * kb[ord[0]]) ++n32;
+        s->prim_rel.push_back(kb[q] / bnd);  // the primitive pair's share of the pair's bound
       }
       keep.swap(sorted_keep);
       PairHdr h;
@@ -572,6 +573,7 @@ int build_setup(int n_mol, const snk_basis* bases, const snk_grid* grids, const 
       s->pairs.push_back(h);
     }
     s->prims.insert(s->prims.end(), one.prims.begin(), one.prims.end());
+    s->prim_rel.insert(s->prim_rel.end(), one.prim_rel.begin(), one.prim_rel.end());
     s->bound.insert(s->bound.end(), one.bound.begin(), one.bound.end());
     s->qbound.insert(s->qbound.end(), one.qbound.begin(), one.qbound.end());
     s->pair_class.insert(s->pair_class.end(), one.pair_class.begin(), one.pair_class.end());

@@ -325,10 +325,12 @@ __global__ void xmax_kernel(const BatchDesc* __restrict__ batches, const double*
 
 // Tile screen sums: one block per (tile of 128 points, batch).  The points'
 // max |X| first (integer max of the IEEE bit patterns: no FP64 arithmetic),
-// then per F column the warp-reduced sum over the tile of |F32| max |X|.
+// then per F column the warp-reduced sum over the tile of |F32| max |X|; the
+// row ends with the tile's bounding sphere (centre, radius), 4 floats.
 __global__ void __launch_bounds__(256) tile_sums_kernel(const BatchDesc* __restrict__ batches,
                                                         const double* __restrict__ ws, const float* __restrict__ ws32,
-                                                        int n_dens, float* __restrict__ tsum) {
+                                                        const double* __restrict__ xyz, int n_dens,
+                                                        float* __restrict__ tsum) {
   const BatchDesc bd = batches[blockIdx.y];
   const int tile = blockIdx.x, i0 = tile * kPointTile;
   if (i0 >= bd.q) return;
@@ -346,7 +348,41 @@ __global__ void __launch_bounds__(256) tile_sums_kernel(const BatchDesc* __restr
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* out = tsum + bd.ssoff + (int64_t)tile * bd.nS;
+  float* out = tsum + bd.ssoff + (int64_t)tile * (bd.nS + 4);
+  if (warp == 0) {  // bounding sphere of the tile: box centre, largest distance
+    const int n = min(kPointTile, bd.q - i0);
+    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
+    for (int t = lane; t < n; t += 32)
+      for (int q = 0; q < 3; ++q) {
+        const float v = (float)xyz[3 * (bd.p0 + i0 + t) + q];
+        mn[q] = fminf(mn[q], v);
+        mx[q] = fmaxf(mx[q], v);
+      }
+    float cen[3];
+    for (int q = 0; q < 3; ++q) {
+      for (int o = 16; o > 0; o >>= 1) {
+        mn[q] = fminf(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
+        mx[q] = fmaxf(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+      }
+      cen[q] = 0.5f * (mn[q] + mx[q]);
+    }
+    float r2 = 0.f;
+    for (int t = lane; t < n; t += 32) {
+      float d2 = 0.f;
+      for (int q = 0; q < 3; ++q) {
+        const float dv = (float)xyz[3 * (bd.p0 + i0 + t) + q] - cen[q];
+        d2 = fmaf(dv, dv, d2);
+      }
+      r2 = fmaxf(r2, d2);
+    }
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if (lane == 0) {
+      out[bd.nS] = cen[0];
+      out[bd.nS + 1] = cen[1];
+      out[bd.nS + 2] = cen[2];
+      out[bd.nS + 3] = sqrtf(r2) * 1.0001f + 1e-6f;  // covers the float rounding of the points
+    }
+  }
   const int64_t dstr = (int64_t)bd.ldq * bd.nS;
   for (int c = warp; c < bd.nS; c += blockDim.x / 32) {
     float s = 0.f;
@@ -682,9 +718,9 @@ cudaError_t launch_screen_geom(cudaStream_t st, const BatchDesc* dbatch, int nba
 }
 
 cudaError_t launch_tile_sums(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_tiles, const double* ws,
-                             const float* ws32, int n_dens, float* tsum) {
+                             const float* ws32, const double* xyz, int n_dens, float* tsum) {
   if (nbatch == 0 || max_tiles == 0) return cudaSuccess;
-  tile_sums_kernel<<<dim3(max_tiles, nbatch), 256, 0, st>>>(dbatch, ws, ws32, n_dens, tsum);
+  tile_sums_kernel<<<dim3(max_tiles, nbatch), 256, 0, st>>>(dbatch, ws, ws32, xyz, n_dens, tsum);
   return cudaGetLastError();
 }
 

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
     int nrun;
     {
       const int r = threadIdx.x, n = tile.k1 - tile.k0;  // n <= kMaxRun = blockDim
-      int p = 0, ca = 0, cb = 0;
+      int p = 0, ca = 0, cb = 0, npp_keep = 0;
       PairHdr h{};
       bool keep = r < n;
       if (keep) {
@@ -273,14 +273,42 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         h = a.pairs[p];
         ca = cmap[h.sa];
         cb = cmap[h.sb];
+        npp_keep = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
         if (a.eps_tile > 0.f) {
-          const float* ts = a.tsum + bd.ssoff + (int64_t)(tile.i0 / kPointTile) * bd.nS;
+          const float* ts = a.tsum + bd.ssoff + (int64_t)(tile.i0 / kPointTile) * (bd.nS + 4);
           float sa = 0.f, sb = 0.f;
 #pragma unroll
           for (int u = 0; u < NA; ++u) sa += ts[ca + u];
 #pragma unroll
           for (int v = 0; v < NB; ++v) sb += ts[cb + v];
-          keep = (float)a.pbound[p] * fmaxf(sa, sb) >= a.eps_tile;
+          // |A_ab| <= min(global bound, total charge / distance) on the tile's sphere
+          const double* A = a.shell_xyz + 3 * h.sa;
+          const float vx = (float)-h.ABx, vy = (float)-h.ABy, vz = (float)-h.ABz;  // B - A
+          const float wx = ts[bd.nS] - (float)A[0], wy = ts[bd.nS + 1] - (float)A[1],
+                      wz = ts[bd.nS + 2] - (float)A[2];
+          const float vv = vx * vx + vy * vy + vz * vz;
+          float tt = vv > 0.f ? (wx * vx + wy * vy + wz * vz) / vv : 0.f;
+          tt = fminf(fmaxf(tt, 0.f), 1.f);
+          const float dx = wx - tt * vx, dy = wy - tt * vy, dz = wz - tt * vz;
+          const float d = sqrtf(dx * dx + dy * dy + dz * dz) - ts[bd.nS + 3] - 1e-4f;
+          const float glob = (float)a.pbound[p], smax = fmaxf(sa, sb);
+          float bnd = glob;
+          if (d > 0.f) bnd = fminf(bnd, (float)a.qbound[p] / d);
+          keep = bnd * smax >= a.eps_tile;
+          if (keep) {
+            // primitive pairs come largest bound first: leave out the tail whose
+            // bounds on this tile add up to less than eps_tile
+            const float4* rec = a.prims_f32 + (size_t)h.pp_off * 2;
+            float tail = 0.f;
+            int n = h.pp_n32;
+            while (n > 1) {
+              const float t2 = tail + rec[2 * (n - 1) + 1].w * glob * smax;
+              if (t2 >= a.eps_tile) break;
+              tail = t2;
+              --n;
+            }
+            npp_keep = n;
+          }
         }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -296,7 +324,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
       if (keep) {
         const int q = before + __popc(bal & ((1u << lane) - 1u));
         s_ppo[q] = h.pp_off;
-        s_ppn[q] = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
+        s_ppn[q] = npp_keep;
         s_sa[q] = h.sa;
         s_sb[q] = h.sb;
         s_ca[q] = ca;

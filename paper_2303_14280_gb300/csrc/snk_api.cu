@@ -707,7 +707,7 @@ int screen_and_plan(snk_ctx* c) {
       bd[t].goff = gcur;
       bd[t].foff32 = f32cur;
       bd[t].ssoff = scur;
-      scur += (int64_t)(bd[t].ldq / kPointTile) * bd[t].nS;
+      scur += (int64_t)(bd[t].ldq / kPointTile) * (bd[t].nS + 4);
       ch.max_tiles = std::max(ch.max_tiles, bd[t].ldq / kPointTile);
       fcur += fs;
       gcur += fs;
@@ -813,6 +813,8 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.hi_ds = (c->opt.precision == SNK_PREC_MIXED && c->opt.ds_integrals) ? 1 : 0;
   a.tsum = c->tsum.p;
   a.pbound = c->bound.p;
+  a.qbound = c->qbound.p;
+  a.shell_xyz = c->center.p;
   a.eps_tile = (k >= kNumClasses && tile_screen(c)) ? (float)c->opt.eps_tile : 0.f;
   a.exec = c->exec.p + 2 * k;
   a.n_dens = c->n_dens;
@@ -898,7 +900,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     SNK_CK(c, mark());
     if (tc) SNK_CK(c, oz_gemm(ch, 1));
     if (tile_screen(c)) {  // per-tile column sums of the tile screen, from X and the FP32 F
-      SNK_CK(c, launch_tile_sums(st, db, nbc, ch.max_tiles, c->ws.p, c->ws32.p, nd, c->tsum.p));
+      SNK_CK(c, launch_tile_sums(st, db, nbc, ch.max_tiles, c->ws.p, c->ws32.p, c->xyz.p, nd, c->tsum.p));
       ++c->launches_build;
     }
     SNK_CK(c, cudaMemsetAsync(c->ws.p + ch.goff, 0, ch.gbytes, st));
@@ -1243,6 +1245,7 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
              r[4] = (float)P.pref;
              r[5] = (float)P.pref_far;
              r[6] = (float)P.k1;
+             r[7] = (float)s.prim_rel[q];
            }
            SNK_CK(cp, upload(cp->prims_f32, pf, st));
            SNK_CK(cp, upload(cp->boys_ds, s.boys_ds, st));

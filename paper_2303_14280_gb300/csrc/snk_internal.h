@@ -143,6 +143,7 @@ struct Setup {
   // shell pairs sorted by class, then a, then b
   std::vector<PairHdr> pairs;
   std::vector<PrimPair> prims;
+  std::vector<double> prim_rel;       // per primitive pair: its bound / its shell pair's bound
   std::vector<double> bound;          // rigorous max_r |A| per pair
   std::vector<double> qbound;         // rigorous total |charge| per pair: |A| <= qbound / distance
   std::vector<int> pair_class;
@@ -261,17 +262,22 @@ struct IntegralArgs {
   const float2* boys_ds;   // (hi, lo) Boys table, nodes rounded to ds values
   const float2* prims_ds;  // 12 (hi, lo) pairs per primitive pair, PrimPair order
   const float2* pair_ab;   // 4 per shell pair: R_a - R_b as 3 (hi, lo) pairs, padding
-  // FP32 record per primitive pair (32 bytes): {zeta, PAx, PAy, PAz}, {pref, pref_far, 1/(2 zeta), 0}
+  // FP32 record per primitive pair (32 bytes): {zeta, PAx, PAy, PAz}, {pref, pref_far, 1/(2 zeta),
+  // its bound / the shell pair's bound}
   const float4* prims_f32;
   const float2* pair_a;    // 4 per shell pair: R_a as 3 (hi, lo) pairs, padding
   int hi_ds;
   int n_dens;      // densities: F and G of density d at foff / goff (F32: foff32) + d ldq nS
   // tile screen of the FP32 lists (eps_tile > 0): a pair is skipped on a
   // 128-point tile when bound_ab x max(sum over b's columns, sum over a's
-  // columns) of tsum is below eps_tile; tsum[ssoff + tile nS + col] =
-  // sum_{i in tile} |F_col(i)| max_nu |X_nu(i)|
+  // columns) of tsum is below eps_tile; tsum[ssoff + tile (nS + 4) + col] =
+  // sum_{i in tile} |F_col(i)| max_nu |X_nu(i)|, then the tile's centre and
+  // radius; bound_ab = min(pbound, qbound / distance from the segment AB to
+  // the tile's sphere)
   const float* tsum;
   const double* pbound;  // rigorous max_r |A_ab(r)| per shell pair
+  const double* qbound;  // rigorous total |charge| per shell pair
+  const double* shell_xyz;
   float eps_tile;
   unsigned long long* exec;  // FP32 lists: += (primitive pairs x points, pairs x points) computed
 };
@@ -363,6 +369,6 @@ cudaError_t launch_xmax(cudaStream_t st, const BatchDesc* dbatch, int nbatch, co
 // Per-tile column sums of the tile screen: for every batch, 128-point tile and
 // F column, sum_i |F32_col(i)| max_nu |X_nu(i)| (summed over the densities).
 cudaError_t launch_tile_sums(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_tiles, const double* ws,
-                             const float* ws32, int n_dens, float* tsum);
+                             const float* ws32, const double* xyz, int n_dens, float* tsum);
 
 }  // namespace snk
