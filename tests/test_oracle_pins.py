@@ -321,6 +321,37 @@ def test_entries_mode_matches_full_build(chain4):
 
 
 @pytest.mark.slow
+def test_blocked_entries_mode_matches_full_build(chain4):
+    """The blocked entries mode (F = Phi P as a library matrix product per
+    block of points, the wanted G rows by the oracle) reproduces the full
+    build's entries, across blocks of ragged size."""
+    p = chain4
+    K = oracle.snk_K(p.basis, p.grid, p.P)
+    mu = np.array([0, 3, 10, 33, 17, 5, 20])
+    nu = np.array([0, 7, 2, 33, 30, 5, 11])
+    vals = oracle.snk_K_entries_blocked(p.basis, p.grid, p.P, mu, nu, block=997)
+    assert np.max(np.abs(vals - K[mu, nu])) <= 1e-15 * max(1.0, np.max(np.abs(K)))
+
+
+def test_becke_partition_c_matches_tensor_form():
+    """The fused C Becke partition of synth (CPU grids) agrees with the tensor
+    form of the same definition, and the cell weights of each point sum to 1."""
+    import torch  # noqa: F401  (the tensor form runs as torch operations)
+    mol = synth.make_cluster_molecule(24, 124)
+    r, _ = synth.mk_radial(20)
+    dirs, _ = synth.angular_product(4, 9)
+    xyz = np.concatenate([(r[:, None, None] * dirs[None]).reshape(-1, 3) + mol.xyz[a] for a in range(24)])
+    own = np.repeat(np.arange(24, dtype=np.int32), r.shape[0] * dirs.shape[0])
+    sel = np.random.default_rng(0).choice(xyz.shape[0], 3000, replace=False)
+    wc = synth.becke_weights(xyz[sel], own[sel], mol.xyz)
+    wt = synth.becke_weights(xyz[sel], own[sel], mol.xyz, device="cpu")
+    assert np.max(np.abs(wc - wt)) <= 1e-13
+    # partition of unity: the weights of one point for every atom add to 1
+    pts = xyz[sel[:50]]
+    tot = sum(synth.becke_weights(pts, np.full(50, a, dtype=np.int32), mol.xyz) for a in range(24))
+    assert np.max(np.abs(tot - 1.0)) <= 1e-12
+
+
 def test_grid_refinement_converges_to_eri_K():
     """Brute force: sn-K approaches the four-centre-ERI exchange as the grid is refined
     (two atoms, s/p/d shells, two occupied orbitals)."""
