@@ -324,20 +324,34 @@ int ensure_events(snk_ctx* c, size_t n) {
 // Integral tiles (batch, run of pairs, 128-point slab) of every list of every
 // chunk, written on the device: the host only computes where each (batch,
 // list)'s tiles start (from the per-list counts it already holds), and
-// gen_tiles writes them.  Within a (chunk, list) the tiles go batch by batch,
-// a run's slabs consecutively; the persistent CTAs take them from a ticket.
+// gen_tiles writes them.  Within a (chunk, list) the batches go in
+// descending order of their work -- primitive pairs x points, the cost
+// measure W_j of Eq. (work_heuristic) extended by the list's pair counts --
+// so that the persistent CTAs, which take tiles from a ticket in order, start
+// on the largest batches and finish on the smallest (longest processing time
+// first); a run's slabs stay consecutive.
 int make_tiles(snk_ctx* c, cudaStream_t st) {
   const auto& bd = c->hbatch;
   const int nb = c->nbatch;
   std::vector<int64_t> tstart((size_t)std::max(nb, 1) * kNumLists, 0);
   int64_t tot = 0;
+  std::vector<int> order;
+  std::vector<double> cost;
   for (auto& ch : c->chunks)
     for (int k = 0; k < kNumLists; ++k) {
       ch.tile_off[k] = tot;
       const int run = c->run[k];
       if (run < 1 || run > 128)  // the FP32 kernel stages at most 128 pairs per tile
         return fail(c, SNK_ERR_INVALID_ARG, "pairs per tile outside 1..128");
+      order.resize(ch.b1 - ch.b0);
+      cost.resize(ch.b1 - ch.b0);
       for (int t = ch.b0; t < ch.b1; ++t) {
+        order[t - ch.b0] = t;
+        cost[t - ch.b0] = (double)c->hpp[(size_t)t * kNumLists + k] * bd[t].q;
+      }
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return cost[x - ch.b0] > cost[y - ch.b0]; });
+      for (int t : order) {
         const int64_t n = c->hcounts[(size_t)t * kNumLists + k];
         tstart[(size_t)t * kNumLists + k] = tot;
         tot += (n + run - 1) / run * ((bd[t].q + kPointTile - 1) / kPointTile);
