@@ -50,18 +50,18 @@ constexpr int TM = 64, TN = 64, TK = 16, GEMM_THREADS = 256;
 
 // C[m][n] = sum_k A(m,k) B(k,n) for the 64 x 64 tile at (m0, n0), K = kdim.
 // la(m, k), lb(k, n) return 0 outside the operands; st(m, n, c) stores.
-template <class LA, class LB, class ST>
+template <class T = double, class LA, class LB, class ST>
 __device__ __forceinline__ void gemm_tile(int m0, int n0, int mdim, int ndim, int kdim, LA la, LB lb,
                                           ST st, bool a_k_fast, bool b_k_fast) {
-  __shared__ double As[TK][TM + 1];
-  __shared__ double Bs[TK][TN + 1];
+  __shared__ T As[TK][TM + 1];
+  __shared__ T Bs[TK][TN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
   for (int k0 = 0; k0 < kdim; k0 += TK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ void gemm_tile(int m0, int n0, int mdim, int ndim, in
         kk = e / TM;
       }
       int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < mdim && k < kdim) ? la(m, k) : 0.0;
+      As[kk][mm] = (m < mdim && k < kdim) ? T(la(m, k)) : T(0);
       int nn;
       if (b_k_fast) {
         kk = e % TK;
@@ -86,12 +86,12 @@ __device__ __forceinline__ void gemm_tile(int m0, int n0, int mdim, int ndim, in
       }
       int n = n0 + nn;
       k = k0 + kk;
-      Bs[kk][nn] = (n < ndim && k < kdim) ? lb(k, n) : 0.0;
+      Bs[kk][nn] = (n < ndim && k < kdim) ? T(lb(k, n)) : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         a[q] = As[kk][ty + 16 * q];
@@ -400,8 +400,8 @@ __global__ void __launch_bounds__(256) tile_sums_kernel(const BatchDesc* __restr
 // ---------------------------------------------------------------- F-tilde
 
 // For molecule blockIdx.z: F-tilde_a^(j) = max_{mu in a} sum_nu |P_{mu nu}|
-// Phi-tilde_nu^(j) over its functions mu and batches j, a GEMM whose store takes
-// the shell maximum.  The molecule's batch rows are consecutive (stride N_b,m
+// Phi-tilde_nu^(j) over its functions mu and batches j, a GEMM (FP32 tiles,
+// rounded up: an upper bound) whose store takes the shell maximum.  The molecule's batch rows are consecutive (stride N_b,m
 // in Phi-tilde, N_shell,m in F-tilde).
 __global__ void __launch_bounds__(GEMM_THREADS) ftilde_kernel(const MolDesc* __restrict__ mols,
                                                               const BatchDesc* __restrict__ batches,
@@ -416,11 +416,13 @@ __global__ void __launch_bounds__(GEMM_THREADS) ftilde_kernel(const MolDesc* __r
   const BatchDesc b0 = batches[md.mb0];
   const double* ph = phit_f + b0.phf_off;
   double* ft = ft_shell + b0.cm_off;
-  gemm_tile(
-      m0, n0, md.nf, md.nb, md.nf, [&](int m, int k) { return fabs(Pm[(int64_t)m * md.nf + k]); },
-      [&](int k, int n) { return ph[(int64_t)n * md.nf + k]; },
-      [&](int m, int n, double c) {
-        atomic_max_nonneg(&ft[(int64_t)n * md.ns + (fshell[md.mf0 + m] - md.ms0)], c);
+  // a screening estimate: FP32 sums of non-negative terms (relative error
+  // below k 2^-24 <= 3e-4 for k <= 5,000 terms), rounded up by 1e-3
+  gemm_tile<float>(
+      m0, n0, md.nf, md.nb, md.nf, [&](int m, int k) { return (float)fabs(Pm[(int64_t)m * md.nf + k]); },
+      [&](int k, int n) { return (float)ph[(int64_t)n * md.nf + k]; },
+      [&](int m, int n, float c) {
+        atomic_max_nonneg(&ft[(int64_t)n * md.ns + (fshell[md.mf0 + m] - md.ms0)], (double)c * (1.0 + 1e-3));
       },
       true, true);
 }
@@ -432,32 +434,38 @@ constexpr int SCR_THREADS = 256;
 // Bound of max_{r in Q_j} |A_ab(r)| for batch j: the global bound A-tilde, or,
 // when the batch's bounding sphere stays clear of the segment AB that holds
 // every Gaussian product centre, the smaller total-charge / distance bound.
-__device__ __forceinline__ double batch_pair_bound(const ScreenArgs& a, int j, int p, const PairHdr& h) {
-  const double bnd = a.bound[p];
+// In FP32 (the FP64 pipe issues at 1/64 of it) with the distance rounded down
+// and the charge rounded up, so the result stays an upper bound.
+__device__ __forceinline__ float batch_pair_bound(const ScreenArgs& a, int j, int p, const PairHdr& h) {
+  const float bnd = (float)a.bound[p] * (1.0f + 1e-6f);
   if (!a.distance) return bnd;
   const double* A = a.shell_xyz + 3 * h.sa;
-  const double vx = -h.ABx, vy = -h.ABy, vz = -h.ABz;  // B - A
-  const double wx = a.bcenter[3 * j] - A[0], wy = a.bcenter[3 * j + 1] - A[1], wz = a.bcenter[3 * j + 2] - A[2];
-  const double vv = vx * vx + vy * vy + vz * vz;
-  double t = vv > 0.0 ? (wx * vx + wy * vy + wz * vz) / vv : 0.0;
-  t = fmin(fmax(t, 0.0), 1.0);
-  const double dx = wx - t * vx, dy = wy - t * vy, dz = wz - t * vz;
-  const double d = sqrt(dx * dx + dy * dy + dz * dz) - a.bradius[j];
-  return d > 0.0 ? fmin(bnd, a.qbound[p] / d) : bnd;
+  const float vx = (float)-h.ABx, vy = (float)-h.ABy, vz = (float)-h.ABz;  // B - A
+  const float wx = (float)(a.bcenter[3 * j] - A[0]), wy = (float)(a.bcenter[3 * j + 1] - A[1]),
+              wz = (float)(a.bcenter[3 * j + 2] - A[2]);
+  const float vv = vx * vx + vy * vy + vz * vz;
+  float t = vv > 0.f ? (wx * vx + wy * vy + wz * vz) / vv : 0.f;
+  t = fminf(fmaxf(t, 0.f), 1.f);
+  const float dx = wx - t * vx, dy = wy - t * vy, dz = wz - t * vz;
+  const float d = sqrtf(dx * dx + dy * dy + dz * dz) * (1.0f - 1e-5f) - (float)a.bradius[j] - 1e-5f;
+  return d > 0.f ? fminf(bnd, (float)a.qbound[p] * (1.0f + 1e-6f) / d) : bnd;
 }
 
 // sn-LinK decision for pair p in batch j, Eq. (sp_set): -1 drop, else the
 // list index class + kNumClasses * precision (precision 1 = FP32 integrals,
-// for pairs whose estimate max(F_a, F_b) phi A stays below fp32_bound).
+// for pairs whose estimate max(F_a, F_b) phi A stays below fp32_bound).  The
+// estimates are formed in FP32 and rounded up by 1e-5 relative, so every pair
+// an exact evaluation keeps is kept, and a pair at the FP32 / FP64 border goes
+// to the FP64 tier.
 __device__ __forceinline__ int classify_pair(const ScreenArgs& a, const BatchDesc& bd, int j, int p, int cls,
                                              const PairHdr& h) {
   if (a.screen == SNK_SCREEN_NONE) return cls;
   const double* ft = a.ft_shell + bd.cm_off;
-  const double fa = ft[h.sa - bd.ms0], fb = ft[h.sb - bd.ms0];
-  const double bnd = batch_pair_bound(a, j, p, h);
-  const double eK = fmax(fa, fb) * a.phit_b[j] * bnd;
-  if (!((fa * fb * bnd >= a.eps_E) || (eK >= a.eps_K))) return -1;
-  return (a.mixed && eK < a.fp32_bound) ? cls + kNumClasses : cls;
+  const float fa = (float)ft[h.sa - bd.ms0], fb = (float)ft[h.sb - bd.ms0];
+  const float bnd = batch_pair_bound(a, j, p, h) * (1.0f + 1e-5f);
+  const float eK = fmaxf(fa, fb) * (float)a.phit_b[j] * bnd;
+  if (!((fa * fb * bnd >= (float)a.eps_E) || (eK >= (float)a.eps_K))) return -1;
+  return (a.mixed && eK < (float)a.fp32_bound) ? cls + kNumClasses : cls;
 }
 
 // Pass 1: per (batch, list) pair counts and primitive-pair counts; marks the
@@ -470,6 +478,7 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
   const int j = blockIdx.x;
   const BatchDesc bd = a.batches[j];
   const MolDesc md = a.mols[bd.mol];
+  signed char* codes = a.codes + a.code_off[j];    // the decision for each pair of the molecule
   unsigned char* fl = sflag + bd.cm_off;           // shells of V_j
   unsigned char* hl = sflag + hflag_off + bd.cm_off;  // shells of V_j's FP64 (high-tier) pairs
   __shared__ int s_cnt[kNumLists];
@@ -485,6 +494,7 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
     for (int p = md.cr[c] + threadIdx.x; p < md.cr[c + 1]; p += SCR_THREADS) {
       const PairHdr h = a.pairs[p];
       const int li = classify_pair(a, bd, j, p, c, h);
+      codes[p - md.cr[0]] = (signed char)li;
       if (li >= 0) {
         fl[h.sa - bd.ms0] = 1;
         fl[h.sb - bd.ms0] = 1;
@@ -512,7 +522,7 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_count_kernel(ScreenArgs a, i
 }
 
 // Pass 2: deterministic compaction (pair order kept) into the per-(batch, list)
-// ranges that the host sized from pass 1.
+// ranges that the host sized from pass 1, from the decisions pass 1 stored.
 __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, const int64_t* __restrict__ list_off,
                                                                  int* __restrict__ list) {
   const int j = blockIdx.x;
@@ -520,12 +530,13 @@ __global__ void __launch_bounds__(SCR_THREADS) pair_write_kernel(ScreenArgs a, c
   const MolDesc md = a.mols[bd.mol];
   __shared__ int warp_tot[2][SCR_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const signed char* codes = a.codes + a.code_off[j];
   for (int c = 0; c < kNumClasses; ++c) {
     int64_t out[2] = {list_off[j * kNumLists + c], list_off[j * kNumLists + c + kNumClasses]};
     for (int base = md.cr[c]; base < md.cr[c + 1]; base += SCR_THREADS) {
       const int p = base + threadIdx.x;
       int li = -1;
-      if (p < md.cr[c + 1]) li = classify_pair(a, bd, j, p, c, a.pairs[p]);
+      if (p < md.cr[c + 1]) li = codes[p - md.cr[0]];
       const unsigned bal[2] = {__ballot_sync(0xffffffffu, li >= 0 && li < kNumClasses),
                                __ballot_sync(0xffffffffu, li >= kNumClasses)};
       if (lane == 0) {

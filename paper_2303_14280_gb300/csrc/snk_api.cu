@@ -136,6 +136,8 @@ struct snk_ctx {
   DevBuf<int> counts, list, list2, sfunc, colmap, tickets;  // list2: rewrite target of the learned screen
   DevBuf<long long> ppcounts;
   DevBuf<unsigned char> sflag;
+  DevBuf<signed char> codes;  // the screen's decision per (batch, pair)
+  DevBuf<int64_t> code_off;
   DevBuf<int64_t> list_off, tstart;  // per (batch, list): first list entry, first tile
   DevBuf<BatchDesc> batch;
   DevBuf<Tile> tiles;
@@ -192,6 +194,7 @@ struct snk_ctx {
     f(pairs), f(prims), f(mols), f(mlp_w), f(shell_feat), f(keep);
     f(P), f(Pscr), f(ft), f(sym), f(Khat), f(K), f(P2);
     f(counts), f(list), f(list2), f(sfunc), f(colmap), f(tickets), f(ppcounts), f(sflag), f(list_off), f(tstart);
+    f(codes), f(code_off);
     f(batch), f(tiles), f(ws), f(ws32), f(arena), f(ozsplit), f(ozjobs), f(ozerr), f(tsum), f(exec);
   }
   snk_ctx() {
@@ -564,6 +567,19 @@ int screen_and_plan(snk_ctx* c) {
   sa.eps_E = c->opt.eps_E;
   sa.eps_K = c->opt.eps_K;
   sa.fp32_bound = c->opt.fp32_bound;
+  {  // one decision byte per (batch, pair of the batch's molecule)
+    std::vector<int64_t> coff(nbx, 0);
+    int64_t tot_codes = 0;
+    for (int j = 0; j < nb; ++j) {
+      coff[j] = tot_codes;
+      const Setup::Mol& m = s.mols[s.bmol[j]];
+      tot_codes += m.cr[kNumClasses] - m.cr[0];
+    }
+    SNK_CK(c, c->codes.ensure((size_t)std::max<int64_t>(tot_codes, 1)));
+    SNK_CK(c, upload(c->code_off, coff, st));
+  }
+  sa.codes = c->codes.p;
+  sa.code_off = c->code_off.p;
   SNK_CK(c, launch_pair_count(st, sa, nb, c->counts.p, c->ppcounts.p, c->sflag.p, (int64_t)cmn));
   ++c->launches_density;
   c->hcounts.assign((size_t)nbx * kNumLists, 0);

@@ -216,6 +216,8 @@ struct ScreenArgs {
   int distance;             // 1: refine A-tilde by charge / distance per batch
   int mixed;                // 1: route low-estimate pairs to the FP32 lists
   double eps_E, eps_K, fp32_bound;
+  signed char* codes;        // pass 1's decision per (batch, pair of its molecule): list index or -1
+  const int64_t* code_off;   // per batch: its row of codes
 };
 
 cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, int* counts, long long* ppcounts,
