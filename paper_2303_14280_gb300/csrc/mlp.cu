@@ -372,6 +372,8 @@ __global__ void features_kernel(ScreenArgs a, const int* __restrict__ pairlist, 
   }
 }
 
+constexpr int kFilterSplit = 8;  // blocks per batch of the learned filter (balances the last wave)
+
 // Learned screen: for every entry of batch j's lists, predict log10 of the
 // block's contribution to K and clear its keep flag if the prediction is below
 // skip_log10.  One warp evaluates 16 entries at a time on the tensor cores.
@@ -395,7 +397,8 @@ __global__ void __launch_bounds__(128) learned_filter_kernel(ScreenArgs a, const
   int64_t tot = 0, n64 = 0;
   for (int L = 0; L < kNumLists; ++L) tot += counts[(int64_t)j * kNumLists + L];
   for (int L = 0; L < kNumClasses; ++L) n64 += counts[(int64_t)j * kNumLists + L];
-  for (int64_t base = (int64_t)warp * 16; base < tot; base += 4 * 16) {
+  // the batch's entries are shared by gridDim.y blocks, 16 per warp step
+  for (int64_t base = ((int64_t)blockIdx.y * 4 + warp) * 16; base < tot; base += (int64_t)gridDim.y * 4 * 16) {
     // lanes 0..15 compute one row of features each
     if (lane < 16) {
       const int64_t e = base + lane;
@@ -559,7 +562,7 @@ cudaError_t launch_learned_filter(cudaStream_t st, const ScreenArgs& a, int nbat
                                   long long* ppcounts, const float* shell_feat, float skip_log10, float fp32_log10,
                                   unsigned char* keep, unsigned char* hflag) {
   if (nbatch == 0) return cudaSuccess;
-  learned_filter_kernel<<<nbatch, 128, 0, st>>>(a, w, pairlist, list_off, counts, shell_feat, skip_log10, fp32_log10,
+  learned_filter_kernel<<<dim3(nbatch, kFilterSplit), 128, 0, st>>>(a, w, pairlist, list_off, counts, shell_feat, skip_log10, fp32_log10,
                                                 keep);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
