@@ -501,16 +501,17 @@ void build_boys_tables(Setup* s) {
       row[2 * (kBoysTerms + 1) + 1] = tl;
     }
   }
-  // FP32 table of the mixed form (rounded from the same FP64 values)
+  // FP32 table of the mixed form: nodes at the float values fl32(k * 0.05f)
+  // that the kernel forms itself, four Taylor coefficients per row
   s->boys_f.assign((size_t)(kBoysLMax + 1) * kBoysRowsF * kBoysColsF, 0.0f);
-  for (int k = 0; k < kBoysRowsF; ++k)
+  for (int k = 0; k < kBoysRowsF; ++k) {
+    const float tk = (float)k * kBoysHF;
+    host_boys(kBoysLMax + kBoysTermsF, (double)tk, F);
     for (int L = 0; L <= kBoysLMax; ++L) {
-      const double* src = &s->boys[((size_t)L * kBoysRows + k) * kBoysCols];
       float* row = &s->boys_f[((size_t)L * kBoysRowsF + k) * kBoysColsF];
-      for (int m = 0; m < kBoysTermsF; ++m) row[m] = (float)src[m];
-      row[kBoysTermsF] = (float)src[kBoysTerms];
-      row[kBoysTermsF + 1] = (float)src[kBoysTerms + 1];
+      for (int m = 0; m < kBoysTermsF; ++m) row[m] = (float)(F[L + m] * invfact[m]);
     }
+  }
 }
 
 // Several independent molecules in one handle: each is set up on its own

@@ -183,23 +183,22 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(IntegralArgs a) {
 
 // ---------------------------------------------------------------- FP32 pairs (mixed form)
 
-// FP32 seeds S_n = pref F_n(T): 5-term Taylor about the nearest node of a
-// 0.1-spaced float table below T = 30 (|T - T_k| <= 0.05: truncation below
-// 3e-9 relative), the asymptotic form above (e^{-T} < 1e-13 is below FP32
+// FP32 seeds S_n = pref F_n(T): 4-term Taylor about the nearest node of a
+// 0.05-spaced float table below T = 30 (|T - T_k| <= 0.025: truncation below
+// 2e-8 relative; one 16-byte row per lookup, the node fl32(k * 0.05f) formed
+// in registers), the asymptotic form above (e^{-T} < 1e-13 is below FP32
 // resolution).  e^{-T} of the downward recursion comes from the hardware
 // exponential (__expf, ~2^-21 relative).
 template <int L>
 __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_far, const float* tab, float* S) {
   if (T < kBoysTMaxF) {
-    static_assert(kBoysColsF == 8 && kBoysTermsF == 6, "an FP32 table row is two float4");
-    const int k = __float2int_rn(T * (float)(1.0 / kBoysH));
-    const float4 lo = reinterpret_cast<const float4*>(tab)[2 * k];      // F_{L+m}/m!, m = 0..3
-    const float4 hi = reinterpret_cast<const float4*>(tab)[2 * k + 1];  // m = 4, 5; e^{-T_k}; T_k
-    const float x = hi.w - T;
-    float f = fmaf(hi.x, x, lo.w);
-    f = fmaf(f, x, lo.z);
-    f = fmaf(f, x, lo.y);
-    f = fmaf(f, x, lo.x);
+    static_assert(kBoysColsF == 4 && kBoysTermsF == 4, "an FP32 table row is one float4");
+    const int k = __float2int_rn(T * (1.0f / kBoysHF));
+    const float4 r = reinterpret_cast<const float4*>(tab)[k];  // F_{L+m}(T_k)/m!, m = 0..3
+    const float x = (float)k * kBoysHF - T;
+    float f = fmaf(r.w, x, r.z);
+    f = fmaf(f, x, r.y);
+    f = fmaf(f, x, r.x);
     S[L] = pref * f;
     if (L > 0) {
       const float pe = pref * __expf(-T);

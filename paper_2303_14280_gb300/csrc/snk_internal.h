@@ -27,12 +27,13 @@ constexpr int kBoysTerms = 8;
 constexpr int kBoysCols = kBoysTerms + 2;
 constexpr int kBoysLMax = 2 * kLMax;
 
-// FP32 Boys table of the mixed form: T_k = k * kBoysH up to kBoysTMaxF, rows
-// of F_{L+m}(T_k)/m! for m = 0..5, exp(-T_k), T_k.
+// FP32 Boys table of the mixed form: nodes T_k = fl32(k * 0.05f) up to
+// kBoysTMaxF, rows of F_{L+m}(T_k)/m! for m = 0..3 (one float4).
 constexpr float kBoysTMaxF = 30.0f;
-constexpr int kBoysRowsF = 302;
-constexpr int kBoysTermsF = 6;
-constexpr int kBoysColsF = kBoysTermsF + 2;
+constexpr float kBoysHF = 0.05f;
+constexpr int kBoysRowsF = 602;
+constexpr int kBoysTermsF = 4;
+constexpr int kBoysColsF = kBoysTermsF;
 
 // Learned block screen: MLP 16 -> 64 -> 64 -> 64 -> 1 (ReLU).
 constexpr int kMlpIn = 16;
