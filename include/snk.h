@@ -228,7 +228,12 @@ int snk_set_density_device(snk_ctx *ctx, const double *dP);
 int snk_set_density_batch(snk_ctx *ctx, const double *const *P);
 
 /* Build K for the loaded density (Alg. 1 on one GPU).  K is host memory in the
- * packed layout of snk_set_density; the call returns when K is written. */
+ * packed layout of snk_set_density; the call returns when K is written.
+ * Every form is reproducible bit for bit: each G entry of an integral launch
+ * has a single writer whose additions come in pair-list order, and the
+ * batches' contributions to K are summed as exact 64-bit fixed-point integers
+ * (resolution 2^-76, |contribution| < 2^30: a larger or non-finite one gives
+ * SNK_ERR_UNSUPPORTED; at most 2^19 grid batches per handle). */
 int snk_build_K(snk_ctx *ctx, double *K);
 /* Same, writing the packed blocks into device memory; returns once the work
  * is enqueued on the library stream (synchronise it before reading dK). */
@@ -251,11 +256,13 @@ enum { SNK_MAX_DENSITIES = 2 };
 int snk_set_density_multi(snk_ctx *ctx, int32_t n_dens, const double *const *P);
 int snk_build_K_multi(snk_ctx *ctx, double *const *K);
 
-/* Autotuner of the integral kernels (after snk_set_density): for every
- * (class, precision) list, times the kernel on the batches of the last
- * workspace chunk for runs of 2..128 shell pairs per 128-point tile and keeps
- * the fastest; the choice holds for later builds and densities of the handle.
- * runs (optional, 12 entries: FP64 ss ps pp ds dp dd, then FP32) receives it. */
+/* Autotuner of the integral kernels (after snk_set_density): for every FP32
+ * list of the mixed form, times the kernel on the batches of the last
+ * workspace chunk for 2..128 shell pairs staged (and tile-screened) per step
+ * of a 128-point tile and keeps the fastest; the choice holds for later builds
+ * and densities of the handle.  runs (optional, 12 entries: FP64 ss ps pp ds
+ * dp dd, then FP32) receives the steps (the FP64 lists take their whole list
+ * per tile and do not use theirs). */
 int snk_autotune(snk_ctx *ctx, int32_t *runs);
 
 /* Stream for all later work on this handle (a cudaStream_t; NULL = the legacy

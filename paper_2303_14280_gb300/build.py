@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsnk.so")
 SOURCES = ["host_setup.cpp", "kernels_dense.cu", "kernels_integrals.cu", "kernels_ozaki.cu", "mlp.cu", "snk_api.cu"]
-HEADERS = ["snk_internal.h", "os_generated.cuh", os.path.join("..", "..", "include", "snk.h")]
+HEADERS = ["snk_internal.h", "os_generated.cuh", "async_copy.cuh", "ds_arith.cuh",
+           os.path.join("..", "..", "include", "snk.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

@@ -605,15 +605,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
 template <int MODE>
 __global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
     kgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc, const int* __restrict__ sfunc,
-                 const double* __restrict__ ws, double* __restrict__ Khat, int dens) {
+                 const double* __restrict__ ws, unsigned long long* __restrict__ Khat, int dens, int* err) {
   const BatchDesc bd = batches[blockIdx.z];
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   if (m0 >= bd.nS || n0 >= bd.nB) return;
   const int64_t dofs = (int64_t)dens * bd.ldq * bd.nS;  // density d's G block
   const int* xf = xfunc + bd.xfunc_off;
   const int* sf = sfunc + bd.sfunc_off;
-  double* Km = Khat + bd.pk_off;
-  auto st = [&](int m, int n, double c) { atomicAdd(&Km[(int64_t)sf[m] * bd.nfm + xf[n]], c); };
+  unsigned long long* Km = Khat + 2 * bd.pk_off;
+  auto st = [&](int m, int n, double c) { khat_add(&Km[2 * ((int64_t)sf[m] * bd.nfm + xf[n])], c, err); };
   if (MODE == 2) {
     const float2* X2 = reinterpret_cast<const float2*>(ws + bd.xoff);
     const float2* G2 = reinterpret_cast<const float2*>(ws + bd.goff) + dofs;
@@ -629,27 +629,27 @@ __global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
   }
 }
 
-// Tiles of list k of batch j (one block per (batch, list)).
+// Tiles of list k of batch j (one block per (batch, list)): one per slab of
+// kPointTile points, each with the whole list, so that every G entry of the
+// list's launch has a single writer (its point's thread) and its additions
+// come in list order.
 __global__ void gen_tiles_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ counts,
                                  const int64_t* __restrict__ list_off, const int64_t* __restrict__ tstart,
-                                 RunLengths runs, Tile* __restrict__ tiles) {
+                                 Tile* __restrict__ tiles) {
   const int j = blockIdx.x, k = blockIdx.y;
   const int64_t e = (int64_t)j * kNumLists + k;
   const int n = counts[e];
   if (n == 0) return;
-  const int run = runs.run[k];
   const int q = batches[j].q;
   const int nslab = (q + kPointTile - 1) / kPointTile;
-  const int nrun = (n + run - 1) / run;
   const int base = (int)list_off[e];
   Tile* out = tiles + tstart[e];
-  for (int u = threadIdx.x; u < nrun * nslab; u += blockDim.x) {
-    const int r = u / nslab, sl = u - r * nslab;
+  for (int u = threadIdx.x; u < nslab; u += blockDim.x) {
     Tile t;
     t.batch = j;
-    t.k0 = base + r * run;
-    t.k1 = base + min(n, (r + 1) * run);
-    t.i0 = sl * kPointTile;
+    t.k0 = base;
+    t.k1 = base + n;
+    t.i0 = u * kPointTile;
     out[u] = t;
   }
 }
@@ -667,14 +667,14 @@ __global__ void abs_sum_kernel(const double* __restrict__ P, int n_dens, int64_t
 // Eq. (sn_k); the row factor f_mu is the Cartesian component factor that the
 // integral kernel leaves out.
 __global__ void finish_kernel(const MolDesc* __restrict__ mols, int n_mol, int64_t packed,
-                              const double* __restrict__ Khat, const double* __restrict__ fcomp,
+                              const unsigned long long* __restrict__ Khat, const double* __restrict__ fcomp,
                               double* __restrict__ K) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < packed; e += (int64_t)gridDim.x * blockDim.x) {
     const MolDesc md = mols[mol_of_packed(mols, n_mol, e)];
     const int64_t le = e - md.pk_off;
     const int mu = (int)(le / md.nf), nu = (int)(le % md.nf);
-    const double a = __dmul_rn(fcomp[md.mf0 + mu], Khat[e]);
-    const double b = __dmul_rn(fcomp[md.mf0 + nu], Khat[md.pk_off + (int64_t)nu * md.nf + mu]);
+    const double a = __dmul_rn(fcomp[md.mf0 + mu], khat_value(Khat + 2 * e));
+    const double b = __dmul_rn(fcomp[md.mf0 + nu], khat_value(Khat + 2 * (md.pk_off + (int64_t)nu * md.nf + mu)));
     // explicit rounding of both products keeps K exactly symmetric (no FMA contraction)
     K[e] = 0.5 * __dadd_rn(a, b);
   }
@@ -776,20 +776,21 @@ cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, i
 }
 
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int dens) {
+                         const int* xfunc, const int* sfunc, const double* ws, unsigned long long* Khat, int mode,
+                         int dens, int* err) {
   if (nbatch == 0 || max_nS == 0 || max_nB == 0) return cudaSuccess;
   dim3 grid((max_nS + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
   if (mode == 2)
-    kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, dens);
+    kgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, dens, err);
   else
-    kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, dens);
+    kgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, sfunc, ws, Khat, dens, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batches, const int* counts,
-                             const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles) {
+                             const int64_t* list_off, const int64_t* tstart, Tile* tiles) {
   if (nbatch == 0) return cudaSuccess;
-  gen_tiles_kernel<<<dim3(nbatch, kNumLists), 256, 0, st>>>(batches, counts, list_off, tstart, runs, tiles);
+  gen_tiles_kernel<<<dim3(nbatch, kNumLists), 256, 0, st>>>(batches, counts, list_off, tstart, tiles);
   return cudaGetLastError();
 }
 
@@ -814,7 +815,7 @@ cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* Khat,
+cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const unsigned long long* Khat,
                           const double* fcomp, double* K) {
   if (packed == 0) return cudaSuccess;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((packed + 255) / 256, 152 * 16));

@@ -10,9 +10,12 @@
 // 3c-CP block is never stored (the merged HRR + contraction of App. A).
 //
 // Parallel decomposition (Sec. II.F, batching levels (1)-(3)): one thread per
-// grid point, a 128-point tile of one batch per CTA iteration, a run of pairs
-// of one class per tile; persistent CTAs take tiles from an atomic ticket.  The
-// Boys interpolation table of the class's L lives in shared memory.
+// grid point, a 128-point tile of one batch per CTA iteration, the batch's
+// whole pair list of one class per tile; persistent CTAs take tiles from an
+// atomic ticket (largest batches first).  Each G entry of a launch therefore
+// has a single writer, its point's thread, whose reductions land in list
+// order: G, and with it K, is the same bit for bit from run to run.  The Boys
+// interpolation table of the class's L lives in shared memory.
 //
 // GB300 issues FP64 at 2 DFMA per SM per clock (1/64 of FP32), so the kernel
 // is FP64-pipe bound by construction: table lookups, index arithmetic, F loads
@@ -25,6 +28,7 @@
 
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "ds_arith.cuh"
 #include "os_generated.cuh"
 #include "snk_internal.h"
@@ -34,8 +38,9 @@ namespace snk {
 namespace {
 
 constexpr int kIntThreads = kPointTile;
-constexpr int kMaxRun = 128;  // longest pair run of a tile (the autotuner's largest candidate)
-static_assert(kMaxRun == kIntThreads, "the FP32 kernel stages a tile's pairs one per thread");
+constexpr int kMaxRun = 128;  // most pairs per staging step (the autotuner's largest candidate)
+constexpr unsigned long long kCopyWaitNs = 2000000000ull;  // 2 s per wait on a bulk copy, then give up
+static_assert(kMaxRun == kIntThreads, "the FP32 kernel stages a step's pairs one per thread");
 constexpr long long kBoysTMaxBits = 0x4049000000000000LL;  // bit pattern of 50.0
 static_assert(kBoysTMax == 50.0, "kBoysTMaxBits encodes 50.0");
 
@@ -222,179 +227,175 @@ __device__ __forceinline__ void boys_seeds_f32(float T, float pref, float pref_f
 // kernel forms A - r_i once from the (hi, lo) float splits of A and r_i, and
 // P - r_i = (P - A) + (A - r_i) per primitive: accurate to FP32 relative to
 // the larger of |P - A| and |A - r_i| wherever the molecule sits, which is
-// what the VRR terms PA_x Theta and PC_x Theta need.  A tile's pair headers,
-// columns, R_a - R_b and R_a are staged in shared memory once per tile (one
-// barrier per tile); the next pair's F is loaded while the current pair
-// computes; for the light classes each warp also stages the pair's records
-// (below).
+// what the VRR terms PA_x Theta and PC_x Theta need.  A tile is a batch's
+// whole list on 128 points, taken in steps of a.run pairs: each step's pair
+// headers, columns, R_a - R_b and R_a are staged in shared memory (one per
+// thread, after the tile screen), and the tile's batch descriptor sits in
+// shared memory too, so that nothing of the tile stays in registers across
+// the pair loop.  Per pair each warp needs the pair's primitive records and
+// the F columns of shell b at its 32 points:
+//   - heavy classes (L >= 2): a ring of three slots per warp, filled by TMA
+//     bulk copies that lane 0 issues two pairs ahead, each slot completing
+//     on its own mbarrier (bounded waits);
+//   - light classes: the next pair's F from global memory into registers and
+//     its records into a second shared buffer while the current pair
+//     computes (fewer instructions per pair than the ring, whose serial
+//     issue does not pay for a pair of a few primitives).
 template <int LA, int LB, int ND>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs a) {
   using C = OsClass<LA, LB>;
   constexpr int NA = C::NA, NB = C::NB;
-  constexpr int kStage = 16;  // primitive records per pair staged per warp (32 float4)
-  // staging pays for the light classes, whose few FP32 operations per
-  // primitive cannot cover the record loads; heavier classes read the records
-  // directly (fewer registers, more resident warps)
-  constexpr bool STAGE = C::L <= 1;
+  constexpr int kStage = 16;               // primitive records of a pair staged (32 float4)
+  constexpr bool RING = C::L >= 2;
+  constexpr int kRing = 3;
+  constexpr int kRecF4 = 2 * kStage;       // float4 of records per slot
+  constexpr int kFbF4 = ND * NB * 32 / 4;  // float4 of F_b per ring slot
+  constexpr int kW = kIntThreads / 32;
   extern __shared__ __align__(16) float s_tabf[];
   const float* gtab = a.boys_f + (size_t)C::L * kBoysRowsF * kBoysColsF;
   for (int e = threadIdx.x; e < kBoysRowsF * kBoysColsF; e += blockDim.x) s_tabf[e] = gtab[e];
-  // the tile's pairs, staged once per tile: primitive range, shells, F / G
-  // columns, R_a - R_b and R_a
   __shared__ int s_ppo[kMaxRun], s_ppn[kMaxRun], s_sa[kMaxRun], s_sb[kMaxRun], s_ca[kMaxRun], s_cb[kMaxRun];
   __shared__ float2 s_ab[kMaxRun][3];  // (hi, lo)
   __shared__ float2 s_A[kMaxRun][3];   // (hi, lo)
-  // per warp, double-buffered: the current pair's primitive records; the next
-  // pair's are loaded (coalesced, one request per 128 B) while this one computes
-  __shared__ float4 s_pr[STAGE ? kIntThreads / 32 : 1][2][STAGE ? kStage * 2 : 1];
-  __shared__ int s_tile, s_wcnt[kIntThreads / 32];
-  __syncthreads();
+  __shared__ __align__(128) float4 s_ring[RING ? kW : 1][RING ? kRing : 1][RING ? kRecF4 + kFbF4 : 1];
+  __shared__ __align__(8) uint64_t s_full[kW][kRing];
+  __shared__ float4 s_pr[RING ? 1 : kW][2][RING ? 1 : kRecF4];
+  __shared__ Tile s_t;
+  __shared__ BatchDesc s_bd;
+  __shared__ int s_tid, s_wcnt[kW];
+  __shared__ volatile int s_abort;  // a wait ran out: the CTA stops taking work
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_abort = 0;
+  if (RING && lane == 0) {
+#pragma unroll
+    for (int s = 0; s < kRing; ++s) mbar_init(&s_full[wid][s], 1);
+    mbar_init_fence();
+  }
+  uint32_t prod = 0, cons = 0;  // ring: this warp's pairs issued into / taken from its slots
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.ticket, 1);
+    __syncthreads();  // every thread is done with the previous tile's descriptors and pairs
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(a.ticket, 1);
+      s_tid = t;
+      if (t < a.n_tiles) {
+        s_t = a.tiles[t];
+        s_bd = a.batches[s_t.batch];
+      }
+    }
     __syncthreads();
-    const int t = s_tile;
-    __syncthreads();  // every thread is done with the previous tile's staged pairs
-    if (t >= a.n_tiles) break;
-    const Tile tile = a.tiles[t];
-    const BatchDesc bd = a.batches[tile.batch];
-    const int* cmap = a.colmap + bd.cm_off - bd.ms0;  // indexed by global shell id
-    // stage the tile's pairs (one per thread, order kept); with the tile screen
-    // only those whose bound on this tile's points reaches eps_tile
-    int nrun;
-    {
-      const int r = threadIdx.x, n = tile.k1 - tile.k0;  // n <= kMaxRun = blockDim
-      int p = 0, ca = 0, cb = 0, npp_keep = 0;
-      PairHdr h{};
-      bool keep = r < n;
-      if (keep) {
-        p = a.pairlist[tile.k0 + r];
-        h = a.pairs[p];
-        ca = cmap[h.sa];
-        cb = cmap[h.sb];
-        npp_keep = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
-        if (a.eps_tile > 0.f) {
-          const float* ts = a.tsum + bd.ssoff + (int64_t)(tile.i0 / kPointTile) * (bd.nS + 4);
-          float sa = 0.f, sb = 0.f;
+    if (s_tid >= a.n_tiles || s_abort) break;
+    // the tile's list in steps of a.run pairs (block-uniform loop: every
+    // thread passes the same barriers)
+    for (int kb = s_t.k0; kb < s_t.k1; kb += a.run) {
+      // stage the step's pairs (one per thread, order kept); with the tile screen
+      // only those whose bound on this tile's points reaches eps_tile
+      int nrun;
+      {
+        const int r = threadIdx.x, n = min(a.run, s_t.k1 - kb);  // n <= kMaxRun = blockDim
+        int p = 0, ca = 0, cb = 0, npp_keep = 0;
+        PairHdr h{};
+        bool keep = r < n;
+        if (keep) {
+          const int* cmap = a.colmap + s_bd.cm_off - s_bd.ms0;  // indexed by global shell id
+          p = a.pairlist[kb + r];
+          h = a.pairs[p];
+          ca = cmap[h.sa];
+          cb = cmap[h.sb];
+          npp_keep = h.pp_n32;  // the leading primitive pairs the FP32 tier keeps
+          if (a.eps_tile > 0.f) {
+            const float* ts = a.tsum + s_bd.ssoff + (int64_t)(s_t.i0 / kPointTile) * (s_bd.nS + 4);
+            float sa = 0.f, sb = 0.f;
 #pragma unroll
-          for (int u = 0; u < NA; ++u) sa += ts[ca + u];
+            for (int u = 0; u < NA; ++u) sa += ts[ca + u];
 #pragma unroll
-          for (int v = 0; v < NB; ++v) sb += ts[cb + v];
-          // |A_ab| <= min(global bound, total charge / distance) on the tile's sphere
-          const double* A = a.shell_xyz + 3 * h.sa;
-          const float vx = (float)-h.ABx, vy = (float)-h.ABy, vz = (float)-h.ABz;  // B - A
-          const float wx = ts[bd.nS] - (float)A[0], wy = ts[bd.nS + 1] - (float)A[1],
-                      wz = ts[bd.nS + 2] - (float)A[2];
-          const float vv = vx * vx + vy * vy + vz * vz;
-          float tt = vv > 0.f ? (wx * vx + wy * vy + wz * vz) / vv : 0.f;
-          tt = fminf(fmaxf(tt, 0.f), 1.f);
-          const float dx = wx - tt * vx, dy = wy - tt * vy, dz = wz - tt * vz;
-          const float d = sqrtf(dx * dx + dy * dy + dz * dz) - ts[bd.nS + 3] - 1e-4f;
-          const float glob = (float)a.pbound[p], smax = fmaxf(sa, sb);
-          float bnd = glob;
-          if (d > 0.f) bnd = fminf(bnd, (float)a.qbound[p] / d);
-          keep = bnd * smax >= a.eps_tile;
-          if (keep) {
-            // primitive pairs come largest bound first: leave out the tail whose
-            // bounds on this tile add up to less than eps_tile
-            const float4* rec = a.prims_f32 + (size_t)h.pp_off * 2;
-            float tail = 0.f;
-            int n = h.pp_n32;
-            while (n > 1) {
-              const float t2 = tail + rec[2 * (n - 1) + 1].w * glob * smax;
-              if (t2 >= a.eps_tile) break;
-              tail = t2;
-              --n;
+            for (int v = 0; v < NB; ++v) sb += ts[cb + v];
+            // |A_ab| <= min(global bound, total charge / distance) on the tile's sphere
+            const double* A = a.shell_xyz + 3 * h.sa;
+            const float vx = (float)-h.ABx, vy = (float)-h.ABy, vz = (float)-h.ABz;  // B - A
+            const float wx = ts[s_bd.nS] - (float)A[0], wy = ts[s_bd.nS + 1] - (float)A[1],
+                        wz = ts[s_bd.nS + 2] - (float)A[2];
+            const float vv = vx * vx + vy * vy + vz * vz;
+            float tt = vv > 0.f ? (wx * vx + wy * vy + wz * vz) / vv : 0.f;
+            tt = fminf(fmaxf(tt, 0.f), 1.f);
+            const float dx = wx - tt * vx, dy = wy - tt * vy, dz = wz - tt * vz;
+            const float d = sqrtf(dx * dx + dy * dy + dz * dz) - ts[s_bd.nS + 3] - 1e-4f;
+            const float glob = (float)a.pbound[p], smax = fmaxf(sa, sb);
+            float bnd = glob;
+            if (d > 0.f) bnd = fminf(bnd, (float)a.qbound[p] / d);
+            keep = bnd * smax >= a.eps_tile;
+            if (keep) {
+              // primitive pairs come largest bound first: leave out the tail whose
+              // bounds on this tile add up to less than eps_tile
+              const float4* rec = a.prims_f32 + (size_t)h.pp_off * 2;
+              float tail = 0.f;
+              int n = h.pp_n32;
+              while (n > 1) {
+                const float t2 = tail + rec[2 * (n - 1) + 1].w * glob * smax;
+                if (t2 >= a.eps_tile) break;
+                tail = t2;
+                --n;
+              }
+              npp_keep = n;
             }
-            npp_keep = n;
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        nrun = 0;
+#pragma unroll
+        for (int w = 0; w < kW; ++w) {
+          before += w < wid ? s_wcnt[w] : 0;
+          nrun += s_wcnt[w];
+        }
+        if (keep) {
+          const int q = before + __popc(bal & ((1u << lane) - 1u));
+          s_ppo[q] = h.pp_off;
+          s_ppn[q] = npp_keep;
+          s_sa[q] = h.sa;
+          s_sb[q] = h.sb;
+          s_ca[q] = ca;
+          s_cb[q] = cb;
+          const float2* ab = a.pair_ab + 4 * (size_t)p;
+          const float2* pa = a.pair_a + 4 * (size_t)p;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            s_ab[q][m] = ab[m];
+            s_A[q][m] = pa[m];
           }
         }
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) s_wcnt[wid] = __popc(bal);
       __syncthreads();
-      int before = 0;
-      nrun = 0;
-#pragma unroll
-      for (int w = 0; w < kIntThreads / 32; ++w) {
-        before += w < wid ? s_wcnt[w] : 0;
-        nrun += s_wcnt[w];
+      if (threadIdx.x == 0 && nrun > 0) {  // the work this step computes, for the flop counts
+        unsigned long long npp = 0;
+        for (int r = 0; r < nrun; ++r) npp += (unsigned long long)s_ppn[r];
+        const unsigned long long pts = (unsigned long long)min(kPointTile, s_bd.q - s_t.i0);
+        atomicAdd(&a.exec[0], npp * pts);
+        atomicAdd(&a.exec[1], (unsigned long long)nrun * pts);
       }
-      if (keep) {
-        const int q = before + __popc(bal & ((1u << lane) - 1u));
-        s_ppo[q] = h.pp_off;
-        s_ppn[q] = npp_keep;
-        s_sa[q] = h.sa;
-        s_sb[q] = h.sb;
-        s_ca[q] = ca;
-        s_cb[q] = cb;
-        const float2* ab = a.pair_ab + 4 * (size_t)p;
-        const float2* pa = a.pair_a + 4 * (size_t)p;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          s_ab[q][m] = ab[m];
-          s_A[q][m] = pa[m];
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && nrun > 0) {  // the work this tile computes, for the flop counts
-      unsigned long long npp = 0;
-      for (int r = 0; r < nrun; ++r) npp += (unsigned long long)s_ppn[r];
-      const unsigned long long pts = (unsigned long long)min(kPointTile, bd.q - tile.i0);
-      atomicAdd(&a.exec[0], npp * pts);
-      atomicAdd(&a.exec[1], (unsigned long long)nrun * pts);
-    }
-    const int i = tile.i0 + threadIdx.x;
-    const bool active = i < bd.q;  // inactive lanes still stage records for their warp
-    if (nrun <= 0 || __all_sync(0xffffffffu, !active)) continue;
-    ds cx = ds_make(0.f, 0.f), cy = cx, cz = cx;
-    if (active) {
-      cx = ds_from(a.xyz[3 * (bd.p0 + i)]);
-      cy = ds_from(a.xyz[3 * (bd.p0 + i) + 1]);
-      cz = ds_from(a.xyz[3 * (bd.p0 + i) + 2]);
-    }
-    const int64_t ldq = bd.ldq, dstr = (int64_t)bd.ldq * bd.nS;  // density d's F / G: + d dstr
-    const float* F = a.ws32 + bd.foff32 + i;
-    double* G64 = a.ws + bd.goff + i;
-    // the FP32 contributions are added to the FP64 G with FP64 atomics: their
-    // order changes K by ~1e-14 from run to run (FP32 atomics: ~1e-10)
-    auto gadd = [&](int d, int col, float v) { atomicAdd(G64 + d * dstr + col * ldq, (double)v); };
-    if (STAGE) {  // the first pair's records
-      const int n2 = min(s_ppn[0], kStage) * 2;
-      const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 2;
-      if (lane < n2) s_pr[wid][0][lane] = src[lane];
-      __syncwarp();
-    }
-    float ga[ND][NA], fa[ND][NA], fn[ND][NB];
-    int cur = -1, cola = 0;
-#pragma unroll
-    for (int d = 0; d < ND; ++d)
-#pragma unroll
-      for (int v = 0; v < NB; ++v) fn[d][v] = active ? F[d * dstr + (s_cb[0] + v) * ldq] : 0.f;
-    for (int r = 0; r < nrun; ++r) {
-      const float4* rec = s_pr[STAGE ? wid : 0][r & 1];
-      float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-      int n2n = 0;
-      if (STAGE && r + 1 < nrun) {  // the next pair's records are in flight while this pair computes
-        n2n = min(s_ppn[r + 1], kStage) * 2;
-        const float4* src = a.prims_f32 + (size_t)s_ppo[r + 1] * 2;
-        if (lane < n2n) pre = src[lane];
-      }
-      float fb[ND][NB];
-#pragma unroll
-      for (int d = 0; d < ND; ++d)
-#pragma unroll
-        for (int v = 0; v < NB; ++v) fb[d][v] = fn[d][v];
-      if (active && r + 1 < nrun) {
-        const int cn = s_cb[r + 1];
-#pragma unroll
-        for (int d = 0; d < ND; ++d)
-#pragma unroll
-          for (int v = 0; v < NB; ++v) fn[d][v] = F[d * dstr + (cn + v) * ldq];
-      }
-      const int sa = s_sa[r];
+      const int i = s_t.i0 + threadIdx.x;
+      const bool active = i < s_bd.q;  // inactive lanes of a partly active warp follow along
+      if (nrun <= 0 || s_abort || __all_sync(0xffffffffu, !active)) continue;
+      ds cx = ds_make(0.f, 0.f), cy = cx, cz = cx;
       if (active) {
+        cx = ds_from(a.xyz[3 * (s_bd.p0 + i)]);
+        cy = ds_from(a.xyz[3 * (s_bd.p0 + i) + 1]);
+        cz = ds_from(a.xyz[3 * (s_bd.p0 + i) + 2]);
+      }
+      const int64_t ldq = s_bd.ldq, dstr = (int64_t)s_bd.ldq * s_bd.nS;  // density d's F / G: + d dstr
+      const float* F = a.ws32 + s_bd.foff32 + i;
+      double* G64 = a.ws + s_bd.goff + i;
+      // the FP32 contributions are added to the FP64 G with FP64 reductions;
+      // each G entry of the launch has one writer (its point's thread), so
+      // they land in list order and G is the same from run to run
+      auto gadd = [&](int d, int col, float v) { atomicAdd(G64 + d * dstr + col * ldq, (double)v); };
+      float ga[ND][NA], fa[ND][NA];
+      int cur = -1, cola = 0;
+      // pair r at this thread's point, from its records (shared memory, or
+      // global memory for more than kStage primitive pairs) and F_b
+      auto compute = [&](int r, const float4* rec, const float (&fb)[ND][NB]) {
+        const int sa = s_sa[r];
         if (sa != cur) {
           if (cur >= 0) {
 #pragma unroll
@@ -427,9 +428,9 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
           C::vrr(S, r0.y, r0.z, r0.w, PCx, PCy, PCz, r1.z, 2.0f * r1.z, 3.0f * r1.z, acc);
         };
         const int ppn = s_ppn[r];
-        if (STAGE && ppn <= kStage) {
+        if (ppn <= kStage) {
           for (int q = 0; q < ppn; ++q) prim(rec[2 * q], rec[2 * q + 1]);
-        } else {  // heavier classes, or more primitive pairs than staged: global memory
+        } else {  // more primitive pairs than staged: global memory
           const float4* pp = a.prims_f32 + (size_t)s_ppo[r] * 2;
           for (int q = 0; q < ppn; ++q) prim(pp[2 * q], pp[2 * q + 1]);
         }
@@ -453,20 +454,110 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
               gadd(d, colb + v, g);
             }
         }
-      }
-      // every lane is past its reads of the other buffer (the previous
-      // iteration's closing __syncwarp), so it can take the next records
-      if (STAGE) {
-        if (lane < n2n) s_pr[wid][(r + 1) & 1][lane] = pre;
-        __syncwarp();
-      }
-    }
-    if (active) {
+      };
+      if constexpr (RING) {
+        // the warp's 32 points of every F column: 128 contiguous, 16-byte
+        // aligned bytes (foff32, ldq and i0 are multiples of 128 floats, and
+        // the columns are ldq >= i0 + 128 long)
+        const float* Fw = a.ws32 + s_bd.foff32 + s_t.i0 + 32 * wid;
+        // pair r into the next slot: its records (at most kStage primitive
+        // pairs; longer contractions are read from global memory) and its
+        // F_b columns, one bulk copy each, all on the slot's barrier.  The
+        // slot was last read by this warp's lanes before the __syncwarp that
+        // precedes every call.
+        auto issue = [&](int r) {
+          if (lane == 0) {
+            const int sl = prod % kRing;
+            uint64_t* bar = &s_full[wid][sl];
+            const int ppn = s_ppn[r];
+            const uint32_t rec_bytes = ppn <= kStage ? 32u * (uint32_t)ppn : 0u;
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, rec_bytes + ND * NB * 128);
+            if (rec_bytes) bulk_copy(s_ring[wid][sl], a.prims_f32 + (size_t)s_ppo[r] * 2, rec_bytes, bar);
+            float* fdst = reinterpret_cast<float*>(s_ring[wid][sl] + kRecF4);
+            const int cb = s_cb[r];
 #pragma unroll
-      for (int d = 0; d < ND; ++d)
+            for (int d = 0; d < ND; ++d)
 #pragma unroll
-        for (int u = 0; u < NA; ++u) gadd(d, cola + u, ga[d][u]);
-    }
+              for (int v = 0; v < NB; ++v)
+                bulk_copy(fdst + (d * NB + v) * 32, Fw + d * dstr + (int64_t)(cb + v) * ldq, 128, bar);
+          }
+          ++prod;
+        };
+        for (int r = 0; r < min(nrun, kRing); ++r) issue(r);
+        for (int r = 0; r < nrun; ++r) {
+          const int sl = cons % kRing;
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(&s_full[wid][sl], (cons / kRing) & 1u, a.err,
+                                                            kCopyWaitNs));
+          ++cons;
+          if (!ok) {
+            // give up: no further work in this CTA; wait (bounded again) for
+            // the copies still in flight into this warp's ring, then leave
+            s_abort = 1;
+            for (uint32_t q = cons - 1; q < prod; ++q)
+              mbar_wait(&s_full[wid][q % kRing], (q / kRing) & 1u, nullptr, kCopyWaitNs);
+            cons = prod;
+            break;
+          }
+          if (active) {
+            const float* fsl = reinterpret_cast<const float*>(s_ring[wid][sl] + kRecF4);
+            float fb[ND][NB];
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+#pragma unroll
+              for (int v = 0; v < NB; ++v) fb[d][v] = fsl[(d * NB + v) * 32 + lane];
+            compute(r, s_ring[wid][sl], fb);
+          }
+          __syncwarp();  // every lane is done with slot sl: it takes pair r + kRing
+          if (r + kRing < nrun) issue(r + kRing);
+        }
+      } else {
+        {  // the first pair's records
+          const int n2 = min(s_ppn[0], kStage) * 2;
+          const float4* src = a.prims_f32 + (size_t)s_ppo[0] * 2;
+          if (lane < n2) s_pr[RING ? 0 : wid][0][lane] = src[lane];
+          __syncwarp();
+        }
+        float fn[ND][NB];
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+          for (int v = 0; v < NB; ++v) fn[d][v] = active ? F[d * dstr + (s_cb[0] + v) * ldq] : 0.f;
+        for (int r = 0; r < nrun; ++r) {
+          // the next pair's records and F are in flight while this pair computes
+          float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+          int n2n = 0;
+          if (r + 1 < nrun) {
+            n2n = min(s_ppn[r + 1], kStage) * 2;
+            const float4* src = a.prims_f32 + (size_t)s_ppo[r + 1] * 2;
+            if (lane < n2n) pre = src[lane];
+          }
+          float fb[ND][NB];
+#pragma unroll
+          for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int v = 0; v < NB; ++v) fb[d][v] = fn[d][v];
+          if (active && r + 1 < nrun) {
+            const int cn = s_cb[r + 1];
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+#pragma unroll
+              for (int v = 0; v < NB; ++v) fn[d][v] = F[d * dstr + (cn + v) * ldq];
+          }
+          if (active) compute(r, s_pr[RING ? 0 : wid][r & 1], fb);
+          // every lane is past its reads of the other buffer (the previous
+          // iteration's closing __syncwarp), so it can take the next records
+          if (lane < n2n) s_pr[RING ? 0 : wid][(r + 1) & 1][lane] = pre;
+          __syncwarp();
+        }
+      }
+      if (active && cur >= 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+          for (int u = 0; u < NA; ++u) gadd(d, cola + u, ga[d][u]);
+      }
+    }  // steps of the tile's list
   }
 }
 

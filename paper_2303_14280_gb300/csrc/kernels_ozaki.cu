@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "snk_internal.h"
 
 namespace snk {
@@ -216,61 +217,8 @@ __global__ void __launch_bounds__(256) oz_split_rows_kernel(const OzSplitJob* __
 
 // ---------------------------------------------------------------- PTX helpers
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for the phase with the given parity; false (and the error flag set)
-// if it does not complete within kOzWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try(bar, parity)) {
-    if (global_ns() - t0 > kOzWaitNs) {
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t parity, int* err) {
+  return mbar_wait(bar, parity, err, kOzWaitNs);
 }
 
 // shared-memory matrix descriptor: no swizzle, K-major, core matrices 128 B
@@ -380,7 +328,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
       mbar_init(&sh->tfull[b], 1);
       mbar_init(&sh->tempty[b], kOzEpiWarps);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   if (warp == 1) {  // the whole warp allocates all 512 columns of tensor memory
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&sh->tmem_base))
@@ -432,7 +380,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
         const uint8_t* Ab = a.arena + ao;
         const uint8_t* Bb = a.arena + bo;
         for (int kt = 0; kt < J.KT && ok; ++kt) {
-          if (!mbar_wait(&sh->empty[stage], phase ^ 1, a.err)) {
+          if (!oz_wait(&sh->empty[stage], phase ^ 1, a.err)) {
             ok = false;
             break;
           }
@@ -471,7 +419,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
         const int KT = a.jobs[jb].KT;
         for (int c0 = 0; c0 < KT && ok; c0 += kOzKtPerChunk) {
           // the epilogue must have drained this buffer
-          if (!mbar_wait(&sh->tempty[buf], tphase ^ 1, a.err)) {
+          if (!oz_wait(&sh->tempty[buf], tphase ^ 1, a.err)) {
             ok = false;
             break;
           }
@@ -479,7 +427,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
           const uint32_t dbase = tmem + (uint32_t)(buf * C::kAcc * kOzRows);
           bool first[3] = {true, true, true};
           for (int kt = c0; kt < min(KT, c0 + kOzKtPerChunk) && ok; ++kt) {
-            if (!mbar_wait(&sh->full[stage], phase, a.err)) {
+            if (!oz_wait(&sh->full[stage], phase, a.err)) {
               ok = false;
               break;
             }
@@ -535,7 +483,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
       const uint32_t thi = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(3 * kOzRows + col0);
       bool first_run = true;
       for (int c0 = 0; c0 < J.KT && ok; c0 += kOzKtPerChunk) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&sh->tfull[buf], tphase, a.err));
+        ok = __all_sync(0xffffffffu, oz_wait(&sh->tfull[buf], tphase, a.err));
         if (!ok) break;
         tc_fence_after();
         const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * C::kAcc * kOzRows + col0);
@@ -623,12 +571,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
         // Kt_{s nu} += sum_i G-hat_{s i} X_{nu i}, scattered into the molecule's block
         const int* sf = a.sfunc + bd.sfunc_off;
         const int* xf = a.xfunc + bd.xfunc_off;
-        double* Km = a.Khat + J.out_off;
+        unsigned long long* Km = a.Khat + 2 * J.out_off;
         const int64_t rowoff = (int64_t)sf[J.c0 + m] * bd.nfm;
 #pragma unroll
         for (int c = 0; c < 64; ++c) {
           const int n = nt * kOzRows + col0 + c;
-          if (n < J.n_lim) atomicAdd(&Km[rowoff + xf[n]], res[c]);
+          if (n < J.n_lim) khat_add(&Km[2 * (rowoff + xf[n])], res[c], a.err);
         }
       }
     }

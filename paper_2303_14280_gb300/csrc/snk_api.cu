@@ -94,7 +94,7 @@ struct DevBuf {
 
 // pairs per integral tile for each class (cheap classes take longer runs);
 // the autotuner replaces these per list
-constexpr int kPairsPerTile[kNumClasses] = {64, 32, 16, 16, 8, 8};
+constexpr int kDefaultStep = 128;  // pairs staged per step of the FP32 kernel, before autotuning
 constexpr int kRunCandidates[] = {2, 4, 8, 16, 32, 64, 128};
 // per chunk: collocation, F operands, F high tier, F rest, integral lists, K operands, K high tier, K rest
 constexpr int kPhaseEvents = 7 + kNumLists;
@@ -131,7 +131,8 @@ struct snk_ctx {
   bool have_density = false;
   int n_dens = 1;  // densities loaded (P, P2, Khat hold n_dens packed blocks)
   int ctas_nd = 0;  // density count the persistent grids (max_ctas) were sized for
-  DevBuf<double> P, Pscr, ft, sym, Khat, K;  // Pscr: sum_d |P_d| for the screen of several densities
+  DevBuf<double> P, Pscr, ft, sym, K;  // Pscr: sum_d |P_d| for the screen of several densities
+  DevBuf<unsigned long long> Khat;     // two words per entry (khat_add)
   DevBuf<float2> P2;  // (hi, lo) pairs of P for the double-FP32 GEMM
   DevBuf<int> counts, list, list2, sfunc, colmap, tickets;  // list2: rewrite target of the learned screen
   DevBuf<long long> ppcounts;
@@ -344,8 +345,8 @@ int make_tiles(snk_ctx* c, cudaStream_t st) {
     for (int k = 0; k < kNumLists; ++k) {
       ch.tile_off[k] = tot;
       const int run = c->run[k];
-      if (run < 1 || run > 128)  // the FP32 kernel stages at most 128 pairs per tile
-        return fail(c, SNK_ERR_INVALID_ARG, "pairs per tile outside 1..128");
+      if (run < 1 || run > 128)  // the FP32 kernel stages at most 128 pairs per step
+        return fail(c, SNK_ERR_INVALID_ARG, "pairs per step outside 1..128");
       order.resize(ch.b1 - ch.b0);
       cost.resize(ch.b1 - ch.b0);
       for (int t = ch.b0; t < ch.b1; ++t) {
@@ -357,15 +358,13 @@ int make_tiles(snk_ctx* c, cudaStream_t st) {
       for (int t : order) {
         const int64_t n = c->hcounts[(size_t)t * kNumLists + k];
         tstart[(size_t)t * kNumLists + k] = tot;
-        tot += (n + run - 1) / run * ((bd[t].q + kPointTile - 1) / kPointTile);
+        tot += n > 0 ? (bd[t].q + kPointTile - 1) / kPointTile : 0;  // one tile per slab of points
       }
       ch.tile_n[k] = tot - ch.tile_off[k];
     }
   SNK_CK(c, c->tiles.ensure((size_t)std::max<int64_t>(tot, 1)));
   SNK_CK(c, upload(c->tstart, tstart, st));
-  RunLengths rl;
-  for (int k = 0; k < kNumLists; ++k) rl.run[k] = c->run[k];
-  SNK_CK(c, launch_gen_tiles(st, nb, c->batch.p, c->counts.p, c->list_off.p, c->tstart.p, rl, c->tiles.p));
+  SNK_CK(c, launch_gen_tiles(st, nb, c->batch.p, c->counts.p, c->list_off.p, c->tstart.p, c->tiles.p));
   ++c->launches_density;
   return SNK_OK;
 }
@@ -758,6 +757,8 @@ int screen_and_plan(snk_ctx* c) {
   SNK_CK(c, upload(c->batch, bd, st));
   if (tile_screen(c)) SNK_CK(c, c->tsum.ensure((size_t)need_tsum));
   SNK_CK(c, c->exec.ensure(2 * kNumLists));
+  SNK_CK(c, c->ozerr.ensure(1));  // device error flag of the products and the K accumulator
+  SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), st));
   double tc_flops = 0.0;
   if (tc) {
     if (int rc = plan_tc(c, &tc_flops)) return rc;
@@ -766,7 +767,7 @@ int screen_and_plan(snk_ctx* c) {
 
   if (int rc = make_tiles(c, st)) return rc;
   SNK_CK(c, c->tickets.ensure(c->chunks.size() * kNumLists + 1));
-  SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(c->n_dens * s.packed, 1)));
+  SNK_CK(c, c->Khat.ensure((size_t)std::max<int64_t>(2 * c->n_dens * s.packed, 2)));
   if (mixed && c->opt.gemm != SNK_GEMM_FP64)
     SNK_CK(c, c->P2.ensure((size_t)std::max<int64_t>(c->n_dens * s.packed, 1)));
   SNK_CK(c, cudaEventRecord(c->ev_screen1, st));
@@ -814,7 +815,9 @@ int check_device_flags(snk_ctx* c) {
   if (h == 0) return SNK_OK;
   SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), c->stream));
   SNK_CK(c, cudaStreamSynchronize(c->stream));
-  if (h == 1) return fail(c, SNK_ERR_TIMEOUT, "a tensor-core product kernel gave up waiting on its pipeline");
+  if (h == 1) return fail(c, SNK_ERR_TIMEOUT, "a kernel gave up waiting on its copy or product pipeline");
+  if (h == kErrKhatRange)
+    return fail(c, SNK_ERR_UNSUPPORTED, "a contribution to K reached 2^30 or was not finite (density or basis out of range)");
   return fail(c, SNK_ERR_CUDA, "a tensor-core product kernel found an operand outside its slice arena");
 }
 
@@ -848,6 +851,8 @@ IntegralArgs integral_args(snk_ctx* c, size_t ci, int k) {
   a.eps_tile = (k >= kNumClasses && tile_screen(c)) ? (float)c->opt.eps_tile : 0.f;
   a.exec = c->exec.p + 2 * k;
   a.n_dens = c->n_dens;
+  a.run = c->run[k];
+  a.err = c->ozerr.p;
   return a;
 }
 
@@ -893,7 +898,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
                            (int64_t)c->arena.n, c->ozerr.p);
   };
   SNK_CK(c, mark());
-  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(double) * (size_t)std::max<int64_t>(nd * pk, 1), st));
+  SNK_CK(c, cudaMemsetAsync(c->Khat.p, 0, sizeof(unsigned long long) * 2 * (size_t)std::max<int64_t>(nd * pk, 1), st));
   if (df32) {  // P2 is allocated with the density (no allocation inside a graph capture)
     SNK_CK(c, launch_split_df32_copy(st, c->P.p, nd * pk, c->P2.p));
     ++c->launches_build;
@@ -958,7 +963,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
     } else {
       for (int d = 0; d < nd; ++d) {
         SNK_CK(c, launch_kgemm(st, db, nbc, ch.max_nS, ch.max_nB, c->xfunc.p, c->sfunc.p, c->ws.p,
-                               c->Khat.p + d * pk, gmode, d));
+                               c->Khat.p + 2 * d * pk, gmode, d, c->ozerr.p));
         ++c->launches_build;
       }
     }
@@ -968,7 +973,7 @@ int enqueue_build(snk_ctx* c, cudaStream_t st, double* dK, bool timed) {
   }
   // K_d = (Kt_d + Kt_d^T) / 2 in every molecule block, Eq. (sn_k)
   for (int d = 0; d < nd; ++d) {
-    SNK_CK(c, launch_finish(st, c->mols.p, s.n_mol, s.packed, c->Khat.p + d * pk, c->fcomp.p, dK + d * pk));
+    SNK_CK(c, launch_finish(st, c->mols.p, s.n_mol, s.packed, c->Khat.p + 2 * d * pk, c->fcomp.p, dK + d * pk));
     ++c->launches_build;
   }
   SNK_CK(c, mark());
@@ -1089,8 +1094,9 @@ void collect_times(snk_ctx* c) {
   }
 }
 
-// Autotuner: for every integral list, time the list's kernel on the last
-// chunk's tiles for each candidate run of pairs per tile, keep the fastest.
+// Autotuner: for every FP32 list, time the list's kernel on the last chunk's
+// tiles for each candidate step of staged pairs, keep the fastest (the other
+// kernels read their pairs straight from the list and have no step).
 // The workspace holds that chunk's X and F after a build; the kernel's G
 // output is garbage afterwards, so the caller's next build recomputes it.
 int autotune(snk_ctx* c, int32_t* runs_out) {
@@ -1111,7 +1117,7 @@ int autotune(snk_ctx* c, int32_t* runs_out) {
   cudaEvent_t e0, e1;
   SNK_CK(c, cudaEventCreate(&e0));
   SNK_CK(c, cudaEventCreate(&e1));
-  for (int k = 0; k < kNumLists; ++k) {
+  for (int k = kNumClasses; k < kNumLists; ++k) {
     if (c->chunks[ci].tile_n[k] == 0) continue;
     double best = 1e300;
     int best_run = c->run[k];
@@ -1167,7 +1173,7 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
       c->opt.tc_slices_hi < 3 || c->opt.tc_slices_hi > 6 ||
       c->opt.tc_slices_lo < 3 || c->opt.tc_slices_lo > 6 || !(c->opt.eps_tile >= 0.0))
     return SNK_ERR_INVALID_ARG;
-  for (int k = 0; k < kNumLists; ++k) c->run[k] = kPairsPerTile[k % kNumClasses] * (k >= kNumClasses ? 2 : 1);
+  for (int k = 0; k < kNumLists; ++k) c->run[k] = kDefaultStep;
   int rc = build_setup(n_mol, bases, grids, &c->opt, &c->s, &c->err);
   if (rc != SNK_OK) return rc;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -1180,6 +1186,7 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
   c->ws_budget = c->opt.workspace_bytes > 0 ? c->opt.workspace_bytes : (int64_t)(fr / 2);
   Setup& s = c->s;
   c->nbatch = (int)s.bstart.size() - 1;
+  if (c->nbatch > kKhatMaxBatches) return SNK_ERR_UNSUPPORTED;  // the K accumulator's low word would overflow
   // local X columns of the B_j shells
   s.bshell_col.resize(s.bshell.size());
   for (int j = 0; j < c->nbatch; ++j) {

@@ -17,6 +17,32 @@ constexpr int kNumLists = 2 * kNumClasses;  // per batch: FP64 lists, then FP32 
 constexpr int kPointTile = 128;  // grid points per integral tile (one per thread)
 constexpr int kLdqAlign = 128;   // leading-dimension padding of batch matrices
 
+// K-hat accumulator: every entry is a pair of 64-bit integers (hi, lo) worth
+// hi 2^-32 + lo 2^-76.  Integer additions are exact and
+// associative, so the sum of the batches' contributions does not depend on
+// the order in which they arrive (K is the same bit for bit from run to run).
+// A contribution v is cut as hi = rint(v 2^32), lo = rint((v - hi 2^-32) 2^76):
+// |v| < 2^30, |lo| <= 2^43 (sums of up to 2^19 batches stay below 2^62), and
+// what is dropped is below 2^-77 ~ 7e-24 per contribution.
+constexpr int kKhatMaxBatches = 1 << 19;
+constexpr int kErrKhatRange = 3;  // device error flag: a contribution outside |v| < 2^30
+#ifdef __CUDACC__
+__device__ __forceinline__ void khat_add(unsigned long long* e, double v, int* err) {
+  if (!(fabs(v) < 0x1p30)) {  // and NaN
+    if (err) atomicExch(err, kErrKhatRange);
+    return;
+  }
+  const long long hi = __double2ll_rn(v * 0x1p32);
+  const double r = fma(-(double)hi, 0x1p-32, v);  // exact: v - hi 2^-32
+  const long long lo = __double2ll_rn(r * 0x1p76);
+  atomicAdd(e, (unsigned long long)hi);
+  atomicAdd(e + 1, (unsigned long long)lo);
+}
+__device__ __forceinline__ double khat_value(const unsigned long long* e) {
+  return (double)(long long)e[0] * 0x1p-32 + (double)(long long)e[1] * 0x1p-76;
+}
+#endif
+
 // Boys table: rows T_k = k * kBoysH, k = 0..kBoysRows-1; for T >= kBoysTMax the
 // asymptotic form is used.  One table per L = 0..4 with kBoysCols doubles per
 // row: F_{L+m}(T_k)/m! for m = 0..7, exp(-T_k), T_k.
@@ -109,14 +135,10 @@ struct MolDesc {
   int32_t pad;
 };
 
-// Integral-kernel tile: batch, pair-list range, first point.
+// Integral-kernel tile: batch, pair-list range (the batch's whole list),
+// first point.
 struct Tile {
   int32_t batch, k0, k1, i0;
-};
-
-// Pairs per tile of each of the kNumLists lists (kernel argument by value).
-struct RunLengths {
-  int32_t run[kNumLists];
 };
 
 // ---------------------------------------------------------------- host setup
@@ -225,7 +247,8 @@ cudaError_t launch_pair_count(cudaStream_t st, const ScreenArgs& a, int nbatch, 
                               unsigned char* sflag, int64_t hflag_off);
 cudaError_t launch_pair_write(cudaStream_t st, const ScreenArgs& a, int nbatch, const int64_t* list_off, int* list);
 // P, Khat and K below are the packed molecule blocks (BatchDesc::pk_off,
-// MolDesc::pk_off); xfunc / sfunc hold molecule-local function indices.
+// MolDesc::pk_off; Khat holds two words per entry, see khat_add); xfunc /
+// sfunc hold molecule-local function indices.
 // mode: 0 FP64, 2 double-FP32 (X, G and P2 then hold (hi, lo) float pairs in
 // place of the doubles, see launch_split_df32).  dens: which density's F / G
 // block of each batch (at foff / goff + dens ldq nS).
@@ -233,14 +256,15 @@ cudaError_t launch_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, i
                          const double* P, const float2* P2, const int* xfunc, const int* sfunc,
                          const double* fcomp, const double* w, double* ws, float* ws32, int mode, int dens);
 cudaError_t launch_kgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nS, int max_nB,
-                         const int* xfunc, const int* sfunc, const double* ws, double* Khat, int mode, int dens);
+                         const int* xfunc, const int* sfunc, const double* ws, unsigned long long* Khat, int mode,
+                         int dens, int* err);
 // In place, each double of buf[0, n) becomes the float pair (fl32(v), fl32(v - fl32(v))).
 cudaError_t launch_split_df32(cudaStream_t st, double* buf, int64_t n);
 cudaError_t launch_split_df32_copy(cudaStream_t st, const double* src, int64_t n, float2* dst);
 // out = sum_d |P_d| over n_dens consecutive arrays of n doubles.
 cudaError_t launch_abs_sum(cudaStream_t st, const double* P, int n_dens, int64_t n, double* out);
-cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* Khat,
-                          const double* fcomp, double* K);
+cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed,
+                          const unsigned long long* Khat, const double* fcomp, double* K);
 cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* P,
                             double* out2);
 
@@ -283,6 +307,8 @@ struct IntegralArgs {
   const double* shell_xyz;
   float eps_tile;
   unsigned long long* exec;  // FP32 lists: += (primitive pairs x points, pairs x points) computed
+  int run;                   // FP32 lists: pairs staged (and tile-screened) per step, 1..kMaxRun
+  int* err;                  // set to 1 when a bounded wait on a copy ran out
 };
 
 cudaError_t launch_integrals(cudaStream_t st, int cls, const IntegralArgs& a, int grid_ctas);
@@ -299,7 +325,7 @@ void class_flops(int cls, double* per_prim, double* per_pair);
 // Tiles of every (batch, list): ceil(count / run) runs x ceil(q / 128) slabs,
 // the (batch, list)'s tiles from tiles[tstart[batch * kNumLists + list]] on.
 cudaError_t launch_gen_tiles(cudaStream_t st, int nbatch, const BatchDesc* batches, const int* counts,
-                             const int64_t* list_off, const int64_t* tstart, RunLengths runs, Tile* tiles);
+                             const int64_t* list_off, const int64_t* tstart, Tile* tiles);
 
 // ---------------------------------------------------------------- split-product tensor-core GEMMs
 
@@ -318,7 +344,7 @@ struct OzSplitJob {
 // operands at a_off / b_off (RTa / RTb row blocks, KT reduction blocks, Sa /
 // Sb slices stored per block); its RTa x RTb tiles are numbered from tile0.
 //   kind 0: F[(c0 + n) ldq + m] = w_m f_{c0+n} C (doubles at ws + out_off, floats at ws32 + out_off32)
-//   kind 1: Khat[out_off + sfunc[c0 + m] N_b,m + xfunc[n]] += C
+//   kind 1: Khat[out_off + sfunc[c0 + m] N_b,m + xfunc[n]] += C (entries of two words, khat_add)
 //   kind 2: ws[out_off + m ldc + n] = C (test export)
 struct OzGemmJob {
   int64_t a_off, b_off, out_off, out_off32;
@@ -337,8 +363,8 @@ struct OzGemmArgs {
   const int* xfunc;
   double* ws;
   float* ws32;
-  double* Khat;
-  int* err;  // set to 1 when a wait ran out, 2 when an operand lay outside the arena
+  unsigned long long* Khat;
+  int* err;  // set to 1 when a wait ran out, 2 when an operand lay outside the arena, kErrKhatRange
 };
 
 int64_t oz_operand_bytes(int rows, int k, int slices);

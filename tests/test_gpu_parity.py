@@ -319,16 +319,30 @@ def test_tile_screen(snk):
         snk.Engine(p.basis, p.grid, eps_tile=-1.0, **form)
 
 
-def test_fp32_tier_run_to_run(snk):
-    """The FP32 pairs add into the FP64 G with FP64 atomics, so repeated
-    builds of the mixed form differ only by FP64 summation order."""
+@pytest.mark.parametrize("form", [
+    dict(),                                                            # plain FP64
+    dict(precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="df32"),
+    dict(precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="split", eps_tile=1e-11),
+    dict(precision="mixed", fp32_bound=1e-3, ds_integrals=1, gemm="split", workspace_bytes=1 << 20),
+])
+def test_builds_are_bitwise_reproducible(snk, form):
+    """Every G entry of an integral launch has one writer whose additions come
+    in list order, and K-hat sums the batches' contributions as exact 64-bit
+    integers: repeated builds, and builds on a fresh handle (another ticket
+    order of the persistent CTAs), give the same K bit for bit."""
     p = synth.cluster(12, 77, n_r=16, n_theta=4, n_phi=9, n_occ=10)
-    eng = snk.Engine(p.basis, p.grid, batch_max=300, precision="mixed", fp32_bound=1e-3, ds_integrals=1,
-                     gemm="split")
-    eng.set_density(p.P)
-    Ks = [eng.build_K() for _ in range(3)]
-    eng.close()
-    assert max(np.max(np.abs(K - Ks[0])) for K in Ks[1:]) <= 1e-13
+    Ks = []
+    for _ in range(2):
+        eng = snk.Engine(p.basis, p.grid, batch_max=300, **form)
+        eng.set_density(p.P)
+        Ks += [eng.build_K() for _ in range(2)]
+        st = eng.stats()
+        eng.close()
+    for K in Ks[1:]:
+        assert np.array_equal(K, Ks[0])
+    assert np.max(np.abs(Ks[0] - Ks[0].T)) == 0.0
+    if "workspace_bytes" in form:
+        assert st["n_chunks"] > 1
 
 
 def test_two_densities_in_one_build(snk, chain4):
