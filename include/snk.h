@@ -369,6 +369,14 @@ int snk_debug_pair_bound(snk_ctx *ctx, int32_t sa, int32_t sb, double *bound);
 int snk_debug_tc_gemm(int32_t M, int32_t N, int32_t K, const double *A, const double *B, int32_t slices,
                       double *C);
 
+/* Failure path of the bounded device waits: one thread waits, with the wait
+ * the library's copy and product pipelines use, on a shared-memory mbarrier
+ * that nothing completes.  After limit_ns (1 .. 2e9 ns) it gives up and sets
+ * the handle's device error flag, and the call returns what a build reports
+ * in that case, SNK_ERR_TIMEOUT (SNK_ERR_INVALID_ARG for a limit out of
+ * range).  The handle stays usable. */
+int snk_debug_wait_timeout(snk_ctx *ctx, int64_t limit_ns);
+
 /* Octree batches: n_batches, then for each batch the point count; the
  * permutation from batch order to input order (n_points entries). */
 int snk_debug_batches(snk_ctx *ctx, int64_t *n_batches, int32_t *counts, int64_t counts_cap,

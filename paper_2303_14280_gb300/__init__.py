@@ -46,7 +46,8 @@ SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molec
            "snk_n_functions", "snk_last_error", "snk_status_string", "snk_destroy", "snk_debug_boys",
            "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc",
            "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad",
-           "snk_set_density_multi", "snk_build_K_multi", "snk_set_allocator", "snk_debug_tc_gemm"]
+           "snk_set_density_multi", "snk_build_K_multi", "snk_set_allocator", "snk_debug_tc_gemm",
+           "snk_debug_wait_timeout"]
 MLP_FEATURES, MLP_WEIGHTS = 16, 9473
 MAX_DENSITIES = 2
 
@@ -148,6 +149,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
                                             _D]
             L.snk_debug_shell_A.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _D, _D]
             L.snk_debug_pair_bound.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _D]
+            L.snk_debug_wait_timeout.argtypes = [_P, ctypes.c_int64]
             L.snk_debug_batches.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), _I32, ctypes.c_int64,
                                             ctypes.POINTER(ctypes.c_int64)]
             L.snk_shell_A_noalloc.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P]
@@ -476,8 +478,13 @@ class Engine:
                     "snk_learn_collect")
         return feat[:n.value].copy(), lab[:n.value].copy()
 
+    def debug_wait_timeout(self, limit_ns: int) -> int:
+        """snk_debug_wait_timeout: the status a build reports when a bounded
+        device wait runs out (SNK_ERR_TIMEOUT), from a wait nothing completes."""
+        return int(lib().snk_debug_wait_timeout(self._h, int(limit_ns)))
+
     def autotune(self) -> dict:
-        """snk_autotune: pairs per tile chosen for each integral list."""
+        """snk_autotune: FP32-list pairs per staging step chosen for each list."""
         runs = (ctypes.c_int32 * 12)()
         self._check(lib().snk_autotune(self._h, runs), "snk_autotune")
         names = [f"fp64_{n}" for n in LISTS] + [f"fp32_{n}" for n in LISTS]

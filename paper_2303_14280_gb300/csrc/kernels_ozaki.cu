@@ -642,4 +642,19 @@ cudaError_t launch_oz_gemm(cudaStream_t st, int slices, const OzGemmArgs& args, 
   }
 }
 
+// The failure path of the bounded waits: an mbarrier expecting one arrival
+// that never comes; the wait gives up after limit_ns and sets *err.
+__global__ void wait_probe_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  mbar_wait(&bar, 0, err, limit_ns);
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+}
+
+cudaError_t launch_wait_probe(cudaStream_t st, int* err, unsigned long long limit_ns) {
+  wait_probe_kernel<<<1, 1, 0, st>>>(err, limit_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace snk

@@ -1626,6 +1626,15 @@ int snk_debug_shell_A(snk_ctx* c, int32_t sa, int32_t sb, int64_t n, const doubl
   return SNK_OK;
 }
 
+int snk_debug_wait_timeout(snk_ctx* c, int64_t limit_ns) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (limit_ns < 1 || limit_ns > 2000000000LL) return fail(c, SNK_ERR_INVALID_ARG, "limit_ns outside 1..2e9");
+  SNK_CK(c, c->ozerr.ensure(1));
+  SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), c->stream));
+  SNK_CK(c, launch_wait_probe(c->stream, c->ozerr.p, (unsigned long long)limit_ns));
+  return check_device_flags(c);
+}
+
 int snk_debug_tc_gemm(int32_t M, int32_t N, int32_t K, const double* A, const double* B, int32_t slices,
                       double* C) {
   if (M < 0 || N < 0 || K < 0 || slices < 3 || slices > 6 || (M * (int64_t)K > 0 && !A) ||

@@ -375,6 +375,8 @@ cudaError_t launch_oz_split(cudaStream_t st, const OzSplitJob* jobs, int n_jobs,
                             int64_t arena_bytes, int* err);
 // slices: 3..6 (products of slice pairs i + j < slices)
 cudaError_t launch_oz_gemm(cudaStream_t st, int slices, const OzGemmArgs& args, int num_sms);
+// one thread waits (bounded by limit_ns) on an mbarrier nothing completes: *err = 1
+cudaError_t launch_wait_probe(cudaStream_t st, int* err, unsigned long long limit_ns);
 
 // learned screen
 cudaError_t launch_labels(cudaStream_t st, int cls, const IntegralArgs& a, int grid, const int64_t* slot_base,
