@@ -36,4 +36,4 @@ def test_golden_error_over_the_stored_entries():
     assert bench.golden_err("cluster96", K) == 0.0
     K[mu[7], nu[7]] += 3e-9
     assert abs(bench.golden_err("cluster96", K) - 3e-9) < 1e-15
-    assert bench.golden_err("cluster512", K) is None     # no stored entries for this workload
+    assert bench.golden_err("cluster24", K) is None      # no stored entries for this workload
