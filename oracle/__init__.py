@@ -64,10 +64,14 @@ def lib():
                                                             _I, _I, _D, ctypes.c_int]
             L.oracle_g_rows.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int, _I, _D,
                                                      ctypes.c_int]
+            L.oracle_xc_point.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
+            L.oracle_collocation_grad.argtypes = basis_args + [ctypes.c_long, _D, _D, _D]
+            L.oracle_vxc.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int, _D, _D, ctypes.c_int]
             L.oracle_mlp_forward.argtypes = [_D, _D, ctypes.c_long, _D]
             L.oracle_mlp_loss_grad.argtypes = [_D, _D, _D, ctypes.c_long, ctypes.c_double, _D, _D]
             for name in ("oracle_normalise", "oracle_collocation", "oracle_shell_A", "oracle_eri_K",
-                         "oracle_snk_K", "oracle_snk_K_entries", "oracle_g_rows", "oracle_mlp_forward", "oracle_mlp_loss_grad"):
+                         "oracle_snk_K", "oracle_snk_K_entries", "oracle_g_rows", "oracle_mlp_forward", "oracle_mlp_loss_grad",
+                         "oracle_xc_point", "oracle_collocation_grad", "oracle_vxc"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -241,3 +245,42 @@ def mlp_loss_grad(w, X, Y, under_weight=4.0):
     _check(lib().oracle_mlp_loss_grad(_dp(w), _dp(X), _dp(Y), ctypes.c_long(X.shape[0]), float(under_weight),
                                       _dp(g), _dp(loss)), "mlp_loss_grad")
     return float(loss[0]), g
+
+
+# ---------------------------------------------------------------- exchange-correlation (Sec. II.C)
+
+XC_LDA_X, XC_PBE_X, XC_PBE = 1, 2, 3
+
+
+def xc_point(functional: int, rho: float, sigma: float) -> np.ndarray:
+    """(eps, d eps / d rho, d eps / d sigma) of a spin-restricted functional
+    (1 Slater exchange, 2 PBE exchange, 3 PBE exchange + correlation); eps is
+    the energy per volume, sigma = |grad rho|^2 (Eq. exc_grid)."""
+    out = np.zeros(3)
+    _check(lib().oracle_xc_point(int(functional), float(rho), float(sigma), _dp(out)), "xc_point")
+    return out
+
+
+def collocation_grad(basis, xyz):
+    """Phi (npts, nf) and grad Phi (npts, 3, nf) at the points (Eq. collocation)."""
+    arrs, args = _basis_args(basis)
+    xyz = _f64(xyz).reshape(-1, 3)
+    nf = sum(ncart(int(x)) for x in arrs[0])
+    phi = np.zeros((xyz.shape[0], nf))
+    gphi = np.zeros((xyz.shape[0], 3, nf))
+    _check(lib().oracle_collocation_grad(*args, ctypes.c_long(xyz.shape[0]), _dp(xyz), _dp(phi), _dp(gphi)),
+           "collocation_grad")
+    return phi, gphi
+
+
+def vxc(basis, grid, P, functional: int, nthreads: int = 0):
+    """(V^xc, E_xc) of the symmetric density matrix P on the grid: Eqs. fmat,
+    den_grid, exc_grid, zmat and vxc_num, point by point, no screening."""
+    arrs, args = _basis_args(basis)
+    xyz, w, P = _f64(grid.xyz), _f64(grid.w), _f64(P)
+    nf = P.shape[0]
+    V = np.zeros((nf, nf))
+    E = np.zeros(1)
+    _check(lib().oracle_vxc(*args, ctypes.c_long(w.shape[0]), _dp(xyz), _dp(w), _dp(P), int(functional), _dp(V),
+                            _dp(E), int(nthreads)), "vxc")
+    return V, float(E[0])

@@ -23,6 +23,10 @@
  *   Ktilde = G Phi^T                Sec. II.D, Eq. (usym_k)
  *   K = (Ktilde + Ktilde^T)/2       Sec. II.D, Eq. (sn_k)
  *   exact K from ERIs               Sec. II.A, Eq. (full_k)
+ *   V^xc and E_xc (GGA)             Sec. II.C, Eqs. (vxc_num), (zmat), (exc_grid),
+ *                                   (den_grid), (fmat), with Slater, PBE exchange
+ *                                   and PBE correlation written from their
+ *                                   published definitions
  *
  * Readings where the paper is silent or garbled:
  *   - the seed of the VRR carries the standard nuclear-attraction prefactor
@@ -857,5 +861,214 @@ int oracle_mlp_loss_grad(const double *w, const double *X, const double *Y, long
       for (int k = 0; k < ORC_NIN; ++k) grad[off[0] + k * ORC_NH + m] += x[k] * d[0][m];
     }
   }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* exchange-correlation potential, Sec. II.C                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * Spin-restricted functionals eps(rho, sigma), sigma = |grad rho|^2, as an
+ * energy per volume (E_xc = sum_i w_i eps(rho_i, sigma_i)), with the two
+ * partial derivatives Eq. (exc_grid) needs.  The paper takes its functionals
+ * from a library; these are written from their published definitions:
+ *   1  Slater (LDA) exchange     eps = C_x rho^{4/3}, C_x = -(3/4)(3/pi)^{1/3}
+ *   2  PBE exchange              eps = C_x rho^{4/3} F_x(s),
+ *                                F_x = 1 + kappa - kappa / (1 + mu s^2 / kappa),
+ *                                s = |grad rho| / (2 k_F rho), k_F = (3 pi^2 rho)^{1/3}
+ *   3  PBE exchange + PBE correlation: rho (e_c^PW92(r_s) + H(r_s, t)),
+ *                                r_s = (3 / (4 pi rho))^{1/3}, t = |grad rho| / (2 k_s rho),
+ *                                k_s = sqrt(4 k_F / pi),
+ *                                H = gamma ln(1 + (beta/gamma) t^2 (1 + A t^2) / (1 + A t^2 + A^2 t^4)),
+ *                                A = (beta/gamma) / (exp(-e_c^PW92 / gamma) - 1)
+ * PW92 (unpolarised): e_c = -2 a (1 + alpha_1 r_s) ln(1 + 1 / Q),
+ *                     Q = 2 a (beta_1 r_s^{1/2} + beta_2 r_s + beta_3 r_s^{3/2} + beta_4 r_s^2).
+ * Points with rho below ORC_XC_RHO_MIN contribute nothing.
+ */
+#define ORC_XC_RHO_MIN 1e-14
+#define ORC_PBE_KAPPA 0.804
+#define ORC_PBE_BETA 0.06672455060314922
+#define ORC_PW92_A 0.031091
+#define ORC_PW92_ALPHA1 0.21370
+#define ORC_PW92_B1 7.5957
+#define ORC_PW92_B2 3.5876
+#define ORC_PW92_B3 1.6382
+#define ORC_PW92_B4 0.49294
+
+/* PW92 correlation energy per electron and its derivative in r_s */
+static void pw92(double rs, double *ec, double *dec_drs) {
+  const double a = ORC_PW92_A, srs = sqrt(rs);
+  const double Q = 2.0 * a * (ORC_PW92_B1 * srs + ORC_PW92_B2 * rs + ORC_PW92_B3 * rs * srs + ORC_PW92_B4 * rs * rs);
+  const double dQ = 2.0 * a * (0.5 * ORC_PW92_B1 / srs + ORC_PW92_B2 + 1.5 * ORC_PW92_B3 * srs + 2.0 * ORC_PW92_B4 * rs);
+  const double lg = log(1.0 + 1.0 / Q);
+  *ec = -2.0 * a * (1.0 + ORC_PW92_ALPHA1 * rs) * lg;
+  *dec_drs = -2.0 * a * ORC_PW92_ALPHA1 * lg + 2.0 * a * (1.0 + ORC_PW92_ALPHA1 * rs) * dQ / (Q * (Q + 1.0));
+}
+
+/* out[0] = eps, out[1] = d eps / d rho, out[2] = d eps / d sigma */
+int oracle_xc_point(int functional, double rho, double sigma, double *out) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (functional < 1 || functional > 3) return -1;
+  if (!(rho >= ORC_XC_RHO_MIN)) return 0;
+  if (sigma < 0.0) sigma = 0.0;
+  const double Cx = -0.75 * cbrt(3.0 / ORC_PI);
+  const double r13 = cbrt(rho), r43 = rho * r13;
+  if (functional == 1) {
+    out[0] = Cx * r43;
+    out[1] = 4.0 / 3.0 * Cx * r13;
+    return 0;
+  }
+  /* PBE exchange */
+  const double kappa = ORC_PBE_KAPPA, mu = ORC_PBE_BETA * ORC_PI * ORC_PI / 3.0;
+  const double kF = cbrt(3.0 * ORC_PI * ORC_PI * rho);
+  const double ds2_dsigma = 1.0 / (4.0 * kF * kF * rho * rho);   /* s^2 = sigma ds2_dsigma */
+  const double s2 = sigma * ds2_dsigma;
+  const double den = 1.0 + mu * s2 / kappa;
+  const double Fx = 1.0 + kappa - kappa / den;
+  const double dFx = mu / (den * den);                             /* dF_x / d(s^2) */
+  out[0] = Cx * r43 * Fx;
+  out[1] = 4.0 / 3.0 * Cx * r13 * Fx + Cx * r43 * dFx * (-8.0 / 3.0) * s2 / rho;
+  out[2] = Cx * r43 * dFx * ds2_dsigma;
+  if (functional == 2) return 0;
+  /* PBE correlation */
+  const double gam = (1.0 - log(2.0)) / (ORC_PI * ORC_PI), beta = ORC_PBE_BETA;
+  const double rs = cbrt(3.0 / (4.0 * ORC_PI * rho));
+  double ec, dec_drs;
+  pw92(rs, &ec, &dec_drs);
+  const double dec_drho = dec_drs * (-rs / (3.0 * rho));
+  const double ks2 = 4.0 * kF / ORC_PI;
+  const double dy_dsigma = 1.0 / (4.0 * ks2 * rho * rho);          /* y = t^2 = sigma dy_dsigma */
+  const double y = sigma * dy_dsigma;
+  const double E = exp(-ec / gam);
+  const double A = beta / gam / (E - 1.0);
+  const double N = 1.0 + A * y, D = 1.0 + A * y + A * A * y * y;
+  const double R = y * N / D;
+  const double arg = 1.0 + beta / gam * R;
+  const double H = gam * log(arg);
+  const double dH_dR = beta / arg;
+  const double dR_dy = (N + A * y) / D - y * N * (A + 2.0 * A * A * y) / (D * D);
+  const double dR_dA = y * y / D - y * N * (y + 2.0 * A * y * y) / (D * D);
+  const double dA_dec = A * A * E / beta;
+  const double dy_drho = -7.0 / 3.0 * y / rho;
+  out[0] += rho * (ec + H);
+  out[1] += ec + H + rho * (dec_drho * (1.0 + dH_dR * dR_dA * dA_dec) + dH_dR * dR_dy * dy_drho);
+  out[2] += rho * dH_dR * dR_dy * dy_dsigma;
+  return 0;
+}
+
+/* Phi and its gradient at one point: phi[nf], gphi[3 nf] (x, y, z blocks) */
+static void collocate_grad_point(const obasis *b, const double r[3], double *phi, double *gphi) {
+  const int nf = b->n_func;
+  for (int s = 0; s < b->n_shells; ++s) {
+    const double *A = b->center + 3 * s;
+    double d[3] = {r[0] - A[0], r[1] - A[1], r[2] - A[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double R0 = 0.0, R1 = 0.0; /* sum_k d_k e^{-a r^2}, sum_k (-2 a_k) d_k e^{-a r^2} */
+    for (int k = b->poff[s]; k < b->poff[s + 1]; ++k) {
+      double e = b->d[k] * exp(-b->exps[k] * r2);
+      R0 += e;
+      R1 += -2.0 * b->exps[k] * e;
+    }
+    int c[6][3];
+    cart_list(b->l[s], c);
+    for (int i = 0; i < ncart(b->l[s]); ++i) {
+      const int mu = b->foff[s] + i;
+      const double f = comp_factor(b->l[s], c[i]);
+      const double mono = pow(d[0], c[i][0]) * pow(d[1], c[i][1]) * pow(d[2], c[i][2]);
+      phi[mu] = f * mono * R0;
+      for (int q = 0; q < 3; ++q) {
+        /* d/dq of x^a y^b z^c R(r): a_q q^{a_q - 1} (others) R + (monomial) q R1 */
+        double dm = 0.0;
+        if (c[i][q] > 0) {
+          dm = c[i][q];
+          for (int p = 0; p < 3; ++p) dm *= pow(d[p], c[i][p] - (p == q ? 1 : 0));
+        }
+        gphi[q * nf + mu] = f * (dm * R0 + mono * d[q] * R1);
+      }
+    }
+  }
+}
+
+int oracle_collocation_grad(int n_shells, const int *l, const int *nprim, const double *center,
+                            const double *exps, const double *coefs, long npts, const double *xyz,
+                            double *phi /* npts x nf */, double *gphi /* npts x 3 x nf */) {
+  obasis b;
+  if (obasis_init(&b, n_shells, l, nprim, center, exps, coefs)) return -1;
+  for (long i = 0; i < npts; ++i)
+    collocate_grad_point(&b, xyz + 3 * i, phi + i * b.n_func, gphi + i * 3 * b.n_func);
+  obasis_free(&b);
+  return 0;
+}
+
+/* V^xc and E_xc for a symmetric density matrix P, point by point:
+ *   Phi, grad Phi                                  Eq. (collocation)
+ *   F_mu = sum_nu P_{mu nu} Phi_nu                 Eq. (fmat)
+ *   rho = sum_mu F_mu Phi_mu,
+ *   grad rho = 2 sum_mu F_mu grad Phi_mu           Eq. (den_grid)
+ *   eps, d eps/d rho, d eps/d sigma                Eq. (exc_grid)
+ *   Z_mu = w/2 (eps_rho Phi_mu + 4 eps_sigma grad rho . grad Phi_mu)   Eq. (zmat)
+ *   V_{mu nu} += Phi_mu Z_nu + Z_mu Phi_nu         Eq. (vxc_num)
+ *   E_xc += w eps */
+int oracle_vxc(int n_shells, const int *l, const int *nprim, const double *center, const double *exps,
+               const double *coefs, long npts, const double *xyz, const double *w, const double *Pm,
+               int functional, double *V, double *Exc, int nthreads) {
+  if (functional < 1 || functional > 3) return -2;
+  obasis b;
+  if (obasis_init(&b, n_shells, l, nprim, center, exps, coefs)) return -1;
+  int nf = b.n_func, nt = n_threads_or_default(nthreads);
+  double *Vt = (double *)calloc((size_t)nt * nf * nf, sizeof(double));
+  double *Et = (double *)calloc((size_t)nt, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    int tid = omp_get_thread_num();
+#else
+    int tid = 0;
+#endif
+    double *phi = (double *)malloc(sizeof(double) * nf);
+    double *gphi = (double *)malloc(sizeof(double) * 3 * nf);
+    double *F = (double *)malloc(sizeof(double) * nf);
+    double *Z = (double *)malloc(sizeof(double) * nf);
+    double *Vl = Vt + (size_t)tid * nf * nf;
+#pragma omp for schedule(static)
+    for (long i = 0; i < npts; ++i) {
+      collocate_grad_point(&b, xyz + 3 * i, phi, gphi);
+      for (int mu = 0; mu < nf; ++mu) {
+        double s = 0.0;
+        for (int nu = 0; nu < nf; ++nu) s += Pm[mu * nf + nu] * phi[nu];
+        F[mu] = s;
+      }
+      double rho = 0.0, g[3] = {0.0, 0.0, 0.0};
+      for (int mu = 0; mu < nf; ++mu) {
+        rho += F[mu] * phi[mu];
+        for (int q = 0; q < 3; ++q) g[q] += 2.0 * F[mu] * gphi[q * nf + mu];
+      }
+      double e[3];
+      oracle_xc_point(functional, rho, g[0] * g[0] + g[1] * g[1] + g[2] * g[2], e);
+      if (!(rho >= ORC_XC_RHO_MIN)) continue;
+      Et[tid] += w[i] * e[0];
+      for (int mu = 0; mu < nf; ++mu) {
+        double gg = g[0] * gphi[mu] + g[1] * gphi[nf + mu] + g[2] * gphi[2 * nf + mu];
+        Z[mu] = 0.5 * w[i] * (e[1] * phi[mu] + 4.0 * e[2] * gg);
+      }
+      for (int mu = 0; mu < nf; ++mu)
+        for (int nu = 0; nu < nf; ++nu) Vl[mu * nf + nu] += phi[mu] * Z[nu] + Z[mu] * phi[nu];
+    }
+    free(phi);
+    free(gphi);
+    free(F);
+    free(Z);
+  }
+  for (int x = 0; x < nf * nf; ++x) {
+    double s = 0.0;
+    for (int t = 0; t < nt; ++t) s += Vt[(size_t)t * nf * nf + x];
+    V[x] = s;
+  }
+  double es = 0.0;
+  for (int t = 0; t < nt; ++t) es += Et[t];
+  *Exc = es;
+  free(Vt);
+  free(Et);
+  obasis_free(&b);
   return 0;
 }
