@@ -372,6 +372,41 @@ def timed(runner, steps, warmup, stream, barrier):
     return e0.elapsed_time(e1), acc
 
 
+def measure_vxc(eng, P, stream, reps=2):
+    """V^xc (Sec. II.C) of the loaded density on the same handle: PBE builds
+    timed with CUDA events on the library stream (one warm-up), the library's
+    phase times, and the Slater homogeneity check tr(V P) = 4/3 E_x."""
+    import torch
+    dV = torch.empty((eng.nf, eng.nf), dtype=torch.float64, device=P.device)
+    pbe = 3
+    eng.build_Vxc(pbe, out=dV)                         # warm-up (plans the batches once)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ph = dict(ms_xc_collocation=0.0, ms_xc_fgemm=0.0, ms_xc_point=0.0, ms_xc_vgemm=0.0)
+    e0.record(stream)
+    for _ in range(reps):
+        _, Exc = eng.build_Vxc(pbe, out=dV)
+        st = eng.stats()
+        for k in ph:
+            ph[k] += st[k] / reps
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    V, Ex = eng.build_Vxc(1)
+    Pn = P.cpu().numpy()
+    hom = abs(float(np.sum(V * Pn)) - 4.0 / 3.0 * Ex) / abs(Ex)
+    gms = ph["ms_xc_fgemm"] + ph["ms_xc_vgemm"]
+    out = {"functional": "PBE (exchange + PW92/PBE correlation), spin-restricted", "ms_per_build": ms,
+           "builds_per_s": 1e3 / ms, "E_xc": Exc, "phases_ms": ph,
+           "slater_homogeneity_rel_err": hom, "gemm_flops": st["xc_gemm_flops"]}
+    if gms > 0:
+        a = st["xc_gemm_flops"] / (gms * 1e-3) / 1e12
+        out["products"] = {"achieved": a, "unit": "TFLOP/s (FP64-equivalent)", "bound": "alu"}
+    if ph["ms_xc_collocation"] > 0:
+        out["collocation_gbs"] = st["xc_colloc_bytes"] / (ph["ms_xc_collocation"] * 1e-3) / 1e9
+    return out
+
+
 def subset_atoms(p, k):
     """Every k-th atom of the molecule in a cost-stratified order (heavy atoms
     first, each kind by distance from the centre), starting at k // 2."""
@@ -533,6 +568,7 @@ def main():
     e2e_value = job_throughput(e2e_s * 1e3, e2e_steps, world, n_mol if batch else 1)
     nbytes = sum(p.P.nbytes for p in probs)
     ch_create = ch.create_s
+    vxc = measure_vxc(ch.engs[0], ch.P[0], stream) if not batch else None
     ch.close()
 
     # ---- plain FP64 beside it: the full build, or its stated subset scaled to the full build
@@ -676,12 +712,18 @@ def main():
         "fp32_pair_points_computed_fraction": (acc["pair_points_fp32"] / acc["pair_points_fp32_listed"]
                                                if acc.get("pair_points_fp32_listed") else None),
         "create_s": ch_create,
+        "vxc": vxc,
         "roofline": roof,
         "clocks": clocks,
         "gpu_launches": int(acc["kernel_launches"]),
         "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps},
     }
+    if vxc and "products" in vxc:      # double-FP32 tiles in the mixed form, FP64 tiles otherwise
+        mixed = chosen_opts.get("precision") == "mixed"
+        peak = FP32_PEAK / DF32_OPS_PER_MAC if mixed else FP64_PEAK
+        vxc["products"].update(peak=peak, frac=vxc["products"]["achieved"] / peak,
+                               tiles="double-FP32" if mixed else "FP64")
     if batch:
         line["autotuned_pairs_per_tile"] = ch.runs
         line["phases_ms_per_step"] = None   # graph replay: no per-phase events

@@ -193,6 +193,12 @@ typedef struct {
                                   (after the tile screen; integrals_fp32 and
                                   flops_fp32 count the same work)                  */
   double pair_points_fp32_listed; /* the same before the tile screen               */
+  double ms_xc_collocation;    /* last snk_build_Vxc: Phi and grad Phi               */
+  double ms_xc_fgemm;          /*   F = X P                                           */
+  double ms_xc_point;          /*   density, functional and Z                        */
+  double ms_xc_vgemm;          /*   V-hat += Z^T X and the symmetrisation            */
+  double xc_gemm_flops;        /*   flops of its two products (2 |Q_j| |B_j|^2 each) */
+  double xc_colloc_bytes;      /*   bytes of Phi and grad Phi written (4 x 8 ldq_j |B_j|) */
 } snk_stats;
 
 /* Fill *opt with the defaults: eps_basis = eps_E = eps_K = 1e-12,
@@ -255,6 +261,34 @@ int snk_build_K_batch(snk_ctx *ctx, double *const *K);
 enum { SNK_MAX_DENSITIES = 2 };
 int snk_set_density_multi(snk_ctx *ctx, int32_t n_dens, const double *const *P);
 int snk_build_K_multi(snk_ctx *ctx, double *const *K);
+
+/* Exchange-correlation potential of the loaded density (Sec. II.C):
+ *
+ *   F_{mu i} = sum_nu P_{mu nu} Phi_{nu i}                          Eq. (fmat)
+ *   rho_i = sum_mu F_{mu i} Phi_{mu i},
+ *   grad rho_i = 2 sum_mu F_{mu i} grad Phi_{mu i}                  Eq. (den_grid)
+ *   E^rho_i, E^gamma_i = d eps / d rho, d eps / d gamma at r_i      Eq. (exc_grid)
+ *   Z_{mu i} = w_i/2 (E^rho_i Phi_{mu i} + 4 E^gamma_i grad rho . grad Phi_{mu i})   Eq. (zmat)
+ *   V_{mu nu} = sum_i Phi_{mu i} Z_{nu i} + Z_{mu i} Phi_{nu i}     Eq. (vxc_num)
+ *   E_xc = sum_i w_i eps(rho_i, gamma_i)
+ *
+ * on the handle's grid batches with the basis screen B_j (Phi, F and Z over
+ * the functions of B_j only).  eps is a spin-restricted functional (energy per
+ * volume, gamma = |grad rho|^2): SNK_XC_LDA_X Slater exchange, SNK_XC_PBE_X
+ * PBE exchange, SNK_XC_PBE PBE exchange and correlation (PW92 uniform-gas
+ * correlation); points with rho < 1e-14 add nothing.  P is the first loaded
+ * density as given (no closed-shell factor).  The two products run as FP64
+ * tiles (precision SNK_PREC_FP64) or double-FP32 tiles (SNK_PREC_MIXED);
+ * V is summed as exact fixed-point integers like K, so it is the same bit for
+ * bit from run to run.  V_out: host N_b x N_b row-major (snk_build_Vxc) or
+ * device N_b x N_b (snk_build_Vxc_device, enqueued on the library stream);
+ * E_xc: host double, may be NULL (snk_build_Vxc_device then returns without
+ * waiting for the stream).  Handles of one molecule only (SNK_ERR_UNSUPPORTED
+ * otherwise); SNK_ERR_BAD_STATE before snk_set_density; SNK_ERR_INVALID_ARG
+ * for an unknown functional or a NULL output. */
+enum { SNK_XC_LDA_X = 1, SNK_XC_PBE_X = 2, SNK_XC_PBE = 3 };
+int snk_build_Vxc(snk_ctx *ctx, int32_t functional, double *V_out, double *E_xc);
+int snk_build_Vxc_device(snk_ctx *ctx, int32_t functional, double *dV, double *E_xc);
 
 /* Autotuner of the integral kernels (after snk_set_density): for every FP32
  * list of the mixed form, times the kernel on the batches of the last

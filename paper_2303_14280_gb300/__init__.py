@@ -47,8 +47,9 @@ SYMBOLS = ["snk_options_default", "snk_create", "snk_create_batch", "snk_n_molec
            "snk_debug_shell_A", "snk_debug_pair_bound", "snk_debug_batches", "snk_shell_A_noalloc",
            "snk_screen_load", "snk_learn_collect", "snk_mlp_train", "snk_mlp_eval", "snk_mlp_grad",
            "snk_set_density_multi", "snk_build_K_multi", "snk_set_allocator", "snk_debug_tc_gemm",
-           "snk_debug_wait_timeout"]
+           "snk_debug_wait_timeout", "snk_build_Vxc", "snk_build_Vxc_device"]
 MLP_FEATURES, MLP_WEIGHTS = 16, 9473
+XC_LDA_X, XC_PBE_X, XC_PBE = 1, 2, 3   # functionals of snk_build_Vxc
 MAX_DENSITIES = 2
 
 
@@ -94,7 +95,9 @@ class SnkStats(ctypes.Structure):
                 ("gemm_flops_hi", ctypes.c_double), ("ms_integrals_class_fp32", ctypes.c_double * 6),
                 ("colloc_bytes", ctypes.c_double), ("ms_gemm_split", ctypes.c_double),
                 ("ms_gemm_hi", ctypes.c_double), ("ms_gemm_lo", ctypes.c_double), ("gemm_tc_flops", ctypes.c_double),
-                ("pair_points_fp32", ctypes.c_double), ("pair_points_fp32_listed", ctypes.c_double)]
+                ("pair_points_fp32", ctypes.c_double), ("pair_points_fp32_listed", ctypes.c_double)] + \
+               [(n, ctypes.c_double) for n in ("ms_xc_collocation", "ms_xc_fgemm", "ms_xc_point", "ms_xc_vgemm",
+                                                "xc_gemm_flops", "xc_colloc_bytes")]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -131,6 +134,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
                          "snk_set_density_batch", "snk_build_K_batch"):
                 getattr(L, name).argtypes = [_P, _P]
             L.snk_autotune.argtypes = [_P, _I32]
+            L.snk_build_Vxc.argtypes = [_P, ctypes.c_int32, _P, _P]
+            L.snk_build_Vxc_device.argtypes = [_P, ctypes.c_int32, _P, _P]
             L.snk_set_density_multi.argtypes = [_P, ctypes.c_int32, _P]
             L.snk_build_K_multi.argtypes = [_P, _P]
             L.snk_set_stream.argtypes = [_P, _P]
@@ -462,6 +467,25 @@ class Engine:
         assert K.dtype == np.float64 and K.flags.c_contiguous and K.size == self.packed
         self._check(lib().snk_build_K(self._h, _P(K.ctypes.data)), "snk_build_K")
         return K
+
+    def build_Vxc(self, functional, out=None):
+        """(V^xc, E_xc) of the loaded density (snk_build_Vxc; Sec. II.C) for
+        functional XC_LDA_X, XC_PBE_X or XC_PBE.  V is a host array, or with
+        out = a contiguous float64 CUDA tensor of N_b x N_b on the engine's
+        device, written there (E_xc is then read back, which waits for the
+        engine's stream)."""
+        fn = int(functional)
+        E = ctypes.c_double(0.0)
+        if out is not None and _is_cuda_tensor(out):
+            import torch
+            if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != self.nf * self.nf:
+                raise ValueError("out must be a contiguous float64 tensor of N_b x N_b elements")
+            self._check(lib().snk_build_Vxc_device(self._h, fn, _P(out.data_ptr()), ctypes.byref(E)),
+                        "snk_build_Vxc_device")
+            return out, E.value
+        V = np.empty((self.nf, self.nf))
+        self._check(lib().snk_build_Vxc(self._h, fn, _P(V.ctypes.data), ctypes.byref(E)), "snk_build_Vxc")
+        return V, E.value
 
     def screen_load(self, weights):
         """Load trained MLP weights for options screen='learned' (snk_screen_load)."""

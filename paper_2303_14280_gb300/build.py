@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsnk.so")
-SOURCES = ["host_setup.cpp", "kernels_dense.cu", "kernels_integrals.cu", "kernels_ozaki.cu", "mlp.cu", "snk_api.cu"]
+SOURCES = ["host_setup.cpp", "kernels_dense.cu", "kernels_integrals.cu", "kernels_ozaki.cu", "kernels_xc.cu", "mlp.cu", "snk_api.cu"]
 HEADERS = ["snk_internal.h", "os_generated.cuh", "async_copy.cuh", "ds_arith.cuh",
            os.path.join("..", "..", "include", "snk.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -629,6 +629,57 @@ __global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
   }
 }
 
+// Exchange-correlation products (Sec. II.C).  F_{i n} = sum_k X_{i k} P[B_j k, B_j n]
+// (Eq. fmat, no weight) into the batch's F block; V-hat_{m n} += sum_i Z_{i m}
+// X_{i n} (Eq. vxc_num) scattered into the fixed-point accumulator.  MODE 0
+// FP64 tiles, MODE 2 double-FP32 tiles with the operands split as they are
+// staged (the FP64 X stays intact for the point kernel).
+template <int MODE>
+__global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
+    xc_fgemm_kernel(const BatchDesc* __restrict__ batches, const double* __restrict__ P,
+                    const int* __restrict__ xfunc, double* __restrict__ ws) {
+  const BatchDesc bd = batches[blockIdx.z];
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= bd.ldq || n0 >= bd.nB) return;
+  const double* X = ws + bd.xoff;
+  double* F = ws + bd.foff;
+  const int* xf = xfunc + bd.xfunc_off;
+  const double* Pm = P + bd.pk_off;
+  auto st = [&](int m, int n, double c) { F[(int64_t)n * bd.ldq + m] = c; };
+  if (MODE == 2) {
+    auto la = [&](int m, int k) { return df32_split(X[(int64_t)k * bd.ldq + m]); };
+    auto lb = [&](int k, int n) { return df32_split(Pm[(int64_t)xf[k] * bd.nfm + xf[n]]); };
+    df32_tile(m0, n0, bd.ldq, bd.nB, bd.nB, la, lb, st, false, false);
+  } else {
+    auto la = [&](int m, int k) { return X[(int64_t)k * bd.ldq + m]; };
+    auto lb = [&](int k, int n) { return Pm[(int64_t)xf[k] * bd.nfm + xf[n]]; };
+    gemm_tile(m0, n0, bd.ldq, bd.nB, bd.nB, la, lb, st, false, false);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(GEMM_THREADS, MODE >= 2 ? 2 : 3)
+    xc_vgemm_kernel(const BatchDesc* __restrict__ batches, const int* __restrict__ xfunc,
+                    const double* __restrict__ ws, unsigned long long* __restrict__ Vhat, int* err) {
+  const BatchDesc bd = batches[blockIdx.z];
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (m0 >= bd.nB || n0 >= bd.nB) return;
+  const double* X = ws + bd.xoff;
+  const double* Z = ws + bd.foff;
+  const int* xf = xfunc + bd.xfunc_off;
+  unsigned long long* Vm = Vhat + 2 * bd.pk_off;
+  auto st = [&](int m, int n, double c) { khat_add(&Vm[2 * ((int64_t)xf[m] * bd.nfm + xf[n])], c, err); };
+  if (MODE == 2) {
+    auto la = [&](int m, int k) { return df32_split(Z[(int64_t)m * bd.ldq + k]); };
+    auto lb = [&](int k, int n) { return df32_split(X[(int64_t)n * bd.ldq + k]); };
+    df32_tile(m0, n0, bd.nB, bd.nB, bd.q, la, lb, st, true, true);
+  } else {
+    auto la = [&](int m, int k) { return Z[(int64_t)m * bd.ldq + k]; };
+    auto lb = [&](int k, int n) { return X[(int64_t)n * bd.ldq + k]; };
+    gemm_tile(m0, n0, bd.nB, bd.nB, bd.q, la, lb, st, true, true);
+  }
+}
+
 // Tiles of list k of batch j (one block per (batch, list)): one per slab of
 // kPointTile points, each with the whole list, so that every G entry of the
 // list's launch has a single writer (its point's thread) and its additions
@@ -828,6 +879,28 @@ cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int
   if (packed == 0) return cudaSuccess;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((packed + 255) / 256, 152 * 8));
   symcheck_kernel<<<blocks, 256, 0, st>>>(mols, n_mol, packed, P, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xc_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nB,
+                            const double* P, const int* xfunc, double* ws, int mode) {
+  if (nbatch == 0 || max_ldq == 0 || max_nB == 0) return cudaSuccess;
+  dim3 grid((max_ldq + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
+  if (mode == 2)
+    xc_fgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, xfunc, ws);
+  else
+    xc_fgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, P, xfunc, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xc_vgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nB, const int* xfunc,
+                            const double* ws, unsigned long long* Vhat, int mode, int* err) {
+  if (nbatch == 0 || max_nB == 0) return cudaSuccess;
+  dim3 grid((max_nB + TM - 1) / TM, (max_nB + TN - 1) / TN, nbatch);
+  if (mode == 2)
+    xc_vgemm_kernel<2><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, ws, Vhat, err);
+  else
+    xc_vgemm_kernel<0><<<grid, GEMM_THREADS, 0, st>>>(dbatch, xfunc, ws, Vhat, err);
   return cudaGetLastError();
 }
 

@@ -171,6 +171,20 @@ struct snk_ctx {
   std::vector<Chunk> chunks;
   int max_ctas[kNumLists] = {0};
 
+  // exchange-correlation potential (snk_build_Vxc): its own batch descriptors
+  // (X, grad X and F / Z of each batch in xcws), chunks, fixed-point V-hat and
+  // E-hat, phase events
+  struct XcChunk {
+    int b0 = 0, b1 = 0, max_ldq = 0, max_nB = 0, max_nBshell = 0;
+  };
+  std::vector<XcChunk> xc_chunks;
+  DevBuf<BatchDesc> xcbatch;
+  DevBuf<double> xcws, xcE;
+  DevBuf<unsigned long long> xchat;
+  std::vector<cudaEvent_t> xcev;
+  bool xc_timed = false;
+  double xc_gemm_flops = 0.0, xc_colloc_bytes = 0.0;
+
   // CUDA graph of the build (options.graph)
   cudaStream_t gstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -197,6 +211,7 @@ struct snk_ctx {
     f(counts), f(list), f(list2), f(sfunc), f(colmap), f(tickets), f(ppcounts), f(sflag), f(list_off), f(tstart);
     f(codes), f(code_off);
     f(batch), f(tiles), f(ws), f(ws32), f(arena), f(ozsplit), f(ozjobs), f(ozerr), f(tsum), f(exec);
+    f(xcbatch), f(xcws), f(xcE), f(xchat);
   }
   snk_ctx() {
     alloc.stream = &stream;
@@ -206,6 +221,7 @@ struct snk_ctx {
   ~snk_ctx() {
     if (gstream) cudaStreamSynchronize(gstream);
     for (auto e : events) cudaEventDestroy(e);
+    for (auto e : xcev) cudaEventDestroy(e);
     if (ev_screen0) cudaEventDestroy(ev_screen0);
     if (ev_screen1) cudaEventDestroy(ev_screen1);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -1312,6 +1328,121 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
 
 }  // namespace
 
+// V^xc of the loaded density (Sec. II.C): per chunk of batches whose X, grad X
+// and F / Z fit the workspace budget, Phi and grad Phi (Eq. collocation),
+// F = X P[B_j, B_j] (Eq. fmat), the density, functional and Z (Eqs. den_grid,
+// exc_grid, zmat), V-hat += Z^T X (Eq. vxc_num); then V = V-hat + V-hat^T.
+int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
+  if (fn < SNK_XC_LDA_X || fn > SNK_XC_PBE) return fail(c, SNK_ERR_INVALID_ARG, "unknown functional");
+  if (!dV) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
+  if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_build_Vxc called before snk_set_density");
+  Setup& s = c->s;
+  if (s.n_mol != 1) return fail(c, SNK_ERR_UNSUPPORTED, "snk_build_Vxc takes handles of one molecule");
+  const int nb = c->nbatch;
+  const int64_t nf = s.nf;
+  if (c->xc_chunks.empty() && nb > 0) {
+    std::vector<BatchDesc> bd(nb);
+    int64_t off = 0, most = 0;
+    double flops = 0.0, bytes = 0.0;
+    snk_ctx::XcChunk ch;
+    for (int j = 0; j < nb; ++j) {
+      BatchDesc b = geometry_desc(s, j);
+      const int64_t blk = (int64_t)b.ldq * b.nB;
+      if (j > ch.b0 && (off + 5 * blk) * 8 > c->ws_budget / 2) {  // beside the exchange workspace
+        ch.b1 = j;
+        c->xc_chunks.push_back(ch);
+        most = std::max(most, off);
+        ch = snk_ctx::XcChunk();
+        ch.b0 = j;
+        off = 0;
+      }
+      b.xoff = off;
+      b.foff = off + 4 * blk;
+      off += 5 * blk;
+      bd[j] = b;
+      ch.max_ldq = std::max(ch.max_ldq, b.ldq);
+      ch.max_nB = std::max(ch.max_nB, b.nB);
+      ch.max_nBshell = std::max(ch.max_nBshell, b.nBshell);
+      flops += 2.0 * b.ldq * b.nB * (double)b.nB + 2.0 * b.q * b.nB * (double)b.nB;
+      bytes += 4.0 * 8.0 * blk;
+    }
+    ch.b1 = nb;
+    c->xc_chunks.push_back(ch);
+    most = std::max(most, off);
+    int rc = SNK_OK;
+    cudaError_t e = c->xcbatch.ensure(nb);
+    if (e == cudaSuccess) e = c->xcws.ensure((size_t)std::max<int64_t>(most, 1));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->xcbatch.p, bd.data(), sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // bd is a local vector
+    if (e != cudaSuccess) {
+      c->xc_chunks.clear();
+      rc = cuda_fail(c, e, "snk_build_Vxc workspace");
+      return rc == SNK_OK ? SNK_ERR_CUDA : rc;
+    }
+    c->xc_gemm_flops = flops;
+    c->xc_colloc_bytes = bytes;
+  }
+  const bool fresh_err = !c->ozerr.p;
+  SNK_CK(c, c->ozerr.ensure(1));
+  if (fresh_err) SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), c->stream));
+  SNK_CK(c, c->xchat.ensure((size_t)(2 * nf * nf + 2)));
+  SNK_CK(c, c->xcE.ensure(1));
+  const size_t nev = 1 + 4 * c->xc_chunks.size();
+  while (c->xcev.size() < nev) {
+    cudaEvent_t ev;
+    SNK_CK(c, cudaEventCreate(&ev));
+    c->xcev.push_back(ev);
+  }
+  const cudaStream_t st = c->stream;
+  const int mode = c->opt.precision == SNK_PREC_MIXED ? 2 : 0;
+  unsigned long long* Vhat = c->xchat.p;
+  unsigned long long* Ehat = c->xchat.p + 2 * nf * nf;
+  int ev = 0;
+  SNK_CK(c, cudaMemsetAsync(c->xchat.p, 0, sizeof(unsigned long long) * (2 * nf * nf + 2), st));
+  SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
+  for (const auto& ch : c->xc_chunks) {
+    const BatchDesc* db = c->xcbatch.p + ch.b0;
+    const int n = ch.b1 - ch.b0;
+    SNK_CK(c, launch_xc_colloc(st, db, n, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
+                               dev_basis(c), c->xcws.p));
+    SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
+    SNK_CK(c, launch_xc_fgemm(st, db, n, ch.max_ldq, ch.max_nB, c->P.p, c->xfunc.p, c->xcws.p, mode));
+    SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
+    SNK_CK(c, launch_xc_point(st, db, n, ch.max_ldq, c->w.p, fn, c->xcws.p, Ehat, c->ozerr.p));
+    SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
+    SNK_CK(c, launch_xc_vgemm(st, db, n, ch.max_nB, c->xfunc.p, c->xcws.p, Vhat, mode, c->ozerr.p));
+    if (&ch == &c->xc_chunks.back()) SNK_CK(c, launch_xc_finish(st, nf, Vhat, Ehat, dV, c->xcE.p));
+    SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
+  }
+  if (c->xc_chunks.empty()) SNK_CK(c, launch_xc_finish(st, nf, Vhat, Ehat, dV, c->xcE.p));
+  c->xc_timed = !c->xc_chunks.empty();
+  if (!E_host) return SNK_OK;
+  SNK_CK(c, cudaMemcpyAsync(E_host, c->xcE.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaStreamSynchronize(st));
+  return check_device_flags(c);
+}
+
+// phase times of the last snk_build_Vxc (waits for its last event)
+void collect_xc_times(snk_ctx* c) {
+  snk_stats& st = c->st;
+  st.xc_gemm_flops = c->xc_gemm_flops;
+  st.xc_colloc_bytes = c->xc_colloc_bytes;
+  if (!c->xc_timed) return;
+  const size_t last = 4 * c->xc_chunks.size();
+  if (cudaEventSynchronize(c->xcev[last]) != cudaSuccess) return;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (size_t k = 0; k < last; ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->xcev[k], c->xcev[k + 1]);
+    t[k % 4] += ms;
+  }
+  st.ms_xc_collocation = t[0];
+  st.ms_xc_fgemm = t[1];
+  st.ms_xc_point = t[2];
+  st.ms_xc_vgemm = t[3];
+}
+
 extern "C" {
 
 void snk_options_default(snk_options* o) {
@@ -1456,6 +1587,25 @@ int snk_build_K(snk_ctx* c, double* K) {
   return check_device_flags(c);
 }
 
+int snk_build_Vxc_device(snk_ctx* c, int32_t functional, double* dV, double* E_xc) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  return build_vxc(c, functional, dV, E_xc);
+}
+
+int snk_build_Vxc(snk_ctx* c, int32_t functional, double* V, double* E_xc) {
+  if (!c) return SNK_ERR_INVALID_ARG;
+  if (!V) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
+  const size_t n = (size_t)c->s.nf * (size_t)c->s.nf;
+  SNK_CK(c, c->K.ensure(std::max<size_t>(n, 1)));
+  double e = 0.0;
+  int rc = build_vxc(c, functional, c->K.p, &e);
+  if (rc != SNK_OK) return rc;
+  if (n) SNK_CK(c, cudaMemcpyAsync(V, c->K.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  SNK_CK(c, cudaStreamSynchronize(c->stream));
+  if (E_xc) *E_xc = e;
+  return SNK_OK;
+}
+
 int snk_build_K_batch(snk_ctx* c, double* const* K) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (int rc = one_density(c)) return rc;
@@ -1543,6 +1693,7 @@ int snk_get_stats(const snk_ctx* c, snk_stats* out) {
   if (!c || !out) return SNK_ERR_INVALID_ARG;
   snk_ctx* m = const_cast<snk_ctx*>(c);
   collect_times(m);
+  collect_xc_times(m);
   *out = m->st;
   return SNK_OK;
 }

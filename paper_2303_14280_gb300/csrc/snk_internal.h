@@ -268,6 +268,23 @@ cudaError_t launch_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64
 cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed, const double* P,
                             double* out2);
 
+// Exchange-correlation potential (Sec. II.C).  Per batch at BatchDesc::xoff:
+// X, dX/dx, dX/dy, dX/dz (ldq x nB each), then F / Z at BatchDesc::foff.
+// mode: 0 FP64 tiles, 2 double-FP32 tiles.  Vhat (two words per entry of the
+// molecule's block at pk_off, see khat_add) and Ehat (two words) accumulate.
+cudaError_t launch_xc_colloc(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nBshell,
+                             const int* bshell, const int* bshell_col, const double* xyz, DeviceBasis basis,
+                             double* ws);
+cudaError_t launch_xc_fgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nB,
+                            const double* P, const int* xfunc, double* ws, int mode);
+cudaError_t launch_xc_point(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, const double* w,
+                            int functional, double* ws, unsigned long long* Ehat, int* err);
+cudaError_t launch_xc_vgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nB, const int* xfunc,
+                            const double* ws, unsigned long long* Vhat, int mode, int* err);
+// V = V-hat + V-hat^T (nf x nf, one molecule) and *E = E-hat.
+cudaError_t launch_xc_finish(cudaStream_t st, int64_t nf, const unsigned long long* Vhat,
+                             const unsigned long long* Ehat, double* V, double* E);
+
 struct IntegralArgs {
   const Tile* tiles;
   int n_tiles;
