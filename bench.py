@@ -719,11 +719,20 @@ def main():
         "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps},
     }
-    if vxc and "products" in vxc:      # double-FP32 tiles in the mixed form, FP64 tiles otherwise
+    if vxc and "products" in vxc:
         mixed = chosen_opts.get("precision") == "mixed"
-        peak = FP32_PEAK / DF32_OPS_PER_MAC if mixed else FP64_PEAK
-        vxc["products"].update(peak=peak, frac=vxc["products"]["achieved"] / peak,
-                               tiles="double-FP32" if mixed else "FP64")
+        pr = vxc["products"]
+        if mixed and chosen_opts.get("gemm") == "split":
+            # tcgen05 split products: S(S+1)/2 bf16 slice products per FP64-equivalent product
+            sl = chosen_opts.get("tc_slices_hi", 5)
+            f64 = pr["achieved"]
+            a = f64 * sl * (sl + 1) // 2
+            pr.update(achieved=a, unit="TFLOP/s (bf16 slice products, algorithmic sizes)", bound="tensor",
+                      peak=BF16_PEAK, frac=a / BF16_PEAK, fp64_equivalent_tflops=f64,
+                      tiles=f"tcgen05 split products, {sl} slices")
+        else:                          # double-FP32 tiles in the mixed form, FP64 tiles otherwise
+            peak = FP32_PEAK / DF32_OPS_PER_MAC if mixed else FP64_PEAK
+            pr.update(peak=peak, frac=pr["achieved"] / peak, tiles="double-FP32" if mixed else "FP64")
     if batch:
         line["autotuned_pairs_per_tile"] = ch.runs
         line["phases_ms_per_step"] = None   # graph replay: no per-phase events

@@ -548,6 +548,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(OzGemmArgs a) {
           const int n = nt * kOzRows + col0 + c;
           if (n < J.n_lim) a.ws[J.out_off + (int64_t)m * J.ldc + n] = res[c];
         }
+      } else if (J.kind == 3) {
+        // plain C stored column-major (point fastest): the F = X P of the
+        // exchange-correlation potential
+        const BatchDesc& bd = a.batches[J.batch];
+        double* F = a.ws + J.out_off;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const int n = nt * kOzRows + col0 + c;
+          if (n < J.n_lim) F[(int64_t)(J.c0 + n) * bd.ldq + m] = res[c];
+        }
       } else if (J.kind == 0) {
         const BatchDesc& bd = a.batches[J.batch];
         // F-hat_{n m} = w_m f_n sum_k X_{m k} P_{k n}, stored column-major (point fastest)

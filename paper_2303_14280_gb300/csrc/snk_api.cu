@@ -174,13 +174,20 @@ struct snk_ctx {
   // exchange-correlation potential (snk_build_Vxc): its own batch descriptors
   // (X, grad X and F / Z of each batch in xcws), chunks, fixed-point V-hat and
   // E-hat, phase events
+  // (with gemm = SPLIT the two products are tcgen05 split products: split and
+  // product jobs of phase 0, F = X P, and phase 1, V-hat += Z^T X, per chunk)
   struct XcChunk {
     int b0 = 0, b1 = 0, max_ldq = 0, max_nB = 0, max_nBshell = 0;
+    int s_off[2] = {0, 0}, s_n[2] = {0, 0}, s_rows[2] = {0, 0}, s_k[2] = {0, 0};
+    int g_off[2] = {0, 0}, g_n[2] = {0, 0}, g_tiles[2] = {0, 0};
   };
   std::vector<XcChunk> xc_chunks;
   DevBuf<BatchDesc> xcbatch;
   DevBuf<double> xcws, xcE;
   DevBuf<unsigned long long> xchat;
+  DevBuf<uint8_t> xcarena;
+  DevBuf<OzSplitJob> xcsplit;
+  DevBuf<OzGemmJob> xcjobs;
   std::vector<cudaEvent_t> xcev;
   bool xc_timed = false;
   double xc_gemm_flops = 0.0, xc_colloc_bytes = 0.0;
@@ -211,7 +218,7 @@ struct snk_ctx {
     f(counts), f(list), f(list2), f(sfunc), f(colmap), f(tickets), f(ppcounts), f(sflag), f(list_off), f(tstart);
     f(codes), f(code_off);
     f(batch), f(tiles), f(ws), f(ws32), f(arena), f(ozsplit), f(ozjobs), f(ozerr), f(tsum), f(exec);
-    f(xcbatch), f(xcws), f(xcE), f(xchat);
+    f(xcbatch), f(xcws), f(xcE), f(xchat), f(xcarena), f(xcsplit), f(xcjobs);
   }
   snk_ctx() {
     alloc.stream = &stream;
@@ -1328,6 +1335,34 @@ int create(int n_mol, const snk_basis* bases, const snk_grid* grids, const snk_o
 
 }  // namespace
 
+// One tensor-core product phase of a V^xc chunk (0: F = X P, 1: V-hat += Z^T
+// X): the operands' bf16 slices into the V^xc arena, then the products.  The
+// row lists of both products are B_j, so xfunc serves as the product kernels'
+// sfunc (the chunk's descriptors carry sfunc_off = xfunc_off).
+int xc_tc_product(snk_ctx* c, const snk_ctx::XcChunk& ch, int phase, unsigned long long* Vhat) {
+  const cudaStream_t st = c->stream;
+  SNK_CK(c, launch_oz_split(st, c->xcsplit.p + ch.s_off[phase], ch.s_n[phase], ch.s_rows[phase], ch.s_k[phase],
+                            c->xcws.p, c->P.p, c->xfunc.p, c->xfunc.p, c->xcarena.p, (int64_t)c->xcarena.n,
+                            c->ozerr.p));
+  OzGemmArgs g;
+  g.jobs = c->xcjobs.p + ch.g_off[phase];
+  g.n_jobs = ch.g_n[phase];
+  g.n_tiles = ch.g_tiles[phase];
+  g.arena = c->xcarena.p;
+  g.arena_bytes = (int64_t)c->xcarena.n;
+  g.batches = c->xcbatch.p + ch.b0;
+  g.w = c->w.p;
+  g.fcomp = c->fcomp.p;
+  g.sfunc = c->xfunc.p;
+  g.xfunc = c->xfunc.p;
+  g.ws = c->xcws.p;
+  g.ws32 = nullptr;
+  g.Khat = Vhat;
+  g.err = c->ozerr.p;
+  SNK_CK(c, launch_oz_gemm(st, c->opt.tc_slices_hi, g, c->num_sms));
+  return SNK_OK;
+}
+
 // V^xc of the loaded density (Sec. II.C): per chunk of batches whose X, grad X
 // and F / Z fit the workspace budget, Phi and grad Phi (Eq. collocation),
 // F = X P[B_j, B_j] (Eq. fmat), the density, functional and Z (Eqs. den_grid,
@@ -1340,25 +1375,42 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
   if (s.n_mol != 1) return fail(c, SNK_ERR_UNSUPPORTED, "snk_build_Vxc takes handles of one molecule");
   const int nb = c->nbatch;
   const int64_t nf = s.nf;
+  const bool tc = c->opt.precision == SNK_PREC_MIXED && c->opt.gemm == SNK_GEMM_SPLIT;
+  const int S = c->opt.tc_slices_hi;  // slices of both tensor-core products
   if (c->xc_chunks.empty() && nb > 0) {
     std::vector<BatchDesc> bd(nb);
-    int64_t off = 0, most = 0;
+    std::vector<OzSplitJob> sj;
+    std::vector<OzGemmJob> gj;
+    int64_t off = 0, most = 0, arena = 0, arena_most = 0;
     double flops = 0.0, bytes = 0.0;
+    // slice bytes of batch b in each phase (the phases reuse one arena)
+    auto arena_of = [&](const BatchDesc& b, int phase) -> int64_t {
+      if (!tc || b.q == 0 || b.nB == 0) return 0;
+      return phase == 0 ? oz_operand_bytes(b.q, b.nB, S) + oz_operand_bytes(b.nB, b.nB, S)
+                        : 2 * oz_operand_bytes(b.nB, b.q, S);
+    };
+    std::vector<snk_ctx::XcChunk> chunks;
     snk_ctx::XcChunk ch;
+    int64_t a0 = 0, a1 = 0;  // the chunk's slice bytes per phase
     for (int j = 0; j < nb; ++j) {
       BatchDesc b = geometry_desc(s, j);
+      b.sfunc_off = b.xfunc_off;  // the products' row lists are B_j too
       const int64_t blk = (int64_t)b.ldq * b.nB;
-      if (j > ch.b0 && (off + 5 * blk) * 8 > c->ws_budget / 2) {  // beside the exchange workspace
+      const int64_t need = (off + 5 * blk) * 8 + std::max(a0 + arena_of(b, 0), a1 + arena_of(b, 1));
+      if (j > ch.b0 && need > c->ws_budget / 2) {  // beside the exchange workspace
         ch.b1 = j;
-        c->xc_chunks.push_back(ch);
+        chunks.push_back(ch);
         most = std::max(most, off);
+        arena_most = std::max(arena_most, std::max(a0, a1));
         ch = snk_ctx::XcChunk();
         ch.b0 = j;
-        off = 0;
+        off = a0 = a1 = 0;
       }
       b.xoff = off;
       b.foff = off + 4 * blk;
       off += 5 * blk;
+      a0 += arena_of(b, 0);
+      a1 += arena_of(b, 1);
       bd[j] = b;
       ch.max_ldq = std::max(ch.max_ldq, b.ldq);
       ch.max_nB = std::max(ch.max_nB, b.nB);
@@ -1367,19 +1419,93 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
       bytes += 4.0 * 8.0 * blk;
     }
     ch.b1 = nb;
-    c->xc_chunks.push_back(ch);
+    chunks.push_back(ch);
     most = std::max(most, off);
-    int rc = SNK_OK;
+    arena_most = std::max(arena_most, std::max(a0, a1));
+    (void)arena;
+    if (tc) {
+      for (auto& C : chunks) {
+        for (int phase = 0; phase < 2; ++phase) {
+          C.s_off[phase] = (int)sj.size();
+          C.g_off[phase] = (int)gj.size();
+          int64_t cur = 0;
+          int tiles = 0;
+          auto add_split = [&](int mode, int R, int K, int ld, const BatchDesc& b, int64_t src) -> int64_t {
+            OzSplitJob J{};
+            J.mode = mode;
+            J.R = R;
+            J.K = K;
+            J.S = S;
+            J.ld = ld;
+            J.r0 = 0;
+            J.sf_off = b.xfunc_off;
+            J.xf_off = b.xfunc_off;
+            J.src_off = src;
+            J.dst_off = cur;
+            sj.push_back(J);
+            C.s_rows[phase] = std::max(C.s_rows[phase], R);
+            C.s_k[phase] = std::max(C.s_k[phase], K);
+            const int64_t at = cur;
+            cur += oz_operand_bytes(R, K, S);
+            return at;
+          };
+          for (int t = C.b0; t < C.b1; ++t) {
+            const BatchDesc& b = bd[t];
+            if (b.q == 0 || b.nB == 0) continue;
+            OzGemmJob G{};
+            G.batch = t - C.b0;  // the launch's descriptors start at the chunk's first batch
+            G.Sa = G.Sb = S;
+            G.c0 = 0;
+            if (phase == 0) {  // F = X_j P[B_j, B_j] (P symmetric: rows of P are its columns)
+              G.a_off = add_split(0, b.q, b.nB, b.ldq, b, b.xoff);
+              G.b_off = add_split(2, b.nB, b.nB, b.nfm, b, b.pk_off);
+              G.RTa = oz_row_tiles(b.q);
+              G.RTb = oz_row_tiles(b.nB);
+              G.KT = oz_k_tiles(b.nB);
+              G.kind = 3;
+              G.m_lim = b.ldq;
+              G.n_lim = b.nB;
+              G.out_off = b.foff;
+            } else {  // V-hat[B_j, B_j] += Z_j^T X_j
+              G.a_off = add_split(1, b.nB, b.q, b.ldq, b, b.foff);
+              G.b_off = add_split(1, b.nB, b.q, b.ldq, b, b.xoff);
+              G.RTa = oz_row_tiles(b.nB);
+              G.RTb = oz_row_tiles(b.nB);
+              G.KT = oz_k_tiles(b.q);
+              G.kind = 1;
+              G.m_lim = b.nB;
+              G.n_lim = b.nB;
+              G.out_off = b.pk_off;
+            }
+            G.tile0 = tiles;
+            tiles += G.RTa * G.RTb;
+            gj.push_back(G);
+          }
+          C.s_n[phase] = (int)sj.size() - C.s_off[phase];
+          C.g_n[phase] = (int)gj.size() - C.g_off[phase];
+          C.g_tiles[phase] = tiles;
+          if (cur > arena_most) return fail(c, SNK_ERR_INVALID_ARG, "internal: V^xc slice arena too small");
+        }
+      }
+    }
     cudaError_t e = c->xcbatch.ensure(nb);
     if (e == cudaSuccess) e = c->xcws.ensure((size_t)std::max<int64_t>(most, 1));
+    if (e == cudaSuccess && tc) e = c->xcarena.ensure((size_t)std::max<int64_t>(arena_most, 1));
+    if (e == cudaSuccess && tc) e = c->xcsplit.ensure(std::max<size_t>(sj.size(), 1));
+    if (e == cudaSuccess && tc) e = c->xcjobs.ensure(std::max<size_t>(gj.size(), 1));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->xcbatch.p, bd.data(), sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // bd is a local vector
+    if (e == cudaSuccess && !sj.empty())
+      e = cudaMemcpyAsync(c->xcsplit.p, sj.data(), sizeof(OzSplitJob) * sj.size(), cudaMemcpyHostToDevice,
+                          c->stream);
+    if (e == cudaSuccess && !gj.empty())
+      e = cudaMemcpyAsync(c->xcjobs.p, gj.data(), sizeof(OzGemmJob) * gj.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // the host vectors are local
     if (e != cudaSuccess) {
-      c->xc_chunks.clear();
-      rc = cuda_fail(c, e, "snk_build_Vxc workspace");
+      const int rc = cuda_fail(c, e, "snk_build_Vxc workspace");
       return rc == SNK_OK ? SNK_ERR_CUDA : rc;
     }
+    c->xc_chunks = chunks;
     c->xc_gemm_flops = flops;
     c->xc_colloc_bytes = bytes;
   }
@@ -1407,11 +1533,19 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
     SNK_CK(c, launch_xc_colloc(st, db, n, ch.max_ldq, ch.max_nBshell, c->bshell.p, c->bshell_col.p, c->xyz.p,
                                dev_basis(c), c->xcws.p));
     SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
-    SNK_CK(c, launch_xc_fgemm(st, db, n, ch.max_ldq, ch.max_nB, c->P.p, c->xfunc.p, c->xcws.p, mode));
+    if (tc) {
+      if (int rc = xc_tc_product(c, ch, 0, Vhat)) return rc;
+    } else {
+      SNK_CK(c, launch_xc_fgemm(st, db, n, ch.max_ldq, ch.max_nB, c->P.p, c->xfunc.p, c->xcws.p, mode));
+    }
     SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
     SNK_CK(c, launch_xc_point(st, db, n, ch.max_ldq, c->w.p, fn, c->xcws.p, Ehat, c->ozerr.p));
     SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
-    SNK_CK(c, launch_xc_vgemm(st, db, n, ch.max_nB, c->xfunc.p, c->xcws.p, Vhat, mode, c->ozerr.p));
+    if (tc) {
+      if (int rc = xc_tc_product(c, ch, 1, Vhat)) return rc;
+    } else {
+      SNK_CK(c, launch_xc_vgemm(st, db, n, ch.max_nB, c->xfunc.p, c->xcws.p, Vhat, mode, c->ozerr.p));
+    }
     if (&ch == &c->xc_chunks.back()) SNK_CK(c, launch_xc_finish(st, nf, Vhat, Ehat, dV, c->xcE.p));
     SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
   }

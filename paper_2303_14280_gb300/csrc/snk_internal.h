@@ -363,6 +363,7 @@ struct OzSplitJob {
 //   kind 0: F[(c0 + n) ldq + m] = w_m f_{c0+n} C (doubles at ws + out_off, floats at ws32 + out_off32)
 //   kind 1: Khat[out_off + sfunc[c0 + m] N_b,m + xfunc[n]] += C (entries of two words, khat_add)
 //   kind 2: ws[out_off + m ldc + n] = C (test export)
+//   kind 3: ws[out_off + (c0 + n) ldq + m] = C (column-major, no weights: F of V^xc)
 struct OzGemmJob {
   int64_t a_off, b_off, out_off, out_off32;
   int32_t RTa, RTb, KT, Sa, Sb, tile0, batch, kind, m_lim, n_lim, c0, ldc;
