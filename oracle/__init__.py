@@ -67,11 +67,13 @@ def lib():
             L.oracle_xc_point.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
             L.oracle_collocation_grad.argtypes = basis_args + [ctypes.c_long, _D, _D, _D]
             L.oracle_vxc.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int, _D, _D, ctypes.c_int]
+            L.oracle_vxc_entries.argtypes = basis_args + [ctypes.c_long, _D, _D, _D, ctypes.c_int, ctypes.c_int,
+                                                          _I, _I, _D, _D, ctypes.c_int]
             L.oracle_mlp_forward.argtypes = [_D, _D, ctypes.c_long, _D]
             L.oracle_mlp_loss_grad.argtypes = [_D, _D, _D, ctypes.c_long, ctypes.c_double, _D, _D]
             for name in ("oracle_normalise", "oracle_collocation", "oracle_shell_A", "oracle_eri_K",
                          "oracle_snk_K", "oracle_snk_K_entries", "oracle_g_rows", "oracle_mlp_forward", "oracle_mlp_loss_grad",
-                         "oracle_xc_point", "oracle_collocation_grad", "oracle_vxc"):
+                         "oracle_xc_point", "oracle_collocation_grad", "oracle_vxc", "oracle_vxc_entries"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -284,3 +286,17 @@ def vxc(basis, grid, P, functional: int, nthreads: int = 0):
     _check(lib().oracle_vxc(*args, ctypes.c_long(w.shape[0]), _dp(xyz), _dp(w), _dp(P), int(functional), _dp(V),
                             _dp(E), int(nthreads)), "vxc")
     return V, float(E[0])
+
+
+def vxc_entries(basis, grid, P, functional: int, mu, nu, nthreads: int = 0):
+    """(V^xc_{mu_k nu_k}, E_xc): the same computation as vxc(), accumulating
+    only the requested entries of V."""
+    arrs, args = _basis_args(basis)
+    xyz, w, P = _f64(grid.xyz), _f64(grid.w), _f64(P)
+    mu, nu = _i32(mu), _i32(nu)
+    out = np.zeros(mu.shape[0])
+    E = np.zeros(1)
+    _check(lib().oracle_vxc_entries(*args, ctypes.c_long(w.shape[0]), _dp(xyz), _dp(w), _dp(P), int(functional),
+                                    int(mu.shape[0]), _ip(mu), _ip(nu), _dp(out), _dp(E), int(nthreads)),
+           "vxc_entries")
+    return out, float(E[0])

@@ -1072,3 +1072,76 @@ int oracle_vxc(int n_shells, const int *l, const int *nprim, const double *cente
   obasis_free(&b);
   return 0;
 }
+
+/* Selected entries V_{mu_k nu_k} and E_xc of the same computation: per point
+ * the density needs F over every function, but Z only over the functions of
+ * the requested entries (all of them are formed here; the saving is the
+ * N_b^2 accumulation of V). */
+int oracle_vxc_entries(int n_shells, const int *l, const int *nprim, const double *center, const double *exps,
+                       const double *coefs, long npts, const double *xyz, const double *w, const double *Pm,
+                       int functional, int n_ent, const int *mu_e, const int *nu_e, double *Ve, double *Exc,
+                       int nthreads) {
+  if (functional < 1 || functional > 3) return -2;
+  obasis b;
+  if (obasis_init(&b, n_shells, l, nprim, center, exps, coefs)) return -1;
+  int nf = b.n_func, nt = n_threads_or_default(nthreads);
+  for (int k = 0; k < n_ent; ++k)
+    if (mu_e[k] < 0 || mu_e[k] >= nf || nu_e[k] < 0 || nu_e[k] >= nf) {
+      obasis_free(&b);
+      return -3;
+    }
+  double *Vt = (double *)calloc((size_t)nt * (n_ent > 0 ? n_ent : 1), sizeof(double));
+  double *Et = (double *)calloc((size_t)nt, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+#ifdef _OPENMP
+    int tid = omp_get_thread_num();
+#else
+    int tid = 0;
+#endif
+    double *phi = (double *)malloc(sizeof(double) * nf);
+    double *gphi = (double *)malloc(sizeof(double) * 3 * nf);
+    double *F = (double *)malloc(sizeof(double) * nf);
+    double *Z = (double *)malloc(sizeof(double) * nf);
+    double *Vl = Vt + (size_t)tid * (n_ent > 0 ? n_ent : 1);
+#pragma omp for schedule(static)
+    for (long i = 0; i < npts; ++i) {
+      collocate_grad_point(&b, xyz + 3 * i, phi, gphi);
+      for (int mu = 0; mu < nf; ++mu) {
+        double s = 0.0;
+        for (int nu = 0; nu < nf; ++nu) s += Pm[mu * nf + nu] * phi[nu];
+        F[mu] = s;
+      }
+      double rho = 0.0, g[3] = {0.0, 0.0, 0.0};
+      for (int mu = 0; mu < nf; ++mu) {
+        rho += F[mu] * phi[mu];
+        for (int q = 0; q < 3; ++q) g[q] += 2.0 * F[mu] * gphi[q * nf + mu];
+      }
+      if (!(rho >= ORC_XC_RHO_MIN)) continue;
+      double e[3];
+      oracle_xc_point(functional, rho, g[0] * g[0] + g[1] * g[1] + g[2] * g[2], e);
+      Et[tid] += w[i] * e[0];
+      for (int mu = 0; mu < nf; ++mu) {
+        double gg = g[0] * gphi[mu] + g[1] * gphi[nf + mu] + g[2] * gphi[2 * nf + mu];
+        Z[mu] = 0.5 * w[i] * (e[1] * phi[mu] + 4.0 * e[2] * gg);
+      }
+      for (int k = 0; k < n_ent; ++k) Vl[k] += phi[mu_e[k]] * Z[nu_e[k]] + Z[mu_e[k]] * phi[nu_e[k]];
+    }
+    free(phi);
+    free(gphi);
+    free(F);
+    free(Z);
+  }
+  for (int k = 0; k < n_ent; ++k) {
+    double s = 0.0;
+    for (int t = 0; t < nt; ++t) s += Vt[(size_t)t * n_ent + k];
+    Ve[k] = s;
+  }
+  double es = 0.0;
+  for (int t = 0; t < nt; ++t) es += Et[t];
+  *Exc = es;
+  free(Vt);
+  free(Et);
+  obasis_free(&b);
+  return 0;
+}

@@ -8,6 +8,8 @@ product term).  The device path drops the functions outside each batch's
 basis screen B_j (|Phi| below eps_basis = 1e-12 on the batch), which moves V
 by far less than that.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -119,3 +121,42 @@ def test_errors(snk, chain4):
     with pytest.raises(snk.SnkError) as e:
         beng.build_Vxc(oracle.XC_LDA_X)
     assert e.value.status == -2
+
+
+GOLDEN96 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster96_vxc_entries.txt")
+
+
+def _golden96():
+    with open(GOLDEN96) as f:
+        exc = next(float(line.split()[2]) for line in f if line.startswith("# E_xc"))
+    d = np.loadtxt(GOLDEN96)
+    return d[:, 0].astype(int), d[:, 1].astype(int), d[:, 2], exc
+
+
+@pytest.fixture(scope="module")
+def c96():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return synth.cluster96(device="cuda")
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN96), reason="cluster96 V^xc oracle entries not generated")
+@pytest.mark.parametrize("form", ["plain", "chosen"])
+def test_cluster96_matches_oracle_entries(snk, c96, form):
+    """Full size (992 functions, 768,000 points): the plain FP64 handle and the
+    handle bench.py times (its options: basis screen 1e-10, tcgen05 split
+    products) against the oracle's PBE V^xc entries (heavy and light rows,
+    near and far) and E_xc."""
+    import bench
+    opts = dict() if form == "plain" else dict(bench.CHOSEN)
+    tol = TOL if form == "plain" else 1e-8
+    eng = snk.Engine(c96.basis, c96.grid, **opts)
+    eng.set_density(c96.P)
+    V, E = eng.build_Vxc(oracle.XC_PBE)
+    mu, nu, ref, exc = _golden96()
+    err = float(np.max(np.abs(V[mu, nu] - ref)))
+    print(f"cluster96 V^xc {form}: max|dV| {err:.3e} over {len(mu)} entries, |dE| {abs(E - exc):.3e}")
+    assert err <= tol and abs(E - exc) <= tol
+    assert np.array_equal(V, V.T)
+    eng.close()

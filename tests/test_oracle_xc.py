@@ -179,3 +179,15 @@ def test_single_gaussian_slater_energy():
         errs.append(abs(E - exact))
         assert abs(V[0, 0] - 4 / 3 * E) <= 1e-13 * abs(E)     # tr(V P) = 4/3 E with P = [[1]]
     assert errs[-1] < 1e-9 * abs(exact) and errs[-1] < errs[0]
+
+
+def test_vxc_entries_mode_matches_full(chain4):
+    """The entries mode accumulates the same sums as the full V."""
+    b, g = chain4.basis, _subgrid(chain4.grid, 3)
+    V, E = oracle.vxc(b, g, chain4.P, PBE)
+    rng = np.random.default_rng(2)
+    mu = rng.integers(0, V.shape[0], 40)
+    nu = rng.integers(0, V.shape[0], 40)
+    Ve, Ee = oracle.vxc_entries(b, g, chain4.P, PBE, mu, nu)
+    np.testing.assert_allclose(Ve, V[mu, nu], rtol=1e-13, atol=1e-15)
+    assert abs(Ee - E) <= 1e-13 * abs(E)
