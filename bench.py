@@ -568,7 +568,12 @@ def main():
     e2e_value = job_throughput(e2e_s * 1e3, e2e_steps, world, n_mol if batch else 1)
     nbytes = sum(p.P.nbytes for p in probs)
     ch_create = ch.create_s
-    vxc = measure_vxc(ch.engs[0], ch.P[0], stream) if not batch else None
+    vxc = None
+    if not batch:
+        try:
+            vxc = measure_vxc(ch.engs[0], ch.P[0], stream)
+        except Exception as e:        # reported, not fatal: the K-build line above stands
+            vxc = {"error": str(e)}
     ch.close()
 
     # ---- plain FP64 beside it: the full build, or its stated subset scaled to the full build

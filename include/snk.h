@@ -276,16 +276,22 @@ int snk_build_K_multi(snk_ctx *ctx, double *const *K);
  * the functions of B_j only).  eps is a spin-restricted functional (energy per
  * volume, gamma = |grad rho|^2): SNK_XC_LDA_X Slater exchange, SNK_XC_PBE_X
  * PBE exchange, SNK_XC_PBE PBE exchange and correlation (PW92 uniform-gas
- * correlation); points with rho < 1e-14 add nothing.  P is the first loaded
- * density as given (no closed-shell factor).  The two products run as FP64
- * tiles (precision SNK_PREC_FP64) or double-FP32 tiles (SNK_PREC_MIXED);
+ * correlation); points with rho < 1e-14 add nothing.  P is the loaded
+ * density as given (no closed-shell factor; one per molecule of a batch
+ * handle).  The two products run as FP64 tiles (precision SNK_PREC_FP64),
+ * double-FP32 tiles (SNK_PREC_MIXED) or, with gemm SNK_GEMM_SPLIT, as bf16
+ * split products on the tcgen05 tensor cores (tc_slices_hi slices);
  * V is summed as exact fixed-point integers like K, so it is the same bit for
- * bit from run to run.  V_out: host N_b x N_b row-major (snk_build_Vxc) or
- * device N_b x N_b (snk_build_Vxc_device, enqueued on the library stream);
- * E_xc: host double, may be NULL (snk_build_Vxc_device then returns without
- * waiting for the stream).  Handles of one molecule only (SNK_ERR_UNSUPPORTED
- * otherwise); SNK_ERR_BAD_STATE before snk_set_density; SNK_ERR_INVALID_ARG
- * for an unknown functional or a NULL output. */
+ * bit from run to run.  V_out: host (snk_build_Vxc) or device
+ * (snk_build_Vxc_device, enqueued on the library stream), the packed
+ * molecule blocks like K (N_b x N_b row-major for one molecule); E_xc: host,
+ * one double per molecule, may be NULL (snk_build_Vxc_device then returns
+ * without waiting for the stream).  SNK_ERR_BAD_STATE before snk_set_density
+ * or with several densities loaded; SNK_ERR_INVALID_ARG for an unknown
+ * functional or a NULL output.  The first call plans the
+ * batches and sizes the V^xc workspace to at most half of the device memory
+ * free at that moment (SNK_ERR_OOM if even one batch does not fit); the
+ * workspace stays with the handle until snk_destroy. */
 enum { SNK_XC_LDA_X = 1, SNK_XC_PBE_X = 2, SNK_XC_PBE = 3 };
 int snk_build_Vxc(snk_ctx *ctx, int32_t functional, double *V_out, double *E_xc);
 int snk_build_Vxc_device(snk_ctx *ctx, int32_t functional, double *dV, double *E_xc);

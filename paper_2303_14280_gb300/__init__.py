@@ -470,22 +470,29 @@ class Engine:
 
     def build_Vxc(self, functional, out=None):
         """(V^xc, E_xc) of the loaded density (snk_build_Vxc; Sec. II.C) for
-        functional XC_LDA_X, XC_PBE_X or XC_PBE.  V is a host array, or with
-        out = a contiguous float64 CUDA tensor of N_b x N_b on the engine's
+        functional XC_LDA_X, XC_PBE_X or XC_PBE.  V is a host array (a list of
+        per-molecule arrays and E_xc a list for a batch handle), or with out =
+        a contiguous float64 CUDA tensor of the packed blocks on the engine's
         device, written there (E_xc is then read back, which waits for the
         engine's stream)."""
         fn = int(functional)
-        E = ctypes.c_double(0.0)
+        E = np.zeros(max(self.n_mol, 1))
+        Ep = _P(E.ctypes.data)
         if out is not None and _is_cuda_tensor(out):
             import torch
-            if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != self.nf * self.nf:
-                raise ValueError("out must be a contiguous float64 tensor of N_b x N_b elements")
-            self._check(lib().snk_build_Vxc_device(self._h, fn, _P(out.data_ptr()), ctypes.byref(E)),
-                        "snk_build_Vxc_device")
-            return out, E.value
-        V = np.empty((self.nf, self.nf))
-        self._check(lib().snk_build_Vxc(self._h, fn, _P(V.ctypes.data), ctypes.byref(E)), "snk_build_Vxc")
-        return V, E.value
+            if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != self.packed:
+                raise ValueError("out must be a contiguous float64 tensor of the packed blocks (N_b^2 per molecule)")
+            self._check(lib().snk_build_Vxc_device(self._h, fn, _P(out.data_ptr()), Ep), "snk_build_Vxc_device")
+            return out, (list(E) if self.batched else float(E[0]))
+        V = np.empty(self.packed)
+        self._check(lib().snk_build_Vxc(self._h, fn, _P(V.ctypes.data), Ep), "snk_build_Vxc")
+        if not self.batched:
+            return V.reshape(self.nf, self.nf), float(E[0])
+        out, off = [], 0
+        for n in self.nfs:
+            out.append(V[off:off + n * n].reshape(n, n))
+            off += n * n
+        return out, list(E)
 
     def screen_load(self, weights):
         """Load trained MLP weights for options screen='learned' (snk_screen_load)."""

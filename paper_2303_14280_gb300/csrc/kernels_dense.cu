@@ -221,6 +221,7 @@ __global__ void split_df32_copy_kernel(const double* __restrict__ src, int64_t n
 // ---------------------------------------------------------------- collocation
 
 constexpr int COL_THREADS = 128, COL_SHELLS = 8;
+constexpr double kColExpCut = 60.0;  // alpha r^2 beyond which a primitive is left out of X
 
 __global__ void __launch_bounds__(COL_THREADS) collocation_kernel(const BatchDesc* __restrict__ batches,
                                                                   const int* __restrict__ bshell,
@@ -252,7 +253,12 @@ __global__ void __launch_bounds__(COL_THREADS) collocation_kernel(const BatchDes
     const double dx = x - B.center[3 * sh], dy = y - B.center[3 * sh + 1], dz = z - B.center[3 * sh + 2];
     const double r2 = dx * dx + dy * dy + dz * dz;
     double rad = 0.0;
-    for (int k = B.poff[sh]; k < B.poff[sh] + B.nprim[sh]; ++k) rad += B.d[k] * exp(-B.exps[k] * r2);
+    for (int k = B.poff[sh]; k < B.poff[sh] + B.nprim[sh]; ++k) {
+      // e^{-60} ~ 9e-27: primitives that far out add nothing representable next to
+      // the batch's other values, and skipping the FP64 exponential is the saving
+      const double x = B.exps[k] * r2;
+      if (x < kColExpCut) rad += B.d[k] * exp(-x);
+    }
     const double* f = B.fcomp + B.foff[sh];
     if (l == 0) {
       out[0] = rad;

@@ -106,6 +106,11 @@ __device__ __forceinline__ void oz_emit8(const double* x, int e, int S, uint8_t*
   for (int q = 0; q < 8; ++q) r[q] = oz_fixed(x[q], e, T);
   for (int s = 0; s < S; ++s) {
     const int k = T - 8 * (s + 1);
+    // the slice's weight 2^(e - 8(s+1)) as a float, built from its exponent
+    // bits while it is a normal number (ldexpf only below that)
+    const int pw = e - 8 * (s + 1);
+    const bool normal = pw >= -126 && pw <= 127;
+    const float scale = normal ? __int_as_float((pw + 127) << 23) : 0.f;
     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -116,7 +121,8 @@ __device__ __forceinline__ void oz_emit8(const double* x, int e, int S, uint8_t*
       } else {
         d = r[q];
       }
-      v[q] = __float2bfloat16_rn(ldexpf((float)d, e - 8 * (s + 1)));  // exact: |d| <= 256
+      const float fd = (float)(int)d;  // exact: |d| <= 256
+      v[q] = __float2bfloat16_rn(normal ? fd * scale : ldexpf(fd, pw));  // exact: a power-of-two scaling
     }
     *reinterpret_cast<uint4*>(dst + (int64_t)s * kOzBlockBytes) = *reinterpret_cast<const uint4*>(v);
   }

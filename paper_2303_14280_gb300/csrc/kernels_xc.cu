@@ -38,6 +38,7 @@ namespace {
 
 constexpr int XC_THREADS = 128, XC_SHELLS = 8;
 constexpr double kXcRhoMin = 1e-14;
+constexpr double kXcExpCut = 60.0;  // alpha r^2 beyond which a primitive is left out of X and grad X
 constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ double pw_int(double x, int n) {  // x^n for n = 0, 1, 2 (0 for n < 0)
@@ -79,7 +80,9 @@ __global__ void __launch_bounds__(XC_THREADS)
     // radial part and its derivative over r^2 (times 2): sum d_k e^{-a_k r^2}, sum -2 a_k d_k e^{-a_k r^2}
     double R0 = 0.0, R1 = 0.0;
     for (int k = B.poff[sh]; k < B.poff[sh] + B.nprim[sh]; ++k) {
-      const double e = B.d[k] * exp(-B.exps[k] * r2);
+      const double x = B.exps[k] * r2;
+      if (x >= kXcExpCut) continue;  // e^{-60} ~ 9e-27: nothing representable next to the rest
+      const double e = B.d[k] * exp(-x);
       R0 += e;
       R1 = fma(-2.0 * B.exps[k], e, R1);
     }
@@ -209,21 +212,33 @@ __global__ void __launch_bounds__(XC_THREADS)
     }
   }
   // the warp's w eps in a fixed order, then one exact fixed-point addition
+  // into the batch's molecule
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) we += __shfl_down_sync(0xffffffffu, we, s);
-  if ((threadIdx.x & 31) == 0 && we != 0.0) khat_add(Ehat, we, err);
+  if ((threadIdx.x & 31) == 0 && we != 0.0) khat_add(Ehat + 2 * bd.mol, we, err);
 }
 
-// V = V-hat + V-hat^T and E_xc from their fixed-point sums (one molecule).
-__global__ void xc_finish_kernel(int64_t nf, const unsigned long long* __restrict__ Vhat,
+// V = V-hat + V-hat^T in every molecule block of the packed matrices, and
+// each molecule's E_xc, from their fixed-point sums.
+__global__ void xc_finish_kernel(const MolDesc* __restrict__ mols, int n_mol, int64_t packed,
+                                 const unsigned long long* __restrict__ Vhat,
                                  const unsigned long long* __restrict__ Ehat, double* __restrict__ V,
                                  double* __restrict__ E) {
-  const int64_t n2 = nf * nf;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / nf, c = e - r * nf;
-    V[e] = khat_value(Vhat + 2 * e) + khat_value(Vhat + 2 * (c * nf + r));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < packed; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_mol - 1;  // the molecule whose block holds e (blocks in pk_off order)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (mols[mid].pk_off <= e)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const int64_t off = mols[lo].pk_off, nf = mols[lo].nf;
+    const int64_t r = (e - off) / nf, c = (e - off) - r * nf;
+    V[e] = khat_value(Vhat + 2 * e) + khat_value(Vhat + 2 * (off + c * nf + r));
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *E = khat_value(Ehat);
+  if (blockIdx.x == 0)
+    for (int m = threadIdx.x; m < n_mol; m += blockDim.x) E[m] = khat_value(Ehat + 2 * m);
 }
 
 }  // namespace
@@ -245,11 +260,11 @@ cudaError_t launch_xc_point(cudaStream_t st, const BatchDesc* dbatch, int nbatch
   return cudaGetLastError();
 }
 
-cudaError_t launch_xc_finish(cudaStream_t st, int64_t nf, const unsigned long long* Vhat,
-                             const unsigned long long* Ehat, double* V, double* E) {
-  const int64_t n2 = nf * nf;
-  const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n2 + 255) / 256, 1), 4096);
-  xc_finish_kernel<<<blocks, 256, 0, st>>>(nf, Vhat, Ehat, V, E);
+cudaError_t launch_xc_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed,
+                             const unsigned long long* Vhat, const unsigned long long* Ehat, double* V, double* E) {
+  if (n_mol == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>(std::max<int64_t>((packed + 255) / 256, 1), 4096);
+  xc_finish_kernel<<<blocks, 256, 0, st>>>(mols, n_mol, packed, Vhat, Ehat, V, E);
   return cudaGetLastError();
 }
 

@@ -1372,12 +1372,18 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
   if (!dV) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
   if (!c->have_density) return fail(c, SNK_ERR_BAD_STATE, "snk_build_Vxc called before snk_set_density");
   Setup& s = c->s;
-  if (s.n_mol != 1) return fail(c, SNK_ERR_UNSUPPORTED, "snk_build_Vxc takes handles of one molecule");
+  if (c->n_dens != 1) return fail(c, SNK_ERR_BAD_STATE, "several densities are loaded: load one for snk_build_Vxc");
   const int nb = c->nbatch;
-  const int64_t nf = s.nf;
+  const int64_t pk = s.packed;
+  const int nm = s.n_mol;
   const bool tc = c->opt.precision == SNK_PREC_MIXED && c->opt.gemm == SNK_GEMM_SPLIT;
   const int S = c->opt.tc_slices_hi;  // slices of both tensor-core products
   if (c->xc_chunks.empty() && nb > 0) {
+    // chunk budget: half of what is free now (the exchange build's buffers are
+    // already held), at most half of the handle's workspace budget
+    size_t fr = 0, tot = 0;
+    SNK_CK(c, cudaMemGetInfo(&fr, &tot));
+    const int64_t budget = std::max<int64_t>(std::min<int64_t>(c->ws_budget / 2, (int64_t)(fr / 2)), 1ll << 26);
     std::vector<BatchDesc> bd(nb);
     std::vector<OzSplitJob> sj;
     std::vector<OzGemmJob> gj;
@@ -1397,7 +1403,7 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
       b.sfunc_off = b.xfunc_off;  // the products' row lists are B_j too
       const int64_t blk = (int64_t)b.ldq * b.nB;
       const int64_t need = (off + 5 * blk) * 8 + std::max(a0 + arena_of(b, 0), a1 + arena_of(b, 1));
-      if (j > ch.b0 && need > c->ws_budget / 2) {  // beside the exchange workspace
+      if (j > ch.b0 && need > budget) {
         ch.b1 = j;
         chunks.push_back(ch);
         most = std::max(most, off);
@@ -1512,8 +1518,8 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
   const bool fresh_err = !c->ozerr.p;
   SNK_CK(c, c->ozerr.ensure(1));
   if (fresh_err) SNK_CK(c, cudaMemsetAsync(c->ozerr.p, 0, sizeof(int), c->stream));
-  SNK_CK(c, c->xchat.ensure((size_t)(2 * nf * nf + 2)));
-  SNK_CK(c, c->xcE.ensure(1));
+  SNK_CK(c, c->xchat.ensure((size_t)(2 * pk + 2 * nm)));
+  SNK_CK(c, c->xcE.ensure((size_t)std::max(nm, 1)));
   const size_t nev = 1 + 4 * c->xc_chunks.size();
   while (c->xcev.size() < nev) {
     cudaEvent_t ev;
@@ -1523,9 +1529,9 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
   const cudaStream_t st = c->stream;
   const int mode = c->opt.precision == SNK_PREC_MIXED ? 2 : 0;
   unsigned long long* Vhat = c->xchat.p;
-  unsigned long long* Ehat = c->xchat.p + 2 * nf * nf;
+  unsigned long long* Ehat = c->xchat.p + 2 * pk;
   int ev = 0;
-  SNK_CK(c, cudaMemsetAsync(c->xchat.p, 0, sizeof(unsigned long long) * (2 * nf * nf + 2), st));
+  SNK_CK(c, cudaMemsetAsync(c->xchat.p, 0, sizeof(unsigned long long) * (2 * pk + 2 * nm), st));
   SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
   for (const auto& ch : c->xc_chunks) {
     const BatchDesc* db = c->xcbatch.p + ch.b0;
@@ -1546,13 +1552,13 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
     } else {
       SNK_CK(c, launch_xc_vgemm(st, db, n, ch.max_nB, c->xfunc.p, c->xcws.p, Vhat, mode, c->ozerr.p));
     }
-    if (&ch == &c->xc_chunks.back()) SNK_CK(c, launch_xc_finish(st, nf, Vhat, Ehat, dV, c->xcE.p));
+    if (&ch == &c->xc_chunks.back()) SNK_CK(c, launch_xc_finish(st, c->mols.p, nm, pk, Vhat, Ehat, dV, c->xcE.p));
     SNK_CK(c, cudaEventRecord(c->xcev[ev++], st));
   }
-  if (c->xc_chunks.empty()) SNK_CK(c, launch_xc_finish(st, nf, Vhat, Ehat, dV, c->xcE.p));
+  if (c->xc_chunks.empty()) SNK_CK(c, launch_xc_finish(st, c->mols.p, nm, pk, Vhat, Ehat, dV, c->xcE.p));
   c->xc_timed = !c->xc_chunks.empty();
   if (!E_host) return SNK_OK;
-  SNK_CK(c, cudaMemcpyAsync(E_host, c->xcE.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SNK_CK(c, cudaMemcpyAsync(E_host, c->xcE.p, sizeof(double) * nm, cudaMemcpyDeviceToHost, st));
   SNK_CK(c, cudaStreamSynchronize(st));
   return check_device_flags(c);
 }
@@ -1729,14 +1735,15 @@ int snk_build_Vxc_device(snk_ctx* c, int32_t functional, double* dV, double* E_x
 int snk_build_Vxc(snk_ctx* c, int32_t functional, double* V, double* E_xc) {
   if (!c) return SNK_ERR_INVALID_ARG;
   if (!V) return fail(c, SNK_ERR_INVALID_ARG, "NULL output");
-  const size_t n = (size_t)c->s.nf * (size_t)c->s.nf;
+  const size_t n = (size_t)c->s.packed;
   SNK_CK(c, c->K.ensure(std::max<size_t>(n, 1)));
-  double e = 0.0;
-  int rc = build_vxc(c, functional, c->K.p, &e);
+  std::vector<double> e((size_t)std::max(c->s.n_mol, 1), 0.0);
+  int rc = build_vxc(c, functional, c->K.p, e.data());
   if (rc != SNK_OK) return rc;
   if (n) SNK_CK(c, cudaMemcpyAsync(V, c->K.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
   SNK_CK(c, cudaStreamSynchronize(c->stream));
-  if (E_xc) *E_xc = e;
+  if (E_xc)
+    for (int m = 0; m < c->s.n_mol; ++m) E_xc[m] = e[m];
   return SNK_OK;
 }
 

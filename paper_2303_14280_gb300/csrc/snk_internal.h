@@ -271,7 +271,8 @@ cudaError_t launch_symcheck(cudaStream_t st, const MolDesc* mols, int n_mol, int
 // Exchange-correlation potential (Sec. II.C).  Per batch at BatchDesc::xoff:
 // X, dX/dx, dX/dy, dX/dz (ldq x nB each), then F / Z at BatchDesc::foff.
 // mode: 0 FP64 tiles, 2 double-FP32 tiles.  Vhat (two words per entry of the
-// molecule's block at pk_off, see khat_add) and Ehat (two words) accumulate.
+// molecule's block at pk_off, see khat_add) and Ehat (two words per
+// molecule, at 2 BatchDesc::mol) accumulate.
 cudaError_t launch_xc_colloc(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_ldq, int max_nBshell,
                              const int* bshell, const int* bshell_col, const double* xyz, DeviceBasis basis,
                              double* ws);
@@ -281,9 +282,10 @@ cudaError_t launch_xc_point(cudaStream_t st, const BatchDesc* dbatch, int nbatch
                             int functional, double* ws, unsigned long long* Ehat, int* err);
 cudaError_t launch_xc_vgemm(cudaStream_t st, const BatchDesc* dbatch, int nbatch, int max_nB, const int* xfunc,
                             const double* ws, unsigned long long* Vhat, int mode, int* err);
-// V = V-hat + V-hat^T (nf x nf, one molecule) and *E = E-hat.
-cudaError_t launch_xc_finish(cudaStream_t st, int64_t nf, const unsigned long long* Vhat,
-                             const unsigned long long* Ehat, double* V, double* E);
+// V = V-hat + V-hat^T in every molecule block of the packed matrices, and
+// E[m] = E-hat of molecule m (two words per molecule).
+cudaError_t launch_xc_finish(cudaStream_t st, const MolDesc* mols, int n_mol, int64_t packed,
+                             const unsigned long long* Vhat, const unsigned long long* Ehat, double* V, double* E);
 
 struct IntegralArgs {
   const Tile* tiles;

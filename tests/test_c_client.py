@@ -61,6 +61,9 @@ int main(void) {
   CHECK(snk_set_density(NULL, NULL) == SNK_ERR_INVALID_ARG);
   CHECK(snk_set_density_multi(NULL, 2, NULL) == SNK_ERR_INVALID_ARG);
   CHECK(snk_build_K_multi(NULL, NULL) == SNK_ERR_INVALID_ARG);
+  CHECK(snk_build_Vxc(NULL, SNK_XC_PBE, NULL, NULL) == SNK_ERR_INVALID_ARG);
+  CHECK(snk_build_Vxc_device(NULL, SNK_XC_LDA_X, NULL, NULL) == SNK_ERR_INVALID_ARG);
+  CHECK(SNK_XC_LDA_X == 1 && SNK_XC_PBE_X == 2 && SNK_XC_PBE == 3);
   CHECK(strlen(snk_status_string(SNK_ERR_NOT_SYMMETRIC)) > 0);
   CHECK(strcmp(snk_last_error(NULL), "NULL handle") == 0);
   snk_destroy(NULL);

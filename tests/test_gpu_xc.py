@@ -115,12 +115,25 @@ def test_errors(snk, chain4):
     assert e.value.status == -1
     V, E = eng.build_Vxc(oracle.XC_LDA_X)        # the handle is still usable
     assert np.isfinite(E) and E < 0
-    mols = [synth.small_molecule(0), synth.small_molecule(1)]
-    beng = snk.Engine([m.basis for m in mols], [m.grid for m in mols])
-    beng.set_density([m.P for m in mols])
+    eng.set_density([chain4.P, 0.5 * chain4.P])     # two densities loaded: one at a time for V^xc
     with pytest.raises(snk.SnkError) as e:
-        beng.build_Vxc(oracle.XC_LDA_X)
-    assert e.value.status == -2
+        eng.build_Vxc(oracle.XC_PBE)
+    assert e.value.status == -4
+
+
+@pytest.mark.parametrize("gemm", ["fp64", "split"])
+def test_batch_handle_per_molecule(snk, gemm):
+    """Several molecules in one handle: every molecule's V^xc block and E_xc
+    against the oracle on that molecule alone."""
+    mols = [synth.small_molecule(m) for m in range(3)]
+    opts = dict() if gemm == "fp64" else dict(precision="mixed", gemm="split", tc_slices_hi=5)
+    beng = snk.Engine([m.basis for m in mols], [m.grid for m in mols], **opts)
+    beng.set_density([m.P for m in mols])
+    Vs, Es = beng.build_Vxc(oracle.XC_PBE)
+    tol = TOL if gemm == "fp64" else TOL_SPLIT
+    for m, V, E in zip(mols, Vs, Es):
+        Vr, Er = oracle.vxc(m.basis, m.grid, m.P, oracle.XC_PBE)
+        assert np.max(np.abs(V - Vr)) <= tol and abs(E - Er) <= tol
 
 
 GOLDEN96 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cluster96_vxc_entries.txt")
