@@ -429,6 +429,7 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel_f32(IntegralArgs 
         };
         const int ppn = s_ppn[r];
         if (ppn <= kStage) {
+#pragma unroll 2
           for (int q = 0; q < ppn; ++q) prim(rec[2 * q], rec[2 * q + 1]);
         } else {  // more primitive pairs than staged: global memory
           const float4* pp = a.prims_f32 + (size_t)s_ppo[r] * 2;
