@@ -482,6 +482,8 @@ class Engine:
             import torch
             if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != self.packed:
                 raise ValueError("out must be a contiguous float64 tensor of the packed blocks (N_b^2 per molecule)")
+            if out.device.index != self.device_index:
+                raise ValueError(f"out must be on cuda:{self.device_index}, the engine's device")
             self._check(lib().snk_build_Vxc_device(self._h, fn, _P(out.data_ptr()), Ep), "snk_build_Vxc_device")
             return out, (list(E) if self.batched else float(E[0]))
         V = np.empty(self.packed)

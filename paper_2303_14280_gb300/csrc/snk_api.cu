@@ -1387,7 +1387,7 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
     std::vector<BatchDesc> bd(nb);
     std::vector<OzSplitJob> sj;
     std::vector<OzGemmJob> gj;
-    int64_t off = 0, most = 0, arena = 0, arena_most = 0;
+    int64_t off = 0, most = 0, arena_most = 0;
     double flops = 0.0, bytes = 0.0;
     // slice bytes of batch b in each phase (the phases reuse one arena)
     auto arena_of = [&](const BatchDesc& b, int phase) -> int64_t {
@@ -1428,7 +1428,6 @@ int build_vxc(snk_ctx* c, int fn, double* dV, double* E_host) {
     chunks.push_back(ch);
     most = std::max(most, off);
     arena_most = std::max(arena_most, std::max(a0, a1));
-    (void)arena;
     if (tc) {
       for (auto& C : chunks) {
         for (int phase = 0; phase < 2; ++phase) {
