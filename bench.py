@@ -249,7 +249,16 @@ def run_reference(args, rank, world):
     import oracle
     import synth
     oracle.build()
-    probs = make_problems(args.workload)
+    # the inputs are made on the GPU when there is one (the Becke partition of
+    # millions of points; not timed), the oracle alone runs on the host cores
+    dev = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = torch.device("cuda", 0)
+    except ImportError:
+        pass
+    probs = make_problems(args.workload, device=dev)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     rng = np.random.default_rng(1)
     n_total = sum(p.grid.n_points for p in probs)
