@@ -1,13 +1,16 @@
 // Exchange-correlation potential of libsnk (sm_103a), Sec. II.C:
 //
 //   Phi_{mu i}, grad Phi_{mu i}                         Eq. (collocation)
-//   F_j = X_j P[B_j, B_j]                                Eq. (fmat)       (kernels_dense.cu)
+//   F_j = X_j P[B_j, B_j]                                Eq. (fmat)       (products below)
 //   rho_i = sum_mu F_{mu i} Phi_{mu i},
 //   grad rho_i = 2 sum_mu F_{mu i} grad Phi_{mu i}       Eq. (den_grid)
 //   eps, d eps / d rho, d eps / d gamma at each point    Eq. (exc_grid)
 //   Z_{mu i} = w_i/2 (E^rho Phi + 4 E^gamma grad rho . grad Phi)   Eq. (zmat)
-//   V-hat += Z_j^T X_j, V = V-hat + V-hat^T              Eq. (vxc_num)  (product in kernels_dense.cu)
+//   V-hat += Z_j^T X_j, V = V-hat + V-hat^T              Eq. (vxc_num)
 //
+// The two products are FP64 or double-FP32 tiles (kernels_dense.cu) or the
+// tcgen05 split products (kernels_ozaki.cu, plain column-major epilogue for F
+// and the fixed-point scatter for V-hat).
 // per batch of the handle's octree, in the same column-major layout as the
 // exchange build (point index fastest, leading dimension ldq): X, dX/dx,
 // dX/dy, dX/dz and F (overwritten by Z) are five consecutive ldq x nB blocks.
