@@ -191,3 +191,15 @@ def test_vxc_entries_mode_matches_full(chain4):
     Ve, Ee = oracle.vxc_entries(b, g, chain4.P, PBE, mu, nu)
     np.testing.assert_allclose(Ve, V[mu, nu], rtol=1e-13, atol=1e-15)
     assert abs(Ee - E) <= 1e-13 * abs(E)
+
+
+def test_vxc_rejects_bad_arguments(chain4):
+    """An unknown functional or an entry outside the basis is refused, not read out of bounds."""
+    b, g = chain4.basis, _subgrid(chain4.grid, 50)
+    with pytest.raises(ValueError):
+        oracle.vxc(b, g, chain4.P, 7)
+    with pytest.raises(ValueError):
+        oracle.vxc_entries(b, g, chain4.P, PBE, [0, 34], [0, 0])
+    with pytest.raises(ValueError):
+        oracle.xc_point(0, 1.0, 0.0)
+    assert np.all(oracle.xc_point(PBE, 1e-15, 1.0) == 0.0)    # below the density cut-off
